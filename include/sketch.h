@@ -1,0 +1,208 @@
+/*
+ * sketch.h -- C ABI of a GB300 (sm_103a) implementation of the convolved
+ * Count sketch of Heddes, Nunes, Givargis and Nicolau, "Convolution and
+ * Cross-Correlation of Count Sketches Enables Fast Cardinality Estimation of
+ * Multi-Join Queries" (PACMMOD 2024).
+ *
+ * The library keeps, for one join query over relations R_0 .. R_{r-1}, one
+ * Count sketch per relation and per median row (d rows), updates them from
+ * batches of tuples on the GPU (Algorithm 2), and estimates the query's
+ * cardinality by combining the sketches with circular cross-correlation and
+ * Hadamard products (Algorithm 3), taking the median over rows (Section 3.3).
+ *
+ * Conventions for every function
+ *   - Returns an sk_status: SK_OK (0) or a negative error code; never throws,
+ *     never aborts.  sk_status_string() names a code.
+ *   - "dev_" pointers are CUDA device pointers (or managed memory) on the
+ *     current device; every other pointer is host memory.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it and is asynchronous unless stated.
+ *   - The caller owns every buffer it passes (counters, columns, weights) and
+ *     keeps it alive until the stream work that uses it has completed.  The
+ *     library owns the sk_set handle, its hash-coefficient table, its status
+ *     word and its estimator scratch; sk_sketch_destroy frees them.
+ *   - Errors found on the device (a key outside a declared domain, an
+ *     estimator overflow) are recorded in the set's status word and reported
+ *     by the next sk_sync or sk_estimate_join.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef SK_SKETCH_H
+#define SK_SKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sk_status;
+
+enum {
+  SK_OK = 0,
+  SK_ERR_INVALID_ARG = -1,        /* null pointer, bad size, relation out of range ... */
+  SK_ERR_CYCLIC_QUERY = -2,       /* the joins close a cycle (Section 2.6: joins are non-cyclic) */
+  SK_ERR_DISCONNECTED_QUERY = -3, /* the relations do not form one connected join graph */
+  SK_ERR_SELF_EDGE = -4,          /* a join inside one relation (use a fictitious copy, Section 2.6) */
+  SK_ERR_UNSUPPORTED_WIDTH = -5,  /* m out of range for the requested operation */
+  SK_ERR_BUFFER_TOO_SMALL = -6,   /* counters buffer smaller than sk_sketch_bytes */
+  SK_ERR_MISMATCH = -7,           /* merge of sets with different query, m, d or seed */
+  SK_ERR_KEY_OUT_OF_DOMAIN = -8,  /* a key fell outside the declared domain_hint (tuple skipped) */
+  SK_ERR_TIMEOUT = -9,            /* a bounded device wait gave up */
+  SK_ERR_CUDA = -10,              /* a CUDA runtime call failed */
+  SK_ERR_OVERFLOW = -11,          /* an exact intermediate would leave the signed 256-bit range */
+  SK_ERR_INEXACT = -12,           /* an FFT correlation could not be certified exact */
+  SK_ERR_NO_MEMORY = -13          /* device allocation failed */
+};
+
+/* Largest number of median rows d a set may have. */
+#define SK_MAX_ROWS 64
+
+/* One join {u, v} between attribute attr_a of relation rel_a and attribute
+ * attr_b of relation rel_b (Section 2.6 notation: an edge of the join graph). */
+typedef struct {
+  int32_t rel_a, attr_a, rel_b, attr_b;
+} sk_edge;
+
+/* A join query Q(R_0, ..., R_{r-1}).  num_join_attrs[k] = |Omega(R_k)| >= 1; the
+ * attributes of R_k are numbered 0 .. |Omega(R_k)|-1 and are the columns of
+ * that relation's update batches, in that order.  The joins must make the
+ * relations one tree (connected, r - 1 joins, no cycle), and every attribute
+ * must take part in at least one join.  Components Psi are the connected
+ * components of the attribute graph; each gets one bin function, each join
+ * one sign function (Section 3.2, Initialization). */
+typedef struct {
+  int32_t num_relations;
+  const int32_t* num_join_attrs;
+  int32_t num_edges;
+  const sk_edge* edges;
+} sk_query;
+
+/* Opaque handle: a query, its hash functions and its counters. */
+typedef struct sk_set sk_set;
+
+/* Signed 256-bit two's-complement integer, little-endian 64-bit limbs. */
+typedef struct {
+  uint64_t limb[4];
+} sk_i256;
+
+/* Result of sk_estimate_join.  row[i] is median row i's estimate X (Eq. 5,
+ * computed by Algorithm 3), exact.  median is the lower median of the d rows,
+ * row[(d-1)/2] of the sorted values (Section 3.3, median trick). */
+typedef struct {
+  sk_i256 median;
+  int64_t median_i64;    /* == median when fits_i64 */
+  int32_t fits_i64;
+  int32_t d;
+  double median_f64;     /* median rounded to double */
+  double mid_mean_f64;   /* mean of the two middle rows (the middle row if d is odd) */
+  double max_residual;   /* max |y - round(y)| over every FFT output rounded to an integer */
+  int32_t max_limbs;     /* largest number of limbs an operand of a correlation was split into */
+  int32_t limb_bits;     /* limb width B of the last correlation step */
+  int32_t corr_steps;    /* correlation steps per row (Algorithm 3's FFT lines) */
+  int32_t retries;       /* steps redone with narrower limbs after a failed certificate */
+  sk_i256 row[SK_MAX_ROWS];
+} sk_estimate;
+
+/* ---------------------------------------------------------------------------
+ * sk_sketch_bytes: size in bytes of the counters buffer for (query, m, d):
+ * r * d * m int64 counters, laid out [relation][row][bucket].
+ * Errors: SK_ERR_INVALID_ARG, query validation codes. */
+sk_status sk_sketch_bytes(const sk_query* query, int64_t m, int32_t d, size_t* bytes);
+
+/* ---------------------------------------------------------------------------
+ * sk_sketch_create: Algorithm 1 lines 1-2 and the initialisation of Section 3.2.
+ * Validates the query, draws per row one bin function per component and one sign
+ * function per join (SplitMix64 from `seed`, each coefficient an element of
+ * GF(2^61 - 1)), uploads them, and zeroes the caller's counters buffer
+ * (dev_counters, `bytes` >= sk_sketch_bytes) on cuda_stream.
+ * 1 <= m <= 2^30 (the estimator additionally needs m a power of two, 2..2^22);
+ * 1 <= d <= SK_MAX_ROWS.  *out receives the handle.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CYCLIC_QUERY, SK_ERR_DISCONNECTED_QUERY,
+ * SK_ERR_SELF_EDGE, SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_BUFFER_TOO_SMALL,
+ * SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
+sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t seed,
+                           void* dev_counters, size_t bytes, void* cuda_stream, sk_set** out);
+
+/* ---------------------------------------------------------------------------
+ * sk_sketch_update_batch: Algorithm 2 for n_rows tuples of relation `relation`.
+ * Tuple i has key dev_cols[a * col_stride + i] for its attribute a (int64,
+ * attribute-major, col_stride >= n_rows) and frequency change
+ * Delta_i = dev_weights[i] (NULL: Delta = 1).  For every median row the tuple's
+ * bin is (sum over its attributes u of h_Psi(u)(key_u)) mod m (Eq. 3) and its
+ * sign the product of s_{u,v}(key_u) over its joins (Eq. 2); counter
+ * [relation][row][bin] += sign * Delta in wrapping int64 (Eq. 4).  A key maps to
+ * the field as (uint64)key mod (2^61 - 1).  domain_hint (host array of |Omega|
+ * exclusive upper bounds, or NULL) declares 0 <= key < bound; tuples with a key
+ * outside it are skipped and SK_ERR_KEY_OUT_OF_DOMAIN is recorded.
+ * Asynchronous on cuda_stream; the columns and weights must stay valid until it
+ * completes.  n_rows == 0 is a no-op.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_sketch_update_batch(sk_set* set, int32_t relation, int64_t n_rows, const int64_t* dev_cols,
+                                 int64_t col_stride, const int64_t* dev_weights,
+                                 const int64_t* domain_hint, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * sk_sketch_merge: dst += src, counter by counter (Section 2.2: linear sketches
+ * combine by addition).  Both sets must have the same query, m, d and seed.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_MISMATCH, SK_ERR_CUDA. */
+sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * sk_estimate_join: Algorithm 3 for every median row, then the lower median.
+ * Root attribute: attribute 0 of relation 0.  Each circular cross-correlation
+ * IFFT(conj(FFT(a)) o FFT(x)) is computed with FP64 FFTs on signed limbs of the
+ * exact operands and rounded back to exact integers; Hadamard products and sums
+ * are exact signed 256-bit integers.  Requires m a power of two, 2 <= m <= 2^22.
+ * Synchronises cuda_stream and fills *out (host memory).
+ * Errors: SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_OVERFLOW, SK_ERR_INEXACT,
+ * SK_ERR_KEY_OUT_OF_DOMAIN (from earlier updates), SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
+sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * sk_sketch_reset: zeroes every counter of the set and its device status word on
+ * cuda_stream (the "set a block of memory to zeros" initialisation of Section
+ * 2.2, without redrawing the hash functions).
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_sketch_reset(sk_set* set, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * sk_sync: synchronises cuda_stream and returns (then clears) the first error
+ * recorded on the device for this set since the last sk_sync. */
+sk_status sk_sync(sk_set* set, void* cuda_stream);
+
+/* sk_sketch_destroy: frees the handle, its coefficient table, status word and
+ * scratch.  Does not touch the caller's counters.  NULL is a no-op. */
+sk_status sk_sketch_destroy(sk_set* set);
+
+/* sk_status_string: static, human-readable name of a status code. */
+const char* sk_status_string(sk_status status);
+
+/* ---------------------------------------------------------------------------
+ * Introspection and test hooks.
+ *
+ * sk_sketch_info: r, m, d, number of components and of joins of a set.
+ * sk_get_coefficients: copies the hash coefficients to host memory:
+ *   uint64 [d][2*components + 4*joins]; per row (b0, b1) of each component's bin
+ *   function h(x) = ((b1 x + b0) mod p) mod m, then (s0, s1, s2, s3) of each
+ *   join's sign function s(x) = +1 if (s0 + s1 x + s2 x^2 + s3 x^3) mod p is even,
+ *   else -1; components are numbered by their smallest attribute, joins sorted
+ *   by their endpoints (attributes numbered relation by relation).
+ *   `count` is the number of uint64 the host buffer holds.
+ * sk_set_coefficients: replaces the table (same layout; every value < 2^61 - 1),
+ *   e.g. to run the method with chosen hash functions.  Enqueued on cuda_stream.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_sketch_info(const sk_set* set, int32_t* r, int64_t* m, int32_t* d, int32_t* n_components,
+                         int32_t* n_joins);
+sk_status sk_get_coefficients(const sk_set* set, uint64_t* host_out, size_t count);
+sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t count, void* cuda_stream);
+
+/* sk_launch_count: number of CUDA kernels this library has launched in this process
+ * (all sets, all devices), for accounting of GPU work. */
+int64_t sk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SK_SKETCH_H */

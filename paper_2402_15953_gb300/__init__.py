@@ -1,0 +1,274 @@
+"""GB300 (sm_103a) convolved Count sketches for multi-join cardinality estimation.
+
+Heddes, Nunes, Givargis, Nicolau, "Convolution and Cross-Correlation of Count
+Sketches Enables Fast Cardinality Estimation of Multi-Join Queries", PACMMOD
+2024.  The computation lives in libsketch.so (C ABI, include/sketch.h; CUDA
+kernels under csrc/); this module only marshals arguments to it with ctypes.
+PyTorch is used for device memory and streams.
+
+The C functions are exposed under their own names (sk_sketch_create,
+sk_sketch_update_batch, sk_sketch_merge, sk_estimate_join, ...), each raising
+SketchError on a non-zero status; SketchSet wraps a handle together with its
+torch-owned counters.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsketch.so")
+
+SK_MAX_ROWS = 64
+
+STATUS = {
+    0: "SK_OK", -1: "SK_ERR_INVALID_ARG", -2: "SK_ERR_CYCLIC_QUERY", -3: "SK_ERR_DISCONNECTED_QUERY",
+    -4: "SK_ERR_SELF_EDGE", -5: "SK_ERR_UNSUPPORTED_WIDTH", -6: "SK_ERR_BUFFER_TOO_SMALL",
+    -7: "SK_ERR_MISMATCH", -8: "SK_ERR_KEY_OUT_OF_DOMAIN", -9: "SK_ERR_TIMEOUT", -10: "SK_ERR_CUDA",
+    -11: "SK_ERR_OVERFLOW", -12: "SK_ERR_INEXACT", -13: "SK_ERR_NO_MEMORY",
+}
+globals().update({name: code for code, name in STATUS.items()})
+
+
+class SketchError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class sk_edge(ctypes.Structure):
+    _fields_ = [("rel_a", ctypes.c_int32), ("attr_a", ctypes.c_int32),
+                ("rel_b", ctypes.c_int32), ("attr_b", ctypes.c_int32)]
+
+
+class sk_query(ctypes.Structure):
+    _fields_ = [("num_relations", ctypes.c_int32), ("num_join_attrs", ctypes.POINTER(ctypes.c_int32)),
+                ("num_edges", ctypes.c_int32), ("edges", ctypes.POINTER(sk_edge))]
+
+
+class sk_i256(ctypes.Structure):
+    _fields_ = [("limb", ctypes.c_uint64 * 4)]
+
+    def value(self) -> int:
+        v = 0
+        for k in range(4):
+            v |= int(self.limb[k]) << (64 * k)
+        return v - (1 << 256) if v >> 255 else v
+
+
+class sk_estimate(ctypes.Structure):
+    _fields_ = [("median", sk_i256), ("median_i64", ctypes.c_int64), ("fits_i64", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("median_f64", ctypes.c_double), ("mid_mean_f64", ctypes.c_double),
+                ("max_residual", ctypes.c_double), ("max_limbs", ctypes.c_int32), ("limb_bits", ctypes.c_int32),
+                ("corr_steps", ctypes.c_int32), ("retries", ctypes.c_int32), ("row", sk_i256 * SK_MAX_ROWS)]
+
+
+EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_sketch_merge",
+           "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
+           "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count"]
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Loads libsketch.so (build it with paper_2402_15953_gb300.build.build()).  There is
+    no fallback: without the library nothing in this package runs."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libsketch.so not built ({p}); run python -m paper_2402_15953_gb300.build")
+    L = ctypes.CDLL(p)
+    vp, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    qp = ctypes.POINTER(sk_query)
+    L.sk_sketch_bytes.argtypes = [qp, i64, i32, ctypes.POINTER(sz)]
+    L.sk_sketch_create.argtypes = [qp, i64, i32, u64, vp, sz, vp, ctypes.POINTER(vp)]
+    L.sk_sketch_update_batch.argtypes = [vp, i32, i64, vp, i64, vp, vp, vp]
+    L.sk_sketch_merge.argtypes = [vp, vp, vp]
+    L.sk_estimate_join.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
+    L.sk_sync.argtypes = [vp, vp]
+    L.sk_sketch_destroy.argtypes = [vp]
+    L.sk_status_string.argtypes = [i32]
+    L.sk_status_string.restype = ctypes.c_char_p
+    L.sk_sketch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.sk_get_coefficients.argtypes = [vp, ctypes.POINTER(u64), sz]
+    L.sk_set_coefficients.argtypes = [vp, ctypes.POINTER(u64), sz, vp]
+    L.sk_sketch_reset.argtypes = [vp, vp]
+    L.sk_launch_count.argtypes = []
+    L.sk_launch_count.restype = i64
+    for name in EXPORTS:
+        if name not in ("sk_status_string", "sk_launch_count"):
+            getattr(L, name).restype = i32
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise SketchError(st, where)
+
+
+def make_query(num_join_attrs: Sequence[int], edges: Sequence[Tuple[int, int, int, int]]):
+    """Builds an sk_query; returns (query, keepalive) -- keep the second value alive while the
+    query is in use."""
+    attrs = (ctypes.c_int32 * len(num_join_attrs))(*[int(a) for a in num_join_attrs])
+    earr = (sk_edge * max(1, len(edges)))(*[sk_edge(*[int(v) for v in e]) for e in edges])
+    q = sk_query(len(num_join_attrs), attrs, len(edges), earr)
+    return q, (attrs, earr)
+
+
+# ---- the C ABI under its own names ----------------------------------------------------
+
+def sk_sketch_bytes(query: sk_query, m: int, d: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().sk_sketch_bytes(ctypes.byref(query), m, d, ctypes.byref(out)), "sk_sketch_bytes")
+    return out.value
+
+
+def sk_sketch_create(query: sk_query, m: int, d: int, seed: int, dev_counters: int, nbytes: int,
+                     stream: int) -> int:
+    h = ctypes.c_void_p(0)
+    _check(load().sk_sketch_create(ctypes.byref(query), m, d, seed & 0xFFFF_FFFF_FFFF_FFFF, dev_counters, nbytes,
+                                   stream, ctypes.byref(h)), "sk_sketch_create")
+    return h.value
+
+
+def sk_sketch_update_batch(handle: int, relation: int, n_rows: int, dev_cols: int, col_stride: int,
+                           dev_weights: Optional[int], domain_hint: Optional[Sequence[int]], stream: int) -> None:
+    dom = None
+    if domain_hint is not None:
+        dom = (ctypes.c_int64 * len(domain_hint))(*[int(v) for v in domain_hint])
+    _check(load().sk_sketch_update_batch(handle, relation, n_rows, dev_cols, col_stride, dev_weights or None,
+                                         ctypes.cast(dom, ctypes.c_void_p) if dom is not None else None, stream),
+           "sk_sketch_update_batch")
+
+
+def sk_sketch_merge(dst: int, src: int, stream: int) -> None:
+    _check(load().sk_sketch_merge(dst, src, stream), "sk_sketch_merge")
+
+
+def sk_estimate_join(handle: int, stream: int) -> sk_estimate:
+    out = sk_estimate()
+    _check(load().sk_estimate_join(handle, ctypes.byref(out), stream), "sk_estimate_join")
+    return out
+
+
+def sk_sync(handle: int, stream: int) -> None:
+    _check(load().sk_sync(handle, stream), "sk_sync")
+
+
+def sk_sketch_destroy(handle: int) -> None:
+    _check(load().sk_sketch_destroy(handle), "sk_sketch_destroy")
+
+
+def sk_sketch_reset(handle: int, stream: int) -> None:
+    _check(load().sk_sketch_reset(handle, stream), "sk_sketch_reset")
+
+
+def sk_launch_count() -> int:
+    return int(load().sk_launch_count())
+
+
+def sk_status_string(status: int) -> str:
+    return load().sk_status_string(status).decode()
+
+
+def sk_sketch_info(handle: int):
+    r, m, d, c, e = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().sk_sketch_info(handle, ctypes.byref(r), ctypes.byref(m), ctypes.byref(d), ctypes.byref(c),
+                                 ctypes.byref(e)), "sk_sketch_info")
+    return r.value, m.value, d.value, c.value, e.value
+
+
+def sk_get_coefficients(handle: int) -> List[List[int]]:
+    _, _, d, c, e = sk_sketch_info(handle)
+    row = 2 * c + 4 * e
+    buf = (ctypes.c_uint64 * (d * row))()
+    _check(load().sk_get_coefficients(handle, buf, d * row), "sk_get_coefficients")
+    return [[int(buf[i * row + j]) for j in range(row)] for i in range(d)]
+
+
+def sk_set_coefficients(handle: int, coeffs: Sequence[Sequence[int]], stream: int) -> None:
+    flat = [int(v) for r in coeffs for v in r]
+    buf = (ctypes.c_uint64 * len(flat))(*flat)
+    _check(load().sk_set_coefficients(handle, buf, len(flat), stream), "sk_set_coefficients")
+
+
+# ---- convenience wrapper ---------------------------------------------------------------
+
+class SketchSet:
+    """The sketches of one join query: counters are a torch int64 tensor [r][d][m] on the
+    current CUDA device; all work runs in libsketch.so on the current torch stream."""
+
+    def __init__(self, num_join_attrs: Sequence[int], edges: Sequence[Tuple[int, int, int, int]], m: int,
+                 d: int, seed: int, device=None, counters=None):
+        import torch
+        self._torch = torch
+        self.num_join_attrs = list(num_join_attrs)
+        self.edges = [tuple(e) for e in edges]
+        self.m, self.d, self.seed = int(m), int(d), int(seed)
+        self.query, self._keep = make_query(self.num_join_attrs, self.edges)
+        nbytes = sk_sketch_bytes(self.query, self.m, self.d)
+        r = len(self.num_join_attrs)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if counters is None:
+            counters = torch.empty((r, self.d, self.m), dtype=torch.int64, device=dev)
+        self.counters = counters
+        self.handle = None
+        self.handle = sk_sketch_create(self.query, self.m, self.d, self.seed, counters.data_ptr(), nbytes,
+                                       self._stream())
+
+    def _stream(self) -> int:
+        return self._torch.cuda.current_stream(self.counters.device).cuda_stream
+
+    def update(self, relation: int, cols, weights=None, domain: Optional[Sequence[int]] = None) -> None:
+        """cols: int64 [a][n] CUDA tensor (attribute-major; the row stride is cols.stride(0));
+        weights: int64 [n] or None (unit weights)."""
+        t = self._torch
+        assert cols.dtype == t.int64 and cols.is_cuda and cols.dim() == 2 and cols.stride(1) == 1
+        n = int(cols.shape[1])
+        wp = None
+        if weights is not None:
+            assert weights.dtype == t.int64 and weights.is_cuda and weights.is_contiguous()
+            wp = weights.data_ptr()
+        sk_sketch_update_batch(self.handle, relation, n, cols.data_ptr(), int(cols.stride(0)) if n else 0, wp,
+                               domain, self._stream())
+
+    def merge(self, other: "SketchSet") -> None:
+        sk_sketch_merge(self.handle, other.handle, self._stream())
+
+    def estimate(self) -> dict:
+        e = sk_estimate_join(self.handle, self._stream())
+        rows = [e.row[i].value() for i in range(e.d)]
+        return {"median": e.median.value(), "rows": rows, "fits_i64": bool(e.fits_i64), "median_i64": e.median_i64,
+                "median_f64": e.median_f64, "mid_mean_f64": e.mid_mean_f64, "max_residual": e.max_residual,
+                "max_limbs": e.max_limbs, "limb_bits": e.limb_bits, "corr_steps": e.corr_steps,
+                "retries": e.retries}
+
+    def sync(self) -> None:
+        sk_sync(self.handle, self._stream())
+
+    def reset(self) -> None:
+        sk_sketch_reset(self.handle, self._stream())
+
+    def coefficients(self) -> List[List[int]]:
+        return sk_get_coefficients(self.handle)
+
+    def set_coefficients(self, coeffs) -> None:
+        sk_set_coefficients(self.handle, coeffs, self._stream())
+
+    def close(self) -> None:
+        if self.handle is not None:
+            sk_sketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,760 @@
+// Estimator (Algorithm 3, Eq. 5) and median over rows (Section 3.3).
+//
+// The host has unrolled Algorithm 3 into a schedule over vector slots (see
+// build_plan); every slot holds d rows of m signed 256-bit integers, so every
+// intermediate of the algorithm is kept exactly.  The steps:
+//   LEAF  slot <- relation sketch (int64 counters, sign-extended)
+//   HAD   x <- y o x                   Hadamard product, exact (overflow checked)
+//   CORR  x <- a (star) x              circular cross-correlation, Definition 3.1,
+//                                      via IFFT(conj(FFT(a)) o FFT(x))
+//   SUM   per-row sum, then the lower median of the d row values
+//
+// CORR splits both operands into L signed B-bit limbs (v = sum_l v_l 2^(B l),
+// v_l in [-2^(B-1), 2^(B-1))), runs FP64 FFTs on the limbs (two real limbs
+// packed per complex transform), forms for every limb-sum s the spectrum
+// sum_{l + l' = s} conj(A_l) X_l', inverts it, rounds every output to the
+// nearest integer and recombines z = sum_s 2^(B s) round(y_s) exactly.  B is
+// picked from a worst-case rounding-error model so the FFT error stays far below
+// 1/2; each step is then certified a posteriori: the largest distance of an
+// output to its nearest integer must be <= 1/4 and, per row, the exact identity
+// sum_j z_j = (sum_j a_j)(sum_j x_j) must hold.  A failed certificate redoes
+// the step with narrower limbs.
+//
+// FFTs: radix-2 decimation-in-time in shared memory; widths up to 2^12 in one
+// pass, wider ones (up to 2^22) as a four-step transform m = R x C (column FFTs
+// with the twiddle W_m^(n2 k1) fused, then row FFTs).  Twiddles come from
+// sincospi.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sk_internal.h"
+
+namespace sk {
+namespace {
+
+// ---------------------------------------------------------------------------
+// signed 256-bit integers (two's complement, little-endian words)
+// ---------------------------------------------------------------------------
+struct I256 {
+  uint64_t w[4];
+};
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ I256 i256_from_i64(int64_t v) {
+  const uint64_t f = v < 0 ? ~0ull : 0ull;
+  return I256{{(uint64_t)v, f, f, f}};
+}
+
+__host__ __device__ __forceinline__ I256 i256_add(const I256& a, const I256& b) {
+  I256 r;
+  uint64_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint64_t s = a.w[k] + b.w[k];
+    const uint64_t c1 = s < a.w[k];
+    const uint64_t t = s + c;
+    const uint64_t c2 = t < s;
+    r.w[k] = t;
+    c = c1 | c2;
+  }
+  return r;
+}
+
+__host__ __device__ __forceinline__ I256 i256_neg(const I256& a) {
+  I256 r;
+  uint64_t c = 1;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint64_t t = ~a.w[k] + c;
+    c = (c && t == 0) ? 1 : 0;
+    r.w[k] = t;
+  }
+  return r;
+}
+
+__host__ __device__ __forceinline__ bool i256_neg_p(const I256& a) { return (int64_t)a.w[3] < 0; }
+
+__host__ __device__ __forceinline__ bool i256_eq(const I256& a, const I256& b) {
+  return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2] && a.w[3] == b.w[3];
+}
+
+// a < b (signed)
+__host__ __device__ __forceinline__ bool i256_lt(const I256& a, const I256& b) {
+  if (a.w[3] != b.w[3]) return (int64_t)a.w[3] < (int64_t)b.w[3];
+  for (int k = 2; k >= 0; k--)
+    if (a.w[k] != b.w[k]) return a.w[k] < b.w[k];
+  return false;
+}
+
+// bit length of |a| (0 for a = 0)
+__host__ __device__ __forceinline__ int i256_bits(const I256& a) {
+  const I256 m = i256_neg_p(a) ? i256_neg(a) : a;
+  for (int k = 3; k >= 0; k--) {
+    if (m.w[k]) {
+#ifdef __CUDA_ARCH__
+      return 64 * k + 64 - __clzll((long long)m.w[k]);
+#else
+      return 64 * k + 64 - __builtin_clzll(m.w[k]);
+#endif
+    }
+  }
+  return 0;
+}
+
+// low 256 bits of a * b: the exact product whenever it fits
+__host__ __device__ __forceinline__ I256 i256_mul(const I256& a, const I256& b) {
+  uint64_t r[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = 0; i + j < 4; j++) {
+      const uint64_t lo = a.w[i] * b.w[j];
+      const uint64_t hi = mulhi64(a.w[i], b.w[j]);
+      uint64_t s = r[i + j] + lo;
+      uint64_t c = s < lo;
+      const uint64_t s2 = s + carry;
+      c += s2 < s;
+      r[i + j] = s2;
+      carry = hi + c;
+    }
+  }
+  return I256{{r[0], r[1], r[2], r[3]}};
+}
+
+// (int64) v << sh, sign-extended, modulo 2^256; 0 <= sh < 256
+__device__ __forceinline__ I256 i256_shl_i64(int64_t v, int sh) {
+  const I256 x = i256_from_i64(v);
+  const int q = sh >> 6, b = sh & 63;
+  I256 r{{0, 0, 0, 0}};
+#pragma unroll
+  for (int k = 3; k >= 0; k--) {
+    const int src = k - q;
+    uint64_t val = 0;
+    if (src >= 0) {
+      val = x.w[src] << b;
+      if (b && src - 1 >= 0) val |= x.w[src - 1] >> (64 - b);
+    }
+    r.w[k] = val;
+  }
+  return r;
+}
+
+// arithmetic shift right by 0 < b < 64
+__device__ __forceinline__ I256 i256_sar(const I256& a, int b) {
+  I256 r;
+#pragma unroll
+  for (int k = 0; k < 3; k++) r.w[k] = (a.w[k] >> b) | (a.w[k + 1] << (64 - b));
+  r.w[3] = (uint64_t)((int64_t)a.w[3] >> b);
+  return r;
+}
+
+__device__ __forceinline__ void record(int* status, int code) { atomicCAS(status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+__global__ void k_leaf(I256* __restrict__ dst, const int64_t* __restrict__ src, int64_t n) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
+    dst[i] = i256_from_i64(src[i]);
+}
+
+__global__ void k_hadamard(I256* __restrict__ x, const I256* __restrict__ y, int64_t n, int* status) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    const I256 a = x[i], b = y[i];
+    if (i256_bits(a) + i256_bits(b) > 255) record(status, SK_ERR_OVERFLOW);
+    x[i] = i256_mul(a, b);
+  }
+}
+
+__global__ void k_maxbits(const I256* __restrict__ v, int64_t n, int* out) {
+  int best = 0;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
+    best = max(best, i256_bits(v[i]));
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
+}
+
+// per-row exact sums: one block per row
+__global__ void k_rowsum(const I256* __restrict__ v, int64_t m, I256* out) {
+  __shared__ I256 part[32];
+  const I256* row = v + (int64_t)blockIdx.x * m;
+  I256 acc{{0, 0, 0, 0}};
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) acc = i256_add(acc, row[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    I256 t;
+#pragma unroll
+    for (int k = 0; k < 4; k++) t.w[k] = __shfl_xor_sync(0xffffffffu, acc.w[k], o);
+    acc = i256_add(acc, t);
+  }
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    I256 s{{0, 0, 0, 0}};
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s = i256_add(s, part[w]);
+    out[blockIdx.x] = s;
+  }
+}
+
+// sorted copy of the d row estimates (the lower median is sorted[(d-1)/2])
+__global__ void k_sort_rows(const I256* __restrict__ rows, int d, I256* sorted) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < d; i++) {
+    const I256 v = rows[i];
+    int j = i - 1;
+    while (j >= 0 && i256_lt(v, sorted[j])) {
+      sorted[j + 1] = sorted[j];
+      j--;
+    }
+    sorted[j + 1] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FFT
+// ---------------------------------------------------------------------------
+__global__ void k_twiddle(double2* tw, int64_t n) {
+  const int64_t half = n >> 1;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += step) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    tw[t] = make_double2(c, -s);   // W_n^t = exp(-2 pi i t / n)
+  }
+}
+
+// W_n^e for 0 <= e < n from the half table
+__device__ __forceinline__ double2 twid(const double2* __restrict__ tw, int64_t e, int64_t half, bool inv) {
+  double2 w;
+  if (e < half) {
+    w = tw[e];
+  } else {
+    w = tw[e - half];
+    w.x = -w.x;
+    w.y = -w.y;
+  }
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In-place radix-2 DIT FFTs of `cnt` vectors of length 2^logL stored back to back in
+// shared memory, input already in bit-reversed order.  tw is the half table of
+// W_N^t; a length-L transform uses W_L^e = W_N^(e * N / L), twstride = N / L.
+__device__ void smem_fft(double2* s, int cnt, int logL, const double2* __restrict__ tw, int64_t twstride,
+                         bool inv) {
+  const int L = 1 << logL;
+  const int halfL = L >> 1;
+  const int total = cnt * halfL;
+  for (int st = 0; st < logL; st++) {
+    const int h = 1 << st;
+    const int64_t tstep = (int64_t)(L >> (st + 1)) * twstride;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      const int v = b >> (logL - 1);
+      const int jj = b & (halfL - 1);
+      const int grp = jj >> st, pos = jj & (h - 1);
+      const int i0 = v * L + grp * 2 * h + pos;
+      const int i1 = i0 + h;
+      double2 w = tw[(int64_t)pos * tstep];
+      if (inv) w.y = -w.y;
+      const double2 a = s[i0];
+      const double2 t = cmul(s[i1], w);
+      s[i0] = make_double2(a.x + t.x, a.y + t.y);
+      s[i1] = make_double2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int i, int bits) { return (int)(__brev((unsigned)i) >> (32 - bits)); }
+
+// whole transforms of length L = 2^logL <= 4096, vpc vectors per block
+__global__ void k_fft_small(const double2* __restrict__ in, double2* __restrict__ out, int64_t batch, int logL,
+                            int vpc, const double2* __restrict__ tw, int64_t twstride, bool inv) {
+  extern __shared__ double2 sm[];
+  const int L = 1 << logL;
+  const int64_t v0 = (int64_t)blockIdx.x * vpc;
+  const int64_t rem = batch - v0;
+  const int cnt = (int)(rem < (int64_t)vpc ? rem : (int64_t)vpc);
+  for (int idx = threadIdx.x; idx < cnt * L; idx += blockDim.x) {
+    const int v = idx >> logL, i = idx & (L - 1);
+    sm[v * L + bitrev(i, logL)] = in[(v0 + v) * L + i];
+  }
+  __syncthreads();
+  smem_fft(sm, cnt, logL, tw, twstride, inv);
+  for (int idx = threadIdx.x; idx < cnt * L; idx += blockDim.x) out[(v0 * L) + idx] = sm[idx];
+}
+
+// four-step, pass 1: length-R transforms down the columns of the R x C view
+// (element n1 * C + n2), then the twiddle W_N^(n2 k1); in place.
+__global__ void k_fft_cols(double2* __restrict__ buf, int logR, int logC, int cb, const double2* __restrict__ tw,
+                           bool inv) {
+  extern __shared__ double2 sm[];
+  const int R = 1 << logR, C = 1 << logC;
+  const int64_t N = (int64_t)R * C;
+  const int blocks_per_vec = C / cb;
+  const int64_t vec = blockIdx.x / blocks_per_vec;
+  const int c0 = (blockIdx.x % blocks_per_vec) * cb;
+  double2* v = buf + vec * N;
+  for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
+    const int c = idx % cb, n1 = idx / cb;
+    sm[c * R + bitrev(n1, logR)] = v[(int64_t)n1 * C + c0 + c];
+  }
+  __syncthreads();
+  smem_fft(sm, cb, logR, tw, C, inv);
+  const int64_t half = N >> 1;
+  for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
+    const int c = idx % cb, k1 = idx / cb;
+    const int64_t n2 = c0 + c;
+    const double2 w = twid(tw, (n2 * k1) & (N - 1), half, inv);
+    v[(int64_t)k1 * C + n2] = cmul(sm[c * R + k1], w);
+  }
+}
+
+// four-step, pass 2: length-C transforms along the rows k1, written to the
+// natural-order output X[k1 + R k2]; out of place.
+__global__ void k_fft_rows(const double2* __restrict__ in, double2* __restrict__ out, int logR, int logC, int rb,
+                           const double2* __restrict__ tw, bool inv) {
+  extern __shared__ double2 sm[];
+  const int R = 1 << logR, C = 1 << logC;
+  const int64_t N = (int64_t)R * C;
+  const int blocks_per_vec = R / rb;
+  const int64_t vec = blockIdx.x / blocks_per_vec;
+  const int r0 = (blockIdx.x % blocks_per_vec) * rb;
+  const double2* vi = in + vec * N;
+  double2* vo = out + vec * N;
+  for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
+    const int rr = idx / C, n2 = idx % C;
+    sm[rr * C + bitrev(n2, logC)] = vi[(int64_t)(r0 + rr) * C + n2];
+  }
+  __syncthreads();
+  smem_fft(sm, rb, logC, tw, R, inv);
+  for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
+    const int rr = idx % rb, k2 = idx / rb;
+    vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[rr * C + k2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// limb split, spectral products, recombination
+// ---------------------------------------------------------------------------
+struct CorrArgs {
+  const I256* a;     // [d][m]
+  const I256* x;     // [d][m]
+  I256* z;           // [d][m] output
+  double2* F;        // packed forward buffer [d][nf][m]
+  double2* G;        // packed inverse buffer [d][ni][m]
+  int64_t m;
+  int logm;
+  int d;
+  int B;             // limb bits
+  int La, Lx;        // limbs of a and x
+  int nf, ni;
+  int* status;
+  unsigned long long* residual;   // max |y - rint(y)| as double bits
+};
+
+// Real vector number q of the forward batch: q < La -> limb q of a, else limb q-La of x.
+// Packed complex vector t holds real vectors 2t (real part) and 2t+1 (imaginary part).
+__global__ void k_split(CorrArgs p) {
+  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t half = 1ll << (p.B - 1), full = 1ll << p.B;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.m, j = g % p.m;
+    double2* F = p.F + (row * p.nf) * p.m + j;
+    for (int which = 0; which < 2; which++) {
+      I256 v = which == 0 ? p.a[g] : p.x[g];
+      const int L = which == 0 ? p.La : p.Lx;
+      const int base = which == 0 ? 0 : p.La;
+      for (int l = 0; l < L; l++) {
+        int64_t dig = (int64_t)(v.w[0] & (uint64_t)(full - 1));
+        if (dig >= half) dig -= full;
+        v = i256_add(v, i256_from_i64(-dig));
+        v = i256_sar(v, p.B);
+        const int q = base + l;
+        double* slot = (double*)(F + (int64_t)(q >> 1) * p.m) + (q & 1);
+        *slot = (double)dig;
+      }
+      if (v.w[0] | v.w[1] | v.w[2] | v.w[3]) record(p.status, SK_ERR_OVERFLOW);
+    }
+    const int nreal = p.La + p.Lx;
+    if (nreal & 1) ((double*)(F + (int64_t)(nreal >> 1) * p.m))[1] = 0.0;
+  }
+}
+
+__global__ void k_product(CorrArgs p) {
+  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.m, k = g % p.m;
+    const int64_t mk = (p.m - k) & (p.m - 1);
+    const double2* F = p.F + (row * p.nf) * p.m;
+    double2 A[kMaxLimbs], X[kMaxLimbs];
+    const int nreal = p.La + p.Lx;
+    for (int q = 0; q < nreal; q++) {
+      const int t = q >> 1;
+      const double2 zk = F[(int64_t)t * p.m + k];
+      const double2 zm = F[(int64_t)t * p.m + mk];
+      // Z = FFT(u + i v): U[k] = (Z[k] + conj Z[-k]) / 2, V[k] = (Z[k] - conj Z[-k]) / (2i)
+      double2 s;
+      if ((q & 1) == 0) {
+        s = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
+      } else {
+        const double dr = zk.x - zm.x, di = zk.y + zm.y;
+        s = make_double2(0.5 * di, -0.5 * dr);
+      }
+      if (q < p.La) A[q] = s; else X[q - p.La] = s;
+    }
+    double2* G = p.G + (row * p.ni) * p.m + k;
+    const int ns = p.La + p.Lx - 1;
+    for (int t = 0; t < p.ni; t++) {
+      double2 P[2];
+      for (int h = 0; h < 2; h++) {
+        const int s = 2 * t + h;
+        double re = 0.0, im = 0.0;
+        if (s < ns) {
+          const int l0 = max(0, s - (p.Lx - 1)), l1 = min(s, p.La - 1);
+          for (int l = l0; l <= l1; l++) {
+            const double2 a = A[l], x = X[s - l];
+            // conj(a) * x
+            re += a.x * x.x + a.y * x.y;
+            im += a.x * x.y - a.y * x.x;
+          }
+        }
+        P[h] = make_double2(re, im);
+      }
+      // pack the two real-output spectra: IFFT(P0 + i P1) = y0 + i y1
+      G[(int64_t)t * p.m] = make_double2(P[0].x - P[1].y, P[0].y + P[1].x);
+    }
+  }
+}
+
+__global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
+  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const double inv_m = 1.0 / (double)p.m;
+  const int ns = p.La + p.Lx - 1;
+  double worst = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.m, j = g % p.m;
+    const double2* y = Y + (row * p.ni) * p.m + j;
+    I256 z{{0, 0, 0, 0}};
+    for (int s = 0; s < ns; s++) {
+      const double2 c = y[(int64_t)(s >> 1) * p.m];
+      const double v = ((s & 1) ? c.y : c.x) * inv_m;
+      const double rv = rint(v);
+      worst = fmax(worst, fabs(v - rv));
+      if (fabs(rv) >= 4503599627370496.0) record(p.status, SK_ERR_INEXACT);   // 2^52
+      z = i256_add(z, i256_shl_i64((int64_t)rv, p.B * s));
+    }
+    p.z[g] = z;
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(p.residual, (unsigned long long)__double_as_longlong(worst));
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+int grid_for(int64_t n, int threads = 256) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((1ll << r) < v) r++;
+  return r;
+}
+
+// Largest limb width B such that, with every limb at its largest magnitude 2^(B-1),
+// the modelled FFT rounding error 3 eps log2(m) npairs m 2^(2B-2) stays below 1/8
+// and each rounded output npairs m 2^(2B-2) stays below 2^51.
+int limb_bits_for(int64_t m, int npairs) {
+  const double logm = std::log2((double)m);
+  for (int B = 24; B >= 2; B--) {
+    const double mag = (double)npairs * (double)m * std::ldexp(1.0, 2 * B - 2);
+    const double err = 3.0 * std::ldexp(1.0, -53) * logm * mag;
+    if (err <= 0.125 && mag < std::ldexp(1.0, 51)) return B;
+  }
+  return 2;
+}
+
+cudaError_t ensure(Scratch& s, size_t bytes) {
+  if (s.bytes >= bytes) return cudaSuccess;
+  if (s.ptr) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(s.ptr);
+    s.ptr = nullptr;
+    s.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&s.ptr, bytes);
+  if (e == cudaSuccess) s.bytes = bytes;
+  return e;
+}
+
+#define SK_CK(x)                                        \
+  do {                                                  \
+    cudaError_t _e = (x);                               \
+    if (_e != cudaSuccess) return set_status_from_cuda(_e); \
+  } while (0)
+
+// Forward (inv = false) or inverse (unnormalised) FFT of `batch` vectors of
+// length m held in src; the result is written to dst, src is clobbered.
+sk_status fft(double2* src, double2* dst, int64_t batch, int64_t m, const double2* tw, bool inv, cudaStream_t st) {
+  const int logm = ilog2(m);
+  if (logm <= 12) {
+    const int L = (int)m;
+    const int vpc = (int)std::max<int64_t>(1, std::min<int64_t>(4096 / L, batch));
+    const int64_t grid = (batch + vpc - 1) / vpc;
+    const size_t smem = (size_t)vpc * L * sizeof(double2);
+    SK_CK(cudaFuncSetAttribute(k_fft_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fft_small<<<(unsigned)grid, 256, smem, st>>>(src, dst, batch, logm, vpc, tw, 1, inv);
+    count_launch();
+    return set_status_from_cuda(cudaGetLastError());
+  }
+  const int logR = logm / 2, logC = logm - logR;
+  const int R = 1 << logR, C = 1 << logC;
+  const int budget = R >= 1024 ? (128 << 10) : (64 << 10);
+  int cb = std::max(1, std::min(C, budget / (R * (int)sizeof(double2))));
+  int rb = std::max(1, std::min(R, budget / (C * (int)sizeof(double2))));
+  const size_t smc = (size_t)cb * R * sizeof(double2), smr = (size_t)rb * C * sizeof(double2);
+  SK_CK(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  SK_CK(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  k_fft_cols<<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  k_fft_rows<<<(unsigned)(batch * (R / rb)), 512, smr, st>>>(src, dst, logR, logC, rb, tw, inv);
+  count_launch();
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+struct HostI256 {
+  static I256 mul(const I256& a, const I256& b) { return i256_mul(a, b); }
+};
+
+}  // namespace
+
+void free_estimator(sk_set* s) {
+  if (s->scratch.ptr) cudaFree(s->scratch.ptr);
+  if (s->fft_scratch.ptr) cudaFree(s->fft_scratch.ptr);
+  if (s->d_twiddle) cudaFree(s->d_twiddle);
+  s->scratch = Scratch();
+  s->fft_scratch = Scratch();
+  s->d_twiddle = nullptr;
+  s->twiddle_m = 0;
+}
+
+sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
+  const int64_t m = s->m;
+  const int d = s->d;
+  const int64_t dm = (int64_t)d * m;
+  const int logm = ilog2(m);
+  // slots (+1 spare for correlation outputs) and small buffers
+  const int nslots = s->n_slots + 1;
+  const size_t slot_bytes = (size_t)dm * sizeof(I256);
+  const size_t small_off = slot_bytes * nslots;
+  const size_t small_bytes = 4 * SK_MAX_ROWS * sizeof(I256) + 64;
+  SK_CK(ensure(s->scratch, small_off + small_bytes));
+  if (s->twiddle_m != m) {
+    if (s->d_twiddle) cudaFree(s->d_twiddle);
+    s->d_twiddle = nullptr;
+    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(m / 2) * sizeof(double2)));
+    s->twiddle_m = m;
+    k_twiddle<<<grid_for(m / 2), 256, 0, st>>>((double2*)s->d_twiddle, m);
+    count_launch();
+    SK_CK(cudaGetLastError());
+  }
+  const double2* tw = (const double2*)s->d_twiddle;
+  char* base = (char*)s->scratch.ptr;
+  std::vector<int> phys(nslots);
+  for (int i = 0; i < nslots; i++) phys[i] = i;
+  auto slot = [&](int i) { return (I256*)(base + slot_bytes * phys[i]); };
+  const int spare = nslots - 1;
+  I256* d_sa = (I256*)(base + small_off);
+  I256* d_sx = d_sa + SK_MAX_ROWS;
+  I256* d_sz = d_sx + SK_MAX_ROWS;
+  I256* d_sorted = d_sz + SK_MAX_ROWS;
+  int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);
+  unsigned long long* d_resid = (unsigned long long*)(d_bits + 4);
+
+  double max_resid = 0.0;
+  int max_limbs = 0, last_B = 0, retries = 0;
+  const int eg = grid_for(dm);
+
+  for (const EstOp& op : s->plan) {
+    if (op.kind == OP_LEAF) {
+      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    } else if (op.kind == OP_HAD) {
+      k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    } else if (op.kind == OP_CORR) {
+      I256* x = slot(op.dst);
+      I256* a = slot(op.src);
+      SK_CK(cudaMemsetAsync(d_bits, 0, 2 * sizeof(int), st));
+      k_maxbits<<<eg, 256, 0, st>>>(a, dm, d_bits);
+      count_launch();
+      k_maxbits<<<eg, 256, 0, st>>>(x, dm, d_bits + 1);
+      count_launch();
+      k_rowsum<<<d, 256, 0, st>>>(a, m, d_sa);
+      count_launch();
+      k_rowsum<<<d, 256, 0, st>>>(x, m, d_sx);
+      count_launch();
+      SK_CK(cudaGetLastError());
+      int hb[2];
+      SK_CK(cudaMemcpyAsync(hb, d_bits, sizeof(hb), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaStreamSynchronize(st));
+      if (hb[0] == 0 || hb[1] == 0) {
+        SK_CK(cudaMemsetAsync(x, 0, slot_bytes, st));
+        continue;
+      }
+      if (hb[0] + hb[1] + logm + 1 > 255) return SK_ERR_OVERFLOW;
+      std::vector<I256> sa(d), sx(d), sz(d);
+      SK_CK(cudaMemcpyAsync(sa.data(), d_sa, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaMemcpyAsync(sx.data(), d_sx, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      int B = limb_bits_for(m, 1);
+      bool done = false;
+      for (int attempt = 0; attempt < 4 && !done; attempt++) {
+        int La = 0, Lx = 0;
+        for (;;) {
+          La = (hb[0] + 2 + B - 1) / B;
+          Lx = (hb[1] + 2 + B - 1) / B;
+          const int nb = limb_bits_for(m, std::min(La, Lx));
+          if (nb >= B) break;
+          B = nb;
+        }
+        if (attempt > 0) {
+          B = std::max(2, B - 3 * attempt);
+          La = (hb[0] + 2 + B - 1) / B;
+          Lx = (hb[1] + 2 + B - 1) / B;
+        }
+        if (La > kMaxLimbs || Lx > kMaxLimbs) return SK_ERR_INEXACT;
+        CorrArgs p;
+        p.a = a;
+        p.x = x;
+        p.z = slot(spare);
+        p.m = m;
+        p.logm = logm;
+        p.d = d;
+        p.B = B;
+        p.La = La;
+        p.Lx = Lx;
+        p.nf = (La + Lx + 1) / 2;
+        p.ni = (La + Lx) / 2;
+        p.status = s->d_status;
+        p.residual = d_resid;
+        const size_t fbytes = (size_t)d * p.nf * m * sizeof(double2);
+        SK_CK(ensure(s->fft_scratch, 2 * fbytes));
+        double2* bufA = (double2*)s->fft_scratch.ptr;
+        double2* bufB = bufA + (size_t)d * p.nf * m;
+        p.F = bufA;
+        SK_CK(cudaMemsetAsync(d_resid, 0, sizeof(unsigned long long), st));
+        k_split<<<eg, 256, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, m, tw, false, st);
+        if (fs != SK_OK) return fs;
+        p.F = bufB;
+        p.G = bufA;
+        k_product<<<eg, 128, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        fs = fft(bufA, bufB, (int64_t)d * p.ni, m, tw, true, st);
+        if (fs != SK_OK) return fs;
+        k_recombine<<<eg, 256, 0, st>>>(p, bufB);
+        count_launch();
+        k_rowsum<<<d, 256, 0, st>>>(p.z, m, d_sz);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        unsigned long long rbits = 0;
+        SK_CK(cudaMemcpyAsync(&rbits, d_resid, sizeof(rbits), cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaMemcpyAsync(sz.data(), d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaStreamSynchronize(st));
+        double resid;
+        std::memcpy(&resid, &rbits, sizeof(resid));
+        bool ok = resid <= 0.25;
+        for (int r = 0; r < d && ok; r++) ok = i256_eq(sz[r], HostI256::mul(sa[r], sx[r]));
+        max_resid = std::max(max_resid, resid);
+        max_limbs = std::max(max_limbs, std::max(La, Lx));
+        last_B = B;
+        if (ok) {
+          std::swap(phys[op.dst], phys[spare]);
+          done = true;
+        } else {
+          retries++;
+        }
+      }
+      if (!done) return SK_ERR_INEXACT;
+    } else {  // OP_SUM
+      k_rowsum<<<d, 256, 0, st>>>(slot(op.dst), m, d_sz);
+      count_launch();
+      k_sort_rows<<<1, 32, 0, st>>>(d_sz, d, d_sorted);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    }
+  }
+  std::vector<I256> rows(d), sorted(d);
+  int status = 0;
+  SK_CK(cudaMemcpyAsync(rows.data(), d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(sorted.data(), d_sorted, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  if (status != 0) {
+    SK_CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
+    SK_CK(cudaStreamSynchronize(st));
+    return (sk_status)status;
+  }
+  auto to_double = [](const I256& v) {
+    const bool neg = i256_neg_p(v);
+    const I256 a = neg ? i256_neg(v) : v;
+    double r = 0.0;
+    for (int k = 3; k >= 0; k--) r = r * 18446744073709551616.0 + (double)a.w[k];
+    return neg ? -r : r;
+  };
+  out->d = d;
+  for (int r = 0; r < d; r++) std::memcpy(&out->row[r], &rows[r], sizeof(sk_i256));
+  const I256 med = sorted[(d - 1) / 2];
+  std::memcpy(&out->median, &med, sizeof(sk_i256));
+  const bool fits = (med.w[1] == med.w[2] && med.w[2] == med.w[3] &&
+                     (med.w[3] == 0 ? (int64_t)med.w[0] >= 0 : (med.w[3] == ~0ull && (int64_t)med.w[0] < 0)));
+  out->fits_i64 = fits ? 1 : 0;
+  out->median_i64 = fits ? (int64_t)med.w[0] : 0;
+  out->median_f64 = to_double(med);
+  out->mid_mean_f64 = (d & 1) ? to_double(sorted[d / 2])
+                              : 0.5 * (to_double(sorted[d / 2 - 1]) + to_double(sorted[d / 2]));
+  out->max_residual = max_resid;
+  out->max_limbs = max_limbs;
+  out->limb_bits = last_B;
+  out->corr_steps = s->corr_steps;
+  out->retries = retries;
+  return SK_OK;
+}
+
+}  // namespace sk

@@ -1,0 +1,87 @@
+// Internal declarations shared by the translation units of libsketch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sketch.h"
+
+namespace sk {
+
+constexpr uint64_t kP61 = (1ull << 61) - 1;   // the Mersenne prime 2^61 - 1
+constexpr int kMaxAttrs = 16;                  // joined attributes per relation handled by the update kernel
+constexpr int kMaxDegree = 16;                 // joins per attribute
+constexpr int kMaxLimbs = 40;                  // limbs per correlation operand
+
+// Update-kernel description of one relation: for every row, for each attribute u in
+// column order, (b0, b1) of u's component bin function followed by (s0..s3) of each
+// join incident to u.  coef_row_len = sum_u (2 + 4 deg(u)).
+struct RelPlan {
+  int a = 0;                        // |Omega(R_k)|
+  int deg[kMaxAttrs] = {0};         // |Gamma(u)| per attribute
+  int coef_row_len = 0;
+  uint64_t* d_coef = nullptr;       // device [d][coef_row_len]
+};
+
+enum OpKind { OP_LEAF = 0, OP_HAD = 1, OP_CORR = 2, OP_SUM = 3 };
+
+// One step of Algorithm 3, unrolled on the host into a fixed schedule over
+// vector slots (each slot holds d rows of m signed 256-bit integers).
+struct EstOp {
+  OpKind kind;
+  int dst;   // slot written (LEAF, HAD: dst = dst o src, CORR: dst = src (star) dst, SUM: slot summed)
+  int src;   // slot read
+  int rel;   // LEAF: relation
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sk
+
+struct sk_set {
+  int r = 0;
+  int64_t m = 0;
+  int d = 0;
+  uint64_t seed = 0;
+  int device = 0;
+  std::vector<int> num_join_attrs, offsets, rel_of, comp_of;
+  std::vector<std::pair<int, int>> edges;     // canonical joins {u, v}, u < v, sorted
+  std::vector<std::vector<int>> gamma, incident;
+  int n_comp = 0;
+  int coef_row_len = 0;                        // 2 * n_comp + 4 * n_edges
+  std::vector<uint64_t> h_coef;                // [d][coef_row_len]
+  std::vector<sk::RelPlan> rel;                // per relation
+  int64_t* counters = nullptr;                 // caller-owned int64 [r][d][m]
+  size_t counter_bytes = 0;
+  int* d_status = nullptr;                     // first device-side error, 0 = none
+  std::vector<sk::EstOp> plan;                 // Algorithm 3 schedule
+  int n_slots = 0;
+  int corr_steps = 0;
+  sk::Scratch scratch;                         // estimator slots and small buffers
+  sk::Scratch fft_scratch;                     // estimator FFT buffers (grown on demand)
+  double* d_twiddle = nullptr;                 // FFT twiddles for width m
+  int64_t twiddle_m = 0;
+};
+
+namespace sk {
+
+// sk_update.cu
+sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols, int64_t col_stride,
+                        const int64_t* weights, const int64_t* domain, cudaStream_t st);
+sk_status launch_merge(int64_t* dst, const int64_t* src, int64_t count, cudaStream_t st);
+
+// sk_estimate.cu
+sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st);
+void free_estimator(sk_set* s);
+
+// sk_api.cu
+sk_status set_status_from_cuda(cudaError_t e);
+void count_launch(int n = 1);   // adds to the process-wide kernel-launch counter
+
+}  // namespace sk

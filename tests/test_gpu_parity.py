@@ -1,0 +1,211 @@
+"""GPU <-> oracle parity through the C ABI: sketches bit-exact, estimates exact.
+
+Every test builds the same seeded inputs for both sides; the oracle draws its
+own hash coefficients from the same seed (it never reads the library's)."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2402_15953_gb300 as pkg
+import synth
+from tests._helpers import random_relations, random_tree_query
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+    assert torch.cuda.is_available()
+
+
+def _gpu_sketch(attrs, edges, m, d, seed, rels, domain=None):
+    s = pkg.SketchSet(attrs, edges, m, d, seed)
+    for k, (cols, w) in enumerate(rels):
+        c = torch.as_tensor(np.ascontiguousarray(cols)).cuda()
+        wt = None if w is None else torch.as_tensor(np.ascontiguousarray(w)).cuda()
+        s.update(k, c, wt, domain=None if domain is None else domain[k])
+    s.sync()
+    torch.cuda.synchronize()
+    return s
+
+
+def _oracle(attrs, edges, m, d, seed, rels):
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(seed, d, q.n_comp, len(q.edges))
+    return q, co, O.sketch_all(q, co, rels, m)
+
+
+def test_coefficients_match_oracle_draw():
+    attrs, edges = [1, 2, 1, 1], [(0, 0, 1, 0), (2, 0, 1, 0), (3, 0, 1, 1)]
+    s = pkg.SketchSet(attrs, edges, 16, 3, 12345)
+    q = O.canonical_query(attrs, edges)
+    assert np.array_equal(np.array(s.coefficients(), dtype=np.uint64),
+                          O.draw_coefficients(12345, 3, q.n_comp, len(q.edges)))
+    s.close()
+
+
+@pytest.mark.parametrize("m", [1, 5, 13, 64, 256, 1000, 4096, 1 << 16])
+def test_update_bit_exact_random_queries(m):
+    rng = random.Random(m)
+    for trial in range(4):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 5))
+        rels = random_relations(rng, attrs, 3000, 1 << rng.choice([4, 10, 40]), signed=trial % 2 == 0)
+        d = rng.choice([1, 3, 7])
+        seed = rng.randrange(1 << 62)
+        s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        _, _, sk = _oracle(attrs, edges, m, d, seed, rels)
+        got = s.counters.cpu().numpy()
+        for k in range(len(attrs)):
+            assert np.array_equal(got[k], sk[k]), (m, trial, k)
+        s.close()
+
+
+def test_update_extreme_keys_and_weights():
+    """Keys at the field's edges (0, p - 1, p, 2^61, 2^63 - 1, negatives) and weights near
+    the int64 limits, wrapping like two's complement."""
+    p = O.P61
+    keys = [0, 1, p - 1, p, p + 1, 1 << 61, (1 << 63) - 1, -1, -(1 << 63), -p, 123456789012345]
+    cols = np.array([keys, keys[::-1]], dtype=np.int64)
+    w = np.array([(1 << 62), -(1 << 62), (1 << 63) - 1, -(1 << 63), 1, -1, 7, 1 << 40, -(1 << 40), 3, 5],
+                 dtype=np.int64)
+    attrs, edges = [2, 1, 1], [(0, 0, 1, 0), (0, 1, 2, 0)]
+    rels = [(cols, w), (cols[:1].copy(), w), (cols[1:].copy(), None)]
+    for m in [7, 256, 1 << 20]:
+        s = _gpu_sketch(attrs, edges, m, 5, 99, rels)
+        _, _, sk = _oracle(attrs, edges, m, 5, 99, rels)
+        got = s.counters.cpu().numpy()
+        for k in range(3):
+            assert np.array_equal(got[k], sk[k])
+        s.close()
+
+
+def test_large_batch_smem_and_global_paths():
+    """The same stream through the shared-memory path (small d*m) and the global-atomic path
+    (large d*m) matches the oracle."""
+    w = synth.chain3(n=200_000, m=512, d=7, seed=3)
+    rels = [(r.cols.numpy(), None) for r in w.relations]
+    for m in [512, 1 << 15]:
+        s = _gpu_sketch(w.num_join_attrs, w.edges, m, 7, 77, rels)
+        _, _, sk = _oracle(w.num_join_attrs, w.edges, m, 7, 77, rels)
+        got = s.counters.cpu().numpy()
+        for k in range(3):
+            assert np.array_equal(got[k], sk[k]), m
+        s.close()
+
+
+def test_chain3_config_exact():
+    """Chain R1(A) - R2(A,B) - R3(B), 10^4 rows each, m = 256, d = 5, seed 42: bit-exact
+    sketches, exact row estimates and median."""
+    w = synth.chain3()
+    rels = [(r.cols.numpy(), None) for r in w.relations]
+    s = _gpu_sketch(w.num_join_attrs, w.edges, w.m, w.d, w.hash_seed, rels)
+    q, co, sk = _oracle(w.num_join_attrs, w.edges, w.m, w.d, w.hash_seed, rels)
+    got = s.counters.cpu().numpy()
+    for k in range(3):
+        assert np.array_equal(got[k], sk[k])
+    est = s.estimate()
+    ref = O.estimate(q, sk)
+    assert est["rows"] == ref.rows
+    assert est["median"] == ref.median and est["fits_i64"] and est["median_i64"] == ref.median
+    assert est["max_residual"] <= 0.25
+    assert est["mid_mean_f64"] == pytest.approx(ref.mid_mean, rel=1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("m", [2, 4, 8, 64, 1024, 1 << 13, 1 << 14])
+def test_estimate_exact_random_queries(m):
+    rng = random.Random(1000 + m)
+    trials = 6 if m <= 1024 else 2
+    for trial in range(trials):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 5))
+        rels = random_relations(rng, attrs, 400 if m <= 1024 else 3000, 1 << rng.choice([3, 12, 30]))
+        d = rng.choice([1, 2, 5])
+        seed = rng.randrange(1 << 62)
+        s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        q, co, sk = _oracle(attrs, edges, m, d, seed, rels)
+        est = s.estimate()
+        ref = O.estimate(q, sk)
+        assert est["rows"] == ref.rows, (m, trial, attrs, edges)
+        assert est["median"] == ref.median
+        s.close()
+
+
+def test_identity_hashing_gives_exact_join_size_on_gpu():
+    """With injective test hashes (bin x * R_q, sign +1) the GPU estimate is the exact join size."""
+    rng = random.Random(7)
+    attrs, edges = [1, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0)]
+    rels = random_relations(rng, attrs, 5000, 30, signed=True)
+    m = 1024
+    s = pkg.SketchSet(attrs, edges, m, 2, 1)
+    q = O.canonical_query(attrs, edges)
+    s.set_coefficients(O.identity_coefficients(q, 2, [30, 30]).tolist())
+    for k, (cols, w) in enumerate(rels):
+        s.update(k, torch.as_tensor(cols).cuda(), torch.as_tensor(w).cuda())
+    est = s.estimate()
+    truth = O.exact_join_size(q, rels)
+    assert est["rows"] == [truth, truth]
+    s.close()
+
+
+def test_merge_equals_single_pass():
+    w = synth.chain3(n=5000, m=128, d=3, seed=5)
+    rels = [(r.cols.numpy(), None) for r in w.relations]
+    full = _gpu_sketch(w.num_join_attrs, w.edges, 128, 3, 8, rels)
+    a = _gpu_sketch(w.num_join_attrs, w.edges, 128, 3, 8, [(c[:, :2000], None) for c, _ in rels])
+    b = _gpu_sketch(w.num_join_attrs, w.edges, 128, 3, 8, [(c[:, 2000:], None) for c, _ in rels])
+    a.merge(b)
+    torch.cuda.synchronize()
+    assert torch.equal(a.counters, full.counters)
+    c = _gpu_sketch(w.num_join_attrs, w.edges, 128, 3, 9, rels)
+    with pytest.raises(pkg.SketchError) as e:
+        a.merge(c)
+    assert e.value.name == "SK_ERR_MISMATCH"
+    for x in (full, a, b, c):
+        x.close()
+
+
+def test_key_out_of_domain_is_reported_and_skipped():
+    attrs, edges = [1, 1], [(0, 0, 1, 0)]
+    cols = np.array([[1, 2, 3, 50, 4]], dtype=np.int64)
+    s = pkg.SketchSet(attrs, edges, 16, 2, 3)
+    s.update(0, torch.as_tensor(cols).cuda(), domain=[10])
+    with pytest.raises(pkg.SketchError) as e:
+        s.sync()
+    assert e.value.name == "SK_ERR_KEY_OUT_OF_DOMAIN"
+    s.sync()  # cleared
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(3, 2, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, np.array([[1, 2, 3, 4]], dtype=np.int64), None, 16)
+    assert np.array_equal(s.counters[0].cpu().numpy(), ref)
+    s.close()
+
+
+def test_invalid_arguments():
+    with pytest.raises(pkg.SketchError) as e:
+        pkg.SketchSet([1, 1], [(0, 0, 0, 0)], 16, 2, 1)
+    assert e.value.name == "SK_ERR_SELF_EDGE"
+    with pytest.raises(pkg.SketchError) as e:
+        pkg.SketchSet([2, 2], [(0, 0, 1, 0), (0, 1, 1, 1)], 16, 2, 1)
+    assert e.value.name == "SK_ERR_CYCLIC_QUERY"
+    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], 12, 2, 1)
+    with pytest.raises(pkg.SketchError) as e:
+        s.estimate()
+    assert e.value.name == "SK_ERR_UNSUPPORTED_WIDTH"
+    with pytest.raises(pkg.SketchError):
+        pkg.sk_sketch_update_batch(s.handle, 5, 10, s.counters.data_ptr(), 10, None, None, 0)
+    s.close()
+
+
+def test_empty_batch_and_empty_relation():
+    attrs, edges = [1, 1], [(0, 0, 1, 0)]
+    s = pkg.SketchSet(attrs, edges, 64, 3, 4)
+    s.update(0, torch.empty((1, 0), dtype=torch.int64, device="cuda"))
+    est = s.estimate()
+    assert est["rows"] == [0, 0, 0] and est["median"] == 0
+    s.close()
