@@ -19,7 +19,7 @@ def lib():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "sketch.h")).read()
-    return sorted(set(re.findall(r"^(?:sk_status|const char\*)\s+(sk_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:sk_status|const char\*|int64_t)\s+(sk_\w+)\s*\(", src, re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):
