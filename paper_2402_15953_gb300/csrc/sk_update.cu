@@ -61,6 +61,25 @@ __device__ __forceinline__ uint64_t addmod(uint64_t a, uint64_t b) {
   return r >= kP61 ? r - kP61 : r;
 }
 
+// Narrow-key arithmetic, used when every key of a tuple lies in [0, 2^32) (then the
+// field element is the key itself).  Values are kept "lazy": congruent mod p and
+// below 2^63, reduced once at the end.  acc * x for acc < 2^63, x < 2^32 is
+// p1 2^32 + p0 with p0 = lo32(acc) x < 2^64 and p1 = hi32(acc) x < 2^63; since
+// 2^61 == 1, p1 2^32 == (p1 >> 29) + ((p1 mod 2^29) << 32) and p0 == (p0 mod 2^61) +
+// (p0 >> 61).  The four terms sum below 2^62 + 2^35, so adding a coefficient
+// (< 2^61) keeps the result below 2^63.
+__device__ __forceinline__ uint64_t mul_narrow(uint64_t acc, uint32_t x) {
+  const uint64_t p0 = (uint64_t)(uint32_t)acc * x;
+  const uint64_t p1 = (uint64_t)(uint32_t)(acc >> 32) * x;
+  return (p1 >> 29) + ((p1 & ((1ull << 29) - 1)) << 32) + (p0 & kP61) + (p0 >> 61);
+}
+
+// v < 2^63 -> v mod p
+__device__ __forceinline__ uint64_t reduce_lazy(uint64_t v) {
+  const uint64_t r = (v & kP61) + (v >> 61);
+  return r >= kP61 ? r - kP61 : r;
+}
+
 __device__ __forceinline__ void record(int* status, int code) { atomicCAS(status, 0, code); }
 
 template <bool POW2>
@@ -99,24 +118,47 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs p) {
     }
     const int64_t delta = p.w ? __ldg(p.w + i) : 1;
     const bool small = SMEM && (delta <= p.smem_wmax && delta >= -p.smem_wmax);
+    bool narrow = true;
+#pragma unroll
+    for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
+      if (A == 0 && u >= na) break;
+      narrow = narrow && (x[u] >> 32) == 0;
+    }
     const uint64_t* cr = s_coef;
     for (int row = 0; row < p.d; row++, cr += p.row_len) {
       uint64_t bin = 0;
       uint32_t sbit = 0;
       int off = 0;
+      if (narrow) {
 #pragma unroll
-      for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
-        if (A == 0 && u >= na) break;
-        const uint64_t xu = x[u];
-        const uint64_t h = addmod(mulmod(cr[off + 1], xu), cr[off]);
-        bin += reduce_m<POW2>(h, p.m);
-        off += 2;
-        for (int e = 0; e < p.deg[u]; e++, off += 4) {
-          uint64_t acc = cr[off + 3];
-          acc = addmod(mulmod(acc, xu), cr[off + 2]);
-          acc = addmod(mulmod(acc, xu), cr[off + 1]);
-          acc = addmod(mulmod(acc, xu), cr[off]);
-          sbit ^= (uint32_t)(acc & 1u);
+        for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
+          if (A == 0 && u >= na) break;
+          const uint32_t xu = (uint32_t)x[u];
+          const uint64_t h = reduce_lazy(mul_narrow(cr[off + 1], xu) + cr[off]);
+          bin += reduce_m<POW2>(h, p.m);
+          off += 2;
+          for (int e = 0; e < p.deg[u]; e++, off += 4) {
+            uint64_t acc = mul_narrow(cr[off + 3], xu) + cr[off + 2];
+            acc = mul_narrow(acc, xu) + cr[off + 1];
+            acc = mul_narrow(acc, xu) + cr[off];
+            sbit ^= (uint32_t)(reduce_lazy(acc) & 1u);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
+          if (A == 0 && u >= na) break;
+          const uint64_t xu = x[u];
+          const uint64_t h = addmod(mulmod(cr[off + 1], xu), cr[off]);
+          bin += reduce_m<POW2>(h, p.m);
+          off += 2;
+          for (int e = 0; e < p.deg[u]; e++, off += 4) {
+            uint64_t acc = cr[off + 3];
+            acc = addmod(mulmod(acc, xu), cr[off + 2]);
+            acc = addmod(mulmod(acc, xu), cr[off + 1]);
+            acc = addmod(mulmod(acc, xu), cr[off]);
+            sbit ^= (uint32_t)(acc & 1u);
+          }
         }
       }
       bin = reduce_m<POW2>(bin, p.m);
