@@ -52,7 +52,8 @@ enum {
   SK_ERR_CUDA = -10,              /* a CUDA runtime call failed */
   SK_ERR_OVERFLOW = -11,          /* an exact intermediate would leave the signed 256-bit range */
   SK_ERR_INEXACT = -12,           /* an FFT correlation could not be certified exact */
-  SK_ERR_NO_MEMORY = -13          /* device allocation failed */
+  SK_ERR_NO_MEMORY = -13,         /* device allocation failed */
+  SK_ERR_SCRATCH_TOO_SMALL = -14  /* the allocation-free estimator's fixed scratch cannot hold this set */
 };
 
 /* Largest number of median rows d a set may have. */
@@ -158,6 +159,31 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
  * Errors: SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_OVERFLOW, SK_ERR_INEXACT,
  * SK_ERR_KEY_OUT_OF_DOMAIN (from earlier updates), SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
 sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * sk_estimate_join_noalloc: the same estimate as sk_estimate_join (identical rows,
+ * median and diagnostics), for callers that cannot allocate device memory while
+ * they estimate -- e.g. code running in a host callback or driver hook that must
+ * not enter the CUDA allocator, a process whose device memory is fully held by
+ * another pool, or a latency-critical path that forbids allocation.  No
+ * counterpart in the paper.
+ * It calls no cudaMalloc/cudaFree and no allocating library routine: all scratch
+ * lives in one static device array of 32 MiB (SK_NOALLOC_SCRATCH_BYTES) that every
+ * GPU loading this library holds until the process exits.  The array's device
+ * address is looked up on the first call on each device (with that device
+ * current), so make that first call before any stream capture.  Every call shares
+ * the array and leaves its contents behind; calls whose GPU work overlaps (other
+ * streams or threads) race on it and must be serialised by the caller.  The
+ * handle itself must have been created earlier (sk_sketch_create allocates).
+ * Limits: the estimator's vector slots ((schedule slots + 1) * d * m * 32 bytes),
+ * twiddles (m * 8 bytes) and small buffers must fit in the array, or the call
+ * returns SK_ERR_SCRATCH_TOO_SMALL before any GPU work; the FFT buffers of each
+ * correlation step (2 * d * ceil(limbs / 2) * m * 16 bytes) must fit in what is
+ * left, or the call returns SK_ERR_SCRATCH_TOO_SMALL at that step.
+ * Synchronises cuda_stream and fills *out.
+ * Errors: those of sk_estimate_join, plus SK_ERR_SCRATCH_TOO_SMALL. */
+#define SK_NOALLOC_SCRATCH_BYTES (32ull << 20)
+sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * sk_sketch_reset: zeroes every counter of the set and its device status word on

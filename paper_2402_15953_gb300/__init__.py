@@ -26,7 +26,7 @@ STATUS = {
     0: "SK_OK", -1: "SK_ERR_INVALID_ARG", -2: "SK_ERR_CYCLIC_QUERY", -3: "SK_ERR_DISCONNECTED_QUERY",
     -4: "SK_ERR_SELF_EDGE", -5: "SK_ERR_UNSUPPORTED_WIDTH", -6: "SK_ERR_BUFFER_TOO_SMALL",
     -7: "SK_ERR_MISMATCH", -8: "SK_ERR_KEY_OUT_OF_DOMAIN", -9: "SK_ERR_TIMEOUT", -10: "SK_ERR_CUDA",
-    -11: "SK_ERR_OVERFLOW", -12: "SK_ERR_INEXACT", -13: "SK_ERR_NO_MEMORY",
+    -11: "SK_ERR_OVERFLOW", -12: "SK_ERR_INEXACT", -13: "SK_ERR_NO_MEMORY", -14: "SK_ERR_SCRATCH_TOO_SMALL",
 }
 globals().update({name: code for code, name in STATUS.items()})
 
@@ -67,7 +67,8 @@ class sk_estimate(ctypes.Structure):
 
 EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_sketch_merge",
            "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
-           "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count"]
+           "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
+           "sk_estimate_join_noalloc"]
 
 _lib = None
 
@@ -89,6 +90,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_sketch_update_batch.argtypes = [vp, i32, i64, vp, i64, vp, vp, vp]
     L.sk_sketch_merge.argtypes = [vp, vp, vp]
     L.sk_estimate_join.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
+    L.sk_estimate_join_noalloc.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
     L.sk_sync.argtypes = [vp, vp]
     L.sk_sketch_destroy.argtypes = [vp]
     L.sk_status_string.argtypes = [i32]

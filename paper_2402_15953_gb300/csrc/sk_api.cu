@@ -259,6 +259,7 @@ const char* sk_status_string(sk_status status) {
     case SK_ERR_OVERFLOW: return "SK_ERR_OVERFLOW";
     case SK_ERR_INEXACT: return "SK_ERR_INEXACT";
     case SK_ERR_NO_MEMORY: return "SK_ERR_NO_MEMORY";
+    case SK_ERR_SCRATCH_TOO_SMALL: return "SK_ERR_SCRATCH_TOO_SMALL";
     default: return "SK_ERR_UNKNOWN";
   }
 }
@@ -354,6 +355,13 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream) {
   std::memset(out, 0, sizeof(*out));
   if (set->m < 2 || set->m > (1ll << 22) || (set->m & (set->m - 1))) return SK_ERR_UNSUPPORTED_WIDTH;
   return run_estimate(set, out, (cudaStream_t)cuda_stream);
+}
+
+sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_stream) {
+  if (!set || !out) return SK_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  if (set->m < 2 || set->m > (1ll << 22) || (set->m & (set->m - 1))) return SK_ERR_UNSUPPORTED_WIDTH;
+  return run_estimate_noalloc(set, out, (cudaStream_t)cuda_stream);
 }
 
 sk_status sk_sketch_reset(sk_set* set, void* cuda_stream) {

@@ -757,4 +757,239 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   return SK_OK;
 }
 
+// ===========================================================================
+// Estimation without device allocation (no counterpart in the paper).
+//
+// Some callers cannot call cudaMalloc while they estimate: code running inside
+// a host callback or a driver-level hook where the CUDA allocator must not be
+// entered, processes whose device memory is fully reserved by another pool, or
+// latency-critical paths that forbid allocation.  sk_estimate_join_noalloc runs
+// the same Algorithm 3 schedule with the same kernels as sk_estimate_join, but
+// carves every scratch buffer (vector slots, FFT buffers, twiddles, small
+// result buffers) out of one file-scope device array of kNoAllocScratchBytes.
+// That array lives in every GPU that loads this library until the process
+// exits.  Its device address is looked up once per device (the first call on
+// that device, with that device current) with cudaGetSymbolAddress; the host-
+// side name of the array is only a stand-in and is never passed to a kernel.
+// All calls share the array: two calls whose work overlaps on the GPU (other
+// streams, other threads) race on it.  Every buffer that must start at zero is
+// cleared on the call's stream before use.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = SK_NOALLOC_SCRATCH_BYTES;   // 32 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+sk_status noalloc_base(char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SK_ERR_INVALID_ARG;
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return set_status_from_cuda(e);
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = (char*)g_noalloc_addr[dev];
+  return SK_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
+  const int64_t m = s->m;
+  const int d = s->d;
+  const int64_t dm = (int64_t)d * m;
+  const int logm = ilog2(m);
+  const int nslots = s->n_slots + 1;
+  if (nslots > 64) return SK_ERR_SCRATCH_TOO_SMALL;
+  // layout: small buffers | twiddles | slots | FFT A | FFT B
+  const size_t small_bytes = align256(4 * SK_MAX_ROWS * sizeof(I256) + 64);
+  const size_t tw_bytes = align256((size_t)(m / 2) * sizeof(double2));
+  const size_t slot_bytes = align256((size_t)dm * sizeof(I256));
+  const size_t fixed = small_bytes + tw_bytes + slot_bytes * nslots;
+  if (fixed > kNoAllocScratchBytes) return SK_ERR_SCRATCH_TOO_SMALL;
+  const size_t fft_room = kNoAllocScratchBytes - fixed;
+  char* base = nullptr;
+  sk_status bs = noalloc_base(&base);
+  if (bs != SK_OK) return bs;
+  I256* d_sa = (I256*)base;
+  I256* d_sx = d_sa + SK_MAX_ROWS;
+  I256* d_sz = d_sx + SK_MAX_ROWS;
+  I256* d_sorted = d_sz + SK_MAX_ROWS;
+  int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);
+  unsigned long long* d_resid = (unsigned long long*)(d_bits + 4);
+  double2* tw = (double2*)(base + small_bytes);
+  char* slot_base = base + small_bytes + tw_bytes;
+  int phys[64];
+  for (int i = 0; i < nslots; i++) phys[i] = i;
+  auto slot = [&](int i) { return (I256*)(slot_base + slot_bytes * phys[i]); };
+  const int spare = nslots - 1;
+
+  SK_CK(cudaMemsetAsync(base, 0, small_bytes, st));
+  k_twiddle<<<grid_for(m / 2), 256, 0, st>>>(tw, m);
+  count_launch();
+  SK_CK(cudaGetLastError());
+
+  double max_resid = 0.0;
+  int max_limbs = 0, last_B = 0, retries = 0;
+  const int eg = grid_for(dm);
+  I256 sa[SK_MAX_ROWS], sx[SK_MAX_ROWS], sz[SK_MAX_ROWS];
+
+  for (const EstOp& op : s->plan) {
+    if (op.kind == OP_LEAF) {
+      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    } else if (op.kind == OP_HAD) {
+      k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    } else if (op.kind == OP_CORR) {
+      I256* x = slot(op.dst);
+      I256* a = slot(op.src);
+      SK_CK(cudaMemsetAsync(d_bits, 0, 2 * sizeof(int), st));
+      k_maxbits<<<eg, 256, 0, st>>>(a, dm, d_bits);
+      count_launch();
+      k_maxbits<<<eg, 256, 0, st>>>(x, dm, d_bits + 1);
+      count_launch();
+      k_rowsum<<<d, 256, 0, st>>>(a, m, d_sa);
+      count_launch();
+      k_rowsum<<<d, 256, 0, st>>>(x, m, d_sx);
+      count_launch();
+      SK_CK(cudaGetLastError());
+      int hb[2];
+      SK_CK(cudaMemcpyAsync(hb, d_bits, sizeof(hb), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaMemcpyAsync(sa, d_sa, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaMemcpyAsync(sx, d_sx, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaStreamSynchronize(st));
+      if (hb[0] == 0 || hb[1] == 0) {
+        SK_CK(cudaMemsetAsync(x, 0, (size_t)dm * sizeof(I256), st));
+        continue;
+      }
+      if (hb[0] + hb[1] + logm + 1 > 255) return SK_ERR_OVERFLOW;
+      int B = limb_bits_for(m, 1);
+      bool done = false;
+      for (int attempt = 0; attempt < 4 && !done; attempt++) {
+        int La = 0, Lx = 0;
+        for (;;) {
+          La = (hb[0] + 2 + B - 1) / B;
+          Lx = (hb[1] + 2 + B - 1) / B;
+          const int nb = limb_bits_for(m, std::min(La, Lx));
+          if (nb >= B) break;
+          B = nb;
+        }
+        if (attempt > 0) {
+          B = std::max(2, B - 3 * attempt);
+          La = (hb[0] + 2 + B - 1) / B;
+          Lx = (hb[1] + 2 + B - 1) / B;
+        }
+        if (La > kMaxLimbs || Lx > kMaxLimbs) return SK_ERR_INEXACT;
+        CorrArgs p;
+        p.a = a;
+        p.x = x;
+        p.z = slot(spare);
+        p.m = m;
+        p.logm = logm;
+        p.d = d;
+        p.B = B;
+        p.La = La;
+        p.Lx = Lx;
+        p.nf = (La + Lx + 1) / 2;
+        p.ni = (La + Lx) / 2;
+        p.status = s->d_status;
+        p.residual = d_resid;
+        const size_t fbytes = align256((size_t)d * p.nf * m * sizeof(double2));
+        if (2 * fbytes > fft_room) return SK_ERR_SCRATCH_TOO_SMALL;
+        double2* bufA = (double2*)(slot_base + slot_bytes * nslots);
+        double2* bufB = (double2*)((char*)bufA + fbytes);
+        p.F = bufA;
+        SK_CK(cudaMemsetAsync(d_resid, 0, sizeof(unsigned long long), st));
+        k_split<<<eg, 256, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, m, tw, false, st);
+        if (fs != SK_OK) return fs;
+        p.F = bufB;
+        p.G = bufA;
+        k_product<<<eg, 128, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        fs = fft(bufA, bufB, (int64_t)d * p.ni, m, tw, true, st);
+        if (fs != SK_OK) return fs;
+        k_recombine<<<eg, 256, 0, st>>>(p, bufB);
+        count_launch();
+        k_rowsum<<<d, 256, 0, st>>>(p.z, m, d_sz);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        unsigned long long rbits = 0;
+        SK_CK(cudaMemcpyAsync(&rbits, d_resid, sizeof(rbits), cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaMemcpyAsync(sz, d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaStreamSynchronize(st));
+        double resid;
+        std::memcpy(&resid, &rbits, sizeof(resid));
+        bool ok = resid <= 0.25;
+        for (int r = 0; r < d && ok; r++) ok = i256_eq(sz[r], HostI256::mul(sa[r], sx[r]));
+        max_resid = std::max(max_resid, resid);
+        max_limbs = std::max(max_limbs, std::max(La, Lx));
+        last_B = B;
+        if (ok) {
+          std::swap(phys[op.dst], phys[spare]);
+          done = true;
+        } else {
+          retries++;
+        }
+      }
+      if (!done) return SK_ERR_INEXACT;
+    } else {  // OP_SUM
+      k_rowsum<<<d, 256, 0, st>>>(slot(op.dst), m, d_sz);
+      count_launch();
+      k_sort_rows<<<1, 32, 0, st>>>(d_sz, d, d_sorted);
+      count_launch();
+      SK_CK(cudaGetLastError());
+    }
+  }
+  I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
+  int status = 0;
+  SK_CK(cudaMemcpyAsync(rows, d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(sorted, d_sorted, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  if (status != 0) {
+    SK_CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
+    SK_CK(cudaStreamSynchronize(st));
+    return (sk_status)status;
+  }
+  auto to_double = [](const I256& v) {
+    const bool neg = i256_neg_p(v);
+    const I256 a = neg ? i256_neg(v) : v;
+    double r = 0.0;
+    for (int k = 3; k >= 0; k--) r = r * 18446744073709551616.0 + (double)a.w[k];
+    return neg ? -r : r;
+  };
+  out->d = d;
+  for (int r = 0; r < d; r++) std::memcpy(&out->row[r], &rows[r], sizeof(sk_i256));
+  const I256 med = sorted[(d - 1) / 2];
+  std::memcpy(&out->median, &med, sizeof(sk_i256));
+  const bool fits = (med.w[1] == med.w[2] && med.w[2] == med.w[3] &&
+                     (med.w[3] == 0 ? (int64_t)med.w[0] >= 0 : (med.w[3] == ~0ull && (int64_t)med.w[0] < 0)));
+  out->fits_i64 = fits ? 1 : 0;
+  out->median_i64 = fits ? (int64_t)med.w[0] : 0;
+  out->median_f64 = to_double(med);
+  out->mid_mean_f64 = (d & 1) ? to_double(sorted[d / 2])
+                              : 0.5 * (to_double(sorted[d / 2 - 1]) + to_double(sorted[d / 2]));
+  out->max_residual = max_resid;
+  out->max_limbs = max_limbs;
+  out->limb_bits = last_B;
+  out->corr_steps = s->corr_steps;
+  out->retries = retries;
+  return SK_OK;
+}
+
 }  // namespace sk
