@@ -232,8 +232,9 @@ class SketchSet:
         """cols: int64 [a][n] CUDA tensor (attribute-major; the row stride is cols.stride(0));
         weights: int64 [n] or None (unit weights)."""
         t = self._torch
-        assert cols.dtype == t.int64 and cols.is_cuda and cols.dim() == 2 and cols.stride(1) == 1
+        assert cols.dtype == t.int64 and cols.is_cuda and cols.dim() == 2
         n = int(cols.shape[1])
+        assert n == 0 or cols.stride(1) == 1
         wp = None
         if weights is not None:
             assert weights.dtype == t.int64 and weights.is_cuda and weights.is_contiguous()

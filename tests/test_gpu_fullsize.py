@@ -1,0 +1,65 @@
+"""Parity at the benchmark's full size and launch configuration (star join: F with 10^8
+tuples x 5 Zipf(1.1) int64 keys over [0, 10^6), five 10^6-row uniform dimensions,
+m = 2^16, d = 9, seed 42), on outputs the oracle can compute: every counter of the
+dimension sketches, two complete rows of the fact sketch, and the estimate of those
+two rows; the median is checked to be the lower median of the GPU's row values."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2402_15953_gb300 as pkg
+import synth
+
+pytestmark = pytest.mark.gpu
+
+ROWS = [0, 4]
+
+
+@pytest.fixture(scope="module")
+def star_run():
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+    wl = synth.star(device="cuda")
+    s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+    for k, rel in enumerate(wl.relations):
+        s.update(k, rel.cols)
+    s.sync()
+    est = s.estimate()
+    counters = s.counters.cpu().numpy()
+    cols = [rel.cols.cpu().numpy() for rel in wl.relations]
+    s.close()
+    del wl
+    torch.cuda.empty_cache()
+    q = O.canonical_query([5, 1, 1, 1, 1, 1], [(0, i, 1 + i, 0) for i in range(5)])
+    co = O.draw_coefficients(42, 9, q.n_comp, len(q.edges))
+    return q, co, cols, counters, est
+
+
+def test_dimension_sketches_all_rows(star_run):
+    q, co, cols, counters, _ = star_run
+    for k in range(1, 6):
+        ref = O.sketch_relation(q, co, k, cols[k], None, 1 << 16, threads=16)
+        assert np.array_equal(counters[k], ref), k
+
+
+def test_fact_sketch_sampled_rows_and_their_estimates(star_run):
+    q, co, cols, counters, est = star_run
+    sub = co[ROWS]
+    ref_f = O.sketch_relation(q, sub, 0, cols[0], None, 1 << 16, threads=16)
+    for t, row in enumerate(ROWS):
+        assert np.array_equal(counters[0][row], ref_f[t]), row
+    ref_d = [O.sketch_relation(q, sub, k, cols[k], None, 1 << 16, threads=16) for k in range(1, 6)]
+    for t, row in enumerate(ROWS):
+        sk_row = [ref_f[t].tolist()] + [rd[t].tolist() for rd in ref_d]
+        assert O.estimate_row(q, sk_row, threads=16) == est["rows"][row], row
+
+
+def test_median_is_lower_median_of_rows(star_run):
+    _, _, _, _, est = star_run
+    rows = sorted(est["rows"])
+    assert est["median"] == rows[(len(rows) - 1) // 2]
+    assert est["max_residual"] <= 0.25
+    if est["fits_i64"]:
+        assert est["median_i64"] == est["median"]

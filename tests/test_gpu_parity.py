@@ -99,6 +99,33 @@ def test_large_batch_smem_and_global_paths():
         s.close()
 
 
+@pytest.mark.parametrize("a,d,m", [(1, 3, 1 << 14), (2, 9, 1 << 16), (3, 17, 1 << 12), (5, 9, 1 << 16),
+                                    (4, 32, 1 << 13), (5, 5, 1 << 20)])
+@pytest.mark.parametrize("cached", ["0", "1"])
+def test_update_hot_key_cache_path(a, d, m, cached, monkeypatch):
+    """Large Zipf batches (many repeated keys), some keys >= 2^32 and negative keys (the
+    full-width arithmetic), signed weights; through the plain kernel and through the
+    hot-key cached kernel (SK_UPDATE_CACHE=1)."""
+    monkeypatch.setenv("SK_UPDATE_CACHE", cached)
+    n = 300_000
+    rng = np.random.default_rng(a * 100 + d)
+    cols = np.stack([synth.zipf_keys(n, 1.1, 1 << 16, 1000 + c).numpy() for c in range(a)])
+    wide = rng.random((a, n)) < 0.05
+    cols = np.where(wide, cols * 1_000_003_117 + (1 << 40), cols)
+    neg = rng.random((a, n)) < 0.02
+    cols = np.where(neg, -cols - 1, cols).astype(np.int64)
+    w = rng.choice(np.array([-2, -1, 1, 1, 3], dtype=np.int64), size=n)
+    attrs = [a] + [1] * a
+    edges = [(0, i, 1 + i, 0) for i in range(a)]
+    rels = [(cols, w)] + [(np.zeros((1, 0), dtype=np.int64), None)] * a
+    s = _gpu_sketch(attrs, edges, m, d, 4242, rels)
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(4242, d, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols, w, m, threads=16)
+    assert np.array_equal(s.counters[0].cpu().numpy(), ref)
+    s.close()
+
+
 def test_chain3_config_exact():
     """Chain R1(A) - R2(A,B) - R3(B), 10^4 rows each, m = 256, d = 5, seed 42: bit-exact
     sketches, exact row estimates and median."""
