@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tuples", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "serving"],
+                    help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
+                         "launches; serving: request loop latency")
+    ap.add_argument("--requests", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -396,11 +400,188 @@ def run_e2e(args, s, wl, stream, world):
             "ms_per_step": dt * 1e3, "steps": steps}
 
 
+def run_batched(args, world, rank):
+    """256 relations (lognormal row counts 1e3..1e7, 1-4 Zipf columns, m = 2^10..2^18, d = 7,
+    +-1 weights with 10% deletions): one step resets the 256 sketches and applies every
+    relation's batch, (a) one sk_sketch_update_batch launch per relation, (b) one persistent
+    sk_update_plan_run (autotuned), (c) the same captured in a CUDA graph.  The sketches of
+    (a) and (b) are compared after timing."""
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    import synth
+    from paper_2402_15953_gb300 import build as pkg_build
+    pkg_build.build()
+    wl = synth.batched(seed=42 + rank, device="cuda")
+    total = sum(b.relation.n for b in wl)
+    sa = [pkg.SketchSet(b.num_join_attrs, b.edges, b.m, b.d, b.hash_seed) for b in wl]
+    sb = [pkg.SketchSet(b.num_join_attrs, b.edges, b.m, b.d, b.hash_seed) for b in wl]
+    plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(sb, wl)])
+    stream = torch.cuda.current_stream()
+    best, tune_ms = plan.autotune()
+
+    def step_a():
+        for s, b in zip(sa, wl):
+            s.reset()
+            s.update(0, b.relation.cols, b.relation.weights)
+
+    def step_b():
+        for s in sb:
+            s.reset()
+        plan.run()
+
+    def timeit(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(world, e0.elapsed_time(e1) / steps)
+
+    ms_a = timeit(step_a, args.steps)
+    ms_b = timeit(step_b, args.steps)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        step_b()
+    side.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        step_b()
+    ms_c = timeit(g.replay, args.steps)
+    step_a()
+    step_b()
+    torch.cuda.synchronize()
+    same = all(torch.equal(x.counters, y.counters) for x, y in zip(sa, sb))
+    line = {"metric": "batched build: tuples/s for 256 relations", "value": world * total / (ms_c / 1e3),
+            "unit": "tuples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "256 relations, rows lognormal(median 1e5, sigma 1.5) in [1e3, 1e7], 1-4 Zipf "
+                                   "columns (s in [0.8, 1.4], domains 1e4..1e7), m = 2^10..2^18, d = 7, +-1 weights "
+                                   "with 10% deletions", "tuples_per_step": total},
+            "per_relation_launches_ms": ms_a, "persistent_plan_ms": ms_b, "persistent_plan_graph_ms": ms_c,
+            "speedup_vs_per_relation": ms_a / ms_c, "identical_sketches": same, "autotuned": best}
+    plan.close()
+    for s in sa + sb:
+        s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, world, rank):
+    """64 live sets (chains of 2-6 relations, m = 2^14..2^18, d = 9); update batches of
+    log-uniform 1e3..1e6 tuples (Zipf 1.1 keys over 1e6, 5% of rows deleted) and estimate
+    requests, 10:1, Poisson arrivals; HBM budget 32 GB.  First every request is submitted
+    at once (saturated throughput), then arrivals at 50% and 90% of that rate; latency =
+    arrival to result on the host."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2402_15953_gb300 import build as pkg_build
+    from paper_2402_15953_gb300.serve import SketchServer
+    pkg_build.build()
+    rng = np.random.default_rng(7 + rank)
+    n_sets = 64
+    sets = []
+    for i in range(n_sets):
+        r = int(rng.integers(2, 7))
+        attrs = [1 if k in (0, r - 1) else 2 for k in range(r)]
+        edges = [(k, 0 if k == 0 else 1, k + 1, 0) for k in range(r - 1)]
+        sets.append((attrs, edges, 1 << int(rng.integers(14, 19)), 9, int(rng.integers(1 << 62))))
+    pool = []
+    for j in range(48):
+        n = int(round(10 ** rng.uniform(3, 6)))
+        for a in (1, 2):
+            cols = torch.stack([synth.zipf_keys(n, 1.1, 1_000_000, synth.sub_seed(j, a, c), "cuda") for c in range(a)])
+            w = torch.where(torch.rand(n, device="cuda") < 0.05, -1, 1).to(torch.int64)
+            pool.append((a, cols.cpu().pin_memory(), w.cpu().pin_memory()))
+    by_arity = {1: [p for p in pool if p[0] == 1], 2: [p for p in pool if p[0] == 2]}
+
+    def make_trace(count, seed):
+        g = np.random.default_rng(seed)
+        tr = []
+        for j in range(count):
+            sid = int(g.integers(n_sets))
+            if j % 11 == 10:
+                tr.append(("estimate", sid))
+            else:
+                attrs = sets[sid][0]
+                rel = int(g.integers(len(attrs)))
+                _, cols, w = by_arity[attrs[rel]][int(g.integers(len(by_arity[attrs[rel]])))]
+                tr.append(("update", sid, rel, cols, w))
+        return tr
+
+    def run(trace, rate):
+        srv = SketchServer(hbm_budget_bytes=32 << 30, update_slots=16, estimate_workers=4)
+        for i, (a, e, m, d, sd) in enumerate(sets):
+            srv.register_set(i, a, e, m, d, sd)
+        reqs = []
+        t0 = time.perf_counter()
+
+        def producer():
+            gaps = np.random.default_rng(99).exponential(1.0 / rate, size=len(trace)) if rate else None
+            t = time.perf_counter()
+            for j, r in enumerate(trace):
+                if rate:
+                    t += gaps[j]
+                    while time.perf_counter() < t:
+                        pass
+                if r[0] == "update":
+                    reqs.append(srv.submit_update(r[1], r[2], r[3], r[4]))
+                else:
+                    reqs.append(srv.submit_estimate(r[1]))
+
+        th = threading.Thread(target=producer)
+        th.start()
+        while th.is_alive() or srv.pending():
+            srv.serve(until_idle=True)
+            time.sleep(1e-4)
+        th.join()
+        srv.serve(until_idle=True)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = sorted(r.latency * 1e3 for r in reqs)
+        est = sorted(r.latency * 1e3 for r in reqs if r.kind == "estimate")
+        tuples = sum(r.cols.shape[1] for r in reqs if r.kind == "update")
+        errors = sum(1 for r in reqs if r.error)
+        return {"requests": len(reqs), "wall_s": wall, "requests_per_s": len(reqs) / wall,
+                "tuples_per_s": tuples / wall, "p50_ms": lat[len(lat) // 2], "p99_ms": percentile(lat, 99.0),
+                "estimate_p50_ms": est[len(est) // 2] if est else None,
+                "estimate_p99_ms": percentile(est, 99.0) if est else None, "errors": errors}
+
+    trace = make_trace(args.requests, 1)
+    run(make_trace(200, 2), None)           # warm-up (scratch allocation, kernel attributes)
+    sat = run(trace, None)
+    points = {"saturated": sat}
+    for frac in (0.5, 0.9):
+        points[f"rate_{int(frac * 100)}pct"] = run(trace, frac * sat["requests_per_s"])
+    line = {"metric": "serving: p50/p99 request latency and throughput", "value": sat["tuples_per_s"],
+            "unit": "tuples/s", "n_gpus": world, "steps": args.requests, "warmup": 200,
+            "ms_per_step": 1e3 / sat["requests_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "64 live sets (chains of 2-6 relations, m = 2^14..2^18, d = 9); update batches "
+                                   "log-uniform 1e3..1e6 tuples, Zipf 1.1 keys over 1e6, 5% deletions; 10 updates : "
+                                   "1 estimate; Poisson arrivals; HBM budget 32 GB"},
+            "points": points}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank)
+    elif args.workload == "serving":
+        run_serving(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

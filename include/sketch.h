@@ -144,6 +144,54 @@ sk_status sk_sketch_update_batch(sk_set* set, int32_t relation, int64_t n_rows, 
                                  const int64_t* domain_hint, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched update: many (set, relation, batch) items in one persistent launch.
+ *
+ * sk_update_plan_create records n_items update batches (each exactly what one
+ * sk_sketch_update_batch call would take: Algorithm 2 for that relation of that
+ * set) and uploads a descriptor table.  sk_update_plan_run then applies all of
+ * them with ONE kernel launch (plus a 8-byte memset of its work counter) on
+ * cuda_stream: CTAs take chunks of tuples from a device work queue in item order,
+ * so small batches share the GPU instead of each paying a launch.  The counters
+ * receive exactly the same values as the item-by-item calls (integer addition is
+ * order independent).  A run is capturable in a CUDA graph.  The plan keeps the
+ * items' pointers: the caller may change the buffers' contents between runs, not
+ * their addresses or sizes.  Items of one plan must not target the same counters
+ * from different plans running concurrently.  Key domains are not checked.  A
+ * relation in a plan may have at most 5 joined attributes.
+ *
+ * sk_update_plan_config: chunk_tuples (tuples per work item), threads (per CTA),
+ * ctas_per_sm, smem_max_counters (items with d*m at most this, and at most 40960,
+ * use a per-chunk int32 shared-memory sub-sketch; 0 = never).  sk_update_plan_autotune times a set
+ * of configurations on the plan itself (every timed run updates the counters:
+ * reset them afterwards) and keeps the fastest.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
+typedef struct {
+  sk_set* set;
+  int32_t relation;
+  int64_t n_rows;
+  const int64_t* dev_cols;
+  int64_t col_stride;
+  const int64_t* dev_weights;
+} sk_update_item;
+
+typedef struct {
+  int32_t chunk_tuples;
+  int32_t threads;
+  int32_t ctas_per_sm;
+  int32_t smem_max_counters;
+} sk_update_plan_config;
+
+typedef struct sk_update_plan sk_update_plan;
+
+sk_status sk_update_plan_create(const sk_update_item* items, int32_t n_items, sk_update_plan** out);
+sk_status sk_update_plan_run(sk_update_plan* plan, void* cuda_stream);
+sk_status sk_update_plan_get_config(const sk_update_plan* plan, sk_update_plan_config* out);
+sk_status sk_update_plan_set_config(sk_update_plan* plan, const sk_update_plan_config* config);
+sk_status sk_update_plan_autotune(sk_update_plan* plan, void* cuda_stream, sk_update_plan_config* best,
+                                  double* best_ms);
+sk_status sk_update_plan_destroy(sk_update_plan* plan);
+
+/* ---------------------------------------------------------------------------
  * sk_sketch_merge: dst += src, counter by counter (Section 2.2: linear sketches
  * combine by addition).  Both sets must have the same query, m, d and seed.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_MISMATCH, SK_ERR_CUDA. */

@@ -65,10 +65,24 @@ class sk_estimate(ctypes.Structure):
                 ("corr_steps", ctypes.c_int32), ("retries", ctypes.c_int32), ("row", sk_i256 * SK_MAX_ROWS)]
 
 
+class sk_update_item(ctypes.Structure):
+    _fields_ = [("set", ctypes.c_void_p), ("relation", ctypes.c_int32), ("n_rows", ctypes.c_int64),
+                ("dev_cols", ctypes.c_void_p), ("col_stride", ctypes.c_int64), ("dev_weights", ctypes.c_void_p)]
+
+
+class sk_update_plan_config(ctypes.Structure):
+    _fields_ = [("chunk_tuples", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_max_counters", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_sketch_merge",
            "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
            "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
-           "sk_estimate_join_noalloc"]
+           "sk_estimate_join_noalloc", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_get_config",
+           "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy"]
 
 _lib = None
 
@@ -100,6 +114,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_get_coefficients.argtypes = [vp, ctypes.POINTER(u64), sz]
     L.sk_set_coefficients.argtypes = [vp, ctypes.POINTER(u64), sz, vp]
     L.sk_sketch_reset.argtypes = [vp, vp]
+    L.sk_update_plan_create.argtypes = [ctypes.POINTER(sk_update_item), i32, ctypes.POINTER(vp)]
+    L.sk_update_plan_run.argtypes = [vp, vp]
+    L.sk_update_plan_get_config.argtypes = [vp, ctypes.POINTER(sk_update_plan_config)]
+    L.sk_update_plan_set_config.argtypes = [vp, ctypes.POINTER(sk_update_plan_config)]
+    L.sk_update_plan_autotune.argtypes = [vp, vp, ctypes.POINTER(sk_update_plan_config), ctypes.POINTER(ctypes.c_double)]
+    L.sk_update_plan_destroy.argtypes = [vp]
     L.sk_launch_count.argtypes = []
     L.sk_launch_count.restype = i64
     for name in EXPORTS:
@@ -201,6 +221,42 @@ def sk_set_coefficients(handle: int, coeffs: Sequence[Sequence[int]], stream: in
     _check(load().sk_set_coefficients(handle, buf, len(flat), stream), "sk_set_coefficients")
 
 
+def sk_update_plan_create(items) -> int:
+    """items: sequence of (set_handle, relation, n_rows, dev_cols, col_stride, dev_weights or None)."""
+    arr = (sk_update_item * max(1, len(items)))(*[sk_update_item(h, r, n, c, st, w or None)
+                                                   for (h, r, n, c, st, w) in items])
+    out = ctypes.c_void_p(0)
+    _check(load().sk_update_plan_create(arr, len(items), ctypes.byref(out)), "sk_update_plan_create")
+    return out.value
+
+
+def sk_update_plan_run(plan: int, stream: int) -> None:
+    _check(load().sk_update_plan_run(plan, stream), "sk_update_plan_run")
+
+
+def sk_update_plan_get_config(plan: int) -> sk_update_plan_config:
+    c = sk_update_plan_config()
+    _check(load().sk_update_plan_get_config(plan, ctypes.byref(c)), "sk_update_plan_get_config")
+    return c
+
+
+def sk_update_plan_set_config(plan: int, chunk_tuples: int, threads: int, ctas_per_sm: int,
+                              smem_max_counters: int) -> None:
+    c = sk_update_plan_config(chunk_tuples, threads, ctas_per_sm, smem_max_counters)
+    _check(load().sk_update_plan_set_config(plan, ctypes.byref(c)), "sk_update_plan_set_config")
+
+
+def sk_update_plan_autotune(plan: int, stream: int):
+    c = sk_update_plan_config()
+    ms = ctypes.c_double(0.0)
+    _check(load().sk_update_plan_autotune(plan, stream, ctypes.byref(c), ctypes.byref(ms)), "sk_update_plan_autotune")
+    return c.as_dict(), ms.value
+
+
+def sk_update_plan_destroy(plan: int) -> None:
+    _check(load().sk_update_plan_destroy(plan), "sk_update_plan_destroy")
+
+
 # ---- convenience wrapper ---------------------------------------------------------------
 
 class SketchSet:
@@ -268,6 +324,54 @@ class SketchSet:
     def close(self) -> None:
         if self.handle is not None:
             sk_sketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UpdatePlan:
+    """Many update batches applied by one persistent launch (sk_update_plan_*).  items are
+    (SketchSet, relation, cols [a][n] int64 CUDA tensor, weights int64 [n] or None); the
+    tensors are kept alive by the plan and may be refilled in place between runs."""
+
+    def __init__(self, items):
+        import torch
+        self._torch = torch
+        self._keep = []
+        raw = []
+        for (sset, rel, cols, w) in items:
+            assert cols.dtype == torch.int64 and cols.is_cuda and cols.dim() == 2
+            n = int(cols.shape[1])
+            assert n == 0 or cols.stride(1) == 1
+            if w is not None:
+                assert w.dtype == torch.int64 and w.is_cuda and w.is_contiguous()
+            self._keep.append((sset, cols, w))
+            raw.append((sset.handle, rel, n, cols.data_ptr() if n else None, int(cols.stride(0)) if n else 0,
+                        None if w is None else w.data_ptr()))
+        self.handle = sk_update_plan_create(raw)
+
+    def _stream(self) -> int:
+        return self._torch.cuda.current_stream().cuda_stream
+
+    def run(self) -> None:
+        sk_update_plan_run(self.handle, self._stream())
+
+    def config(self) -> dict:
+        return sk_update_plan_get_config(self.handle).as_dict()
+
+    def set_config(self, chunk_tuples: int, threads: int, ctas_per_sm: int, smem_max_counters: int) -> None:
+        sk_update_plan_set_config(self.handle, chunk_tuples, threads, ctas_per_sm, smem_max_counters)
+
+    def autotune(self):
+        return sk_update_plan_autotune(self.handle, self._stream())
+
+    def close(self) -> None:
+        if self.handle is not None:
+            sk_update_plan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -33,8 +33,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(ROOT, "include", "sketch.h"),
-                                                                         os.path.abspath(__file__)]
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+    return _sources() + headers + [os.path.join(ROOT, "include", "sketch.h"), os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

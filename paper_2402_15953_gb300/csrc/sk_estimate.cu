@@ -186,12 +186,21 @@ __global__ void k_maxbits(const I256* __restrict__ v, int64_t n, int* out) {
   if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
 }
 
-// per-row exact sums: one block per row
+// per-row exact sums: one block per row, four independent accumulators per thread
 __global__ void k_rowsum(const I256* __restrict__ v, int64_t m, I256* out) {
   __shared__ I256 part[32];
   const I256* row = v + (int64_t)blockIdx.x * m;
-  I256 acc{{0, 0, 0, 0}};
-  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) acc = i256_add(acc, row[j]);
+  I256 acc{{0, 0, 0, 0}}, acc1{{0, 0, 0, 0}}, acc2{{0, 0, 0, 0}}, acc3{{0, 0, 0, 0}};
+  const int64_t step = blockDim.x;
+  int64_t j = threadIdx.x;
+  for (; j + 3 * step < m; j += 4 * step) {
+    acc = i256_add(acc, row[j]);
+    acc1 = i256_add(acc1, row[j + step]);
+    acc2 = i256_add(acc2, row[j + 2 * step]);
+    acc3 = i256_add(acc3, row[j + 3 * step]);
+  }
+  for (; j < m; j += step) acc = i256_add(acc, row[j]);
+  acc = i256_add(i256_add(acc, acc1), i256_add(acc2, acc3));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     I256 t;
@@ -261,7 +270,47 @@ __device__ void smem_fft(double2* s, int cnt, int logL, const double2* __restric
   const int L = 1 << logL;
   const int halfL = L >> 1;
   const int total = cnt * halfL;
-  for (int st = 0; st < logL; st++) {
+  int st = 0;
+  // Pairs of radix-2 stages (half sizes h and 2h) fused: the four elements b, b+h, b+2h,
+  // b+3h (b = group * 4h + pos, pos < h) are closed under both stages.  Stage one
+  // pairs (b, b+h), (b+2h, b+3h) with W_2h^pos; stage two pairs (b, b+2h) with
+  // W_4h^pos and (b+h, b+3h) with W_4h^(pos+h) = W_4h^pos * W_4^1 = -i W_4h^pos
+  // (+i for the inverse).
+  if (logL >= 2) {
+    const int quarterL = L >> 2;
+    const int total4 = cnt * quarterL;
+    for (; st + 1 < logL; st += 2) {
+      const int h = 1 << st;
+      const int64_t t1 = (int64_t)(L >> (st + 1)) * twstride;   // W_2h^pos = tw[pos * t1]
+      const int64_t t2 = (int64_t)(L >> (st + 2)) * twstride;   // W_4h^pos = tw[pos * t2]
+      for (int b4 = threadIdx.x; b4 < total4; b4 += blockDim.x) {
+        const int v = b4 >> (logL - 2);
+        const int jj = b4 & (quarterL - 1);
+        const int grp = jj >> st, pos = jj & (h - 1);
+        const int i0 = v * L + grp * 4 * h + pos;
+        double2 w1 = tw[(int64_t)pos * t1];
+        double2 w2 = tw[(int64_t)pos * t2];
+        if (inv) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+        }
+        const double2 w3 = inv ? make_double2(-w2.y, w2.x) : make_double2(w2.y, -w2.x);
+        const double2 a0 = s[i0], a1 = s[i0 + h], a2 = s[i0 + 2 * h], a3 = s[i0 + 3 * h];
+        const double2 t01 = cmul(a1, w1), t23 = cmul(a3, w1);
+        const double2 b0 = make_double2(a0.x + t01.x, a0.y + t01.y);
+        const double2 b1 = make_double2(a0.x - t01.x, a0.y - t01.y);
+        const double2 b2 = make_double2(a2.x + t23.x, a2.y + t23.y);
+        const double2 b3 = make_double2(a2.x - t23.x, a2.y - t23.y);
+        const double2 u2 = cmul(b2, w2), u3 = cmul(b3, w3);
+        s[i0] = make_double2(b0.x + u2.x, b0.y + u2.y);
+        s[i0 + 2 * h] = make_double2(b0.x - u2.x, b0.y - u2.y);
+        s[i0 + h] = make_double2(b1.x + u3.x, b1.y + u3.y);
+        s[i0 + 3 * h] = make_double2(b1.x - u3.x, b1.y - u3.y);
+      }
+      __syncthreads();
+    }
+  }
+  for (; st < logL; st++) {
     const int h = 1 << st;
     const int64_t tstep = (int64_t)(L >> (st + 1)) * twstride;
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
@@ -503,16 +552,19 @@ int limb_bits_for(int64_t m, int npairs) {
   return 2;
 }
 
-cudaError_t ensure(Scratch& s, size_t bytes) {
+// Grows a scratch buffer with the stream-ordered allocator: the old buffer is only
+// ever used by earlier work of this estimate on the same stream (sk_estimate_join
+// synchronises its stream before returning), so freeing and reallocating in stream
+// order needs no device-wide synchronisation.
+cudaError_t ensure(Scratch& s, size_t bytes, cudaStream_t st) {
   if (s.bytes >= bytes) return cudaSuccess;
   if (s.ptr) {
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = cudaFreeAsync(s.ptr, st);
     if (e != cudaSuccess) return e;
-    cudaFree(s.ptr);
     s.ptr = nullptr;
     s.bytes = 0;
   }
-  cudaError_t e = cudaMalloc(&s.ptr, bytes);
+  cudaError_t e = cudaMallocAsync(&s.ptr, bytes, st);
   if (e == cudaSuccess) s.bytes = bytes;
   return e;
 }
@@ -579,7 +631,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const size_t slot_bytes = (size_t)dm * sizeof(I256);
   const size_t small_off = slot_bytes * nslots;
   const size_t small_bytes = 4 * SK_MAX_ROWS * sizeof(I256) + 64;
-  SK_CK(ensure(s->scratch, small_off + small_bytes));
+  SK_CK(ensure(s->scratch, small_off + small_bytes, st));
   if (s->twiddle_m != m) {
     if (s->d_twiddle) cudaFree(s->d_twiddle);
     s->d_twiddle = nullptr;
@@ -623,9 +675,9 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
       count_launch();
       k_maxbits<<<eg, 256, 0, st>>>(x, dm, d_bits + 1);
       count_launch();
-      k_rowsum<<<d, 256, 0, st>>>(a, m, d_sa);
+      k_rowsum<<<d, 1024, 0, st>>>(a, m, d_sa);
       count_launch();
-      k_rowsum<<<d, 256, 0, st>>>(x, m, d_sx);
+      k_rowsum<<<d, 1024, 0, st>>>(x, m, d_sx);
       count_launch();
       SK_CK(cudaGetLastError());
       int hb[2];
@@ -671,7 +723,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
         p.status = s->d_status;
         p.residual = d_resid;
         const size_t fbytes = (size_t)d * p.nf * m * sizeof(double2);
-        SK_CK(ensure(s->fft_scratch, 2 * fbytes));
+        SK_CK(ensure(s->fft_scratch, 2 * fbytes, st));
         double2* bufA = (double2*)s->fft_scratch.ptr;
         double2* bufB = bufA + (size_t)d * p.nf * m;
         p.F = bufA;
@@ -690,7 +742,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
         if (fs != SK_OK) return fs;
         k_recombine<<<eg, 256, 0, st>>>(p, bufB);
         count_launch();
-        k_rowsum<<<d, 256, 0, st>>>(p.z, m, d_sz);
+        k_rowsum<<<d, 1024, 0, st>>>(p.z, m, d_sz);
         count_launch();
         SK_CK(cudaGetLastError());
         unsigned long long rbits = 0;
@@ -713,7 +765,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
       }
       if (!done) return SK_ERR_INEXACT;
     } else {  // OP_SUM
-      k_rowsum<<<d, 256, 0, st>>>(slot(op.dst), m, d_sz);
+      k_rowsum<<<d, 1024, 0, st>>>(slot(op.dst), m, d_sz);
       count_launch();
       k_sort_rows<<<1, 32, 0, st>>>(d_sz, d, d_sorted);
       count_launch();
@@ -859,9 +911,9 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
       count_launch();
       k_maxbits<<<eg, 256, 0, st>>>(x, dm, d_bits + 1);
       count_launch();
-      k_rowsum<<<d, 256, 0, st>>>(a, m, d_sa);
+      k_rowsum<<<d, 1024, 0, st>>>(a, m, d_sa);
       count_launch();
-      k_rowsum<<<d, 256, 0, st>>>(x, m, d_sx);
+      k_rowsum<<<d, 1024, 0, st>>>(x, m, d_sx);
       count_launch();
       SK_CK(cudaGetLastError());
       int hb[2];
@@ -925,7 +977,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
         if (fs != SK_OK) return fs;
         k_recombine<<<eg, 256, 0, st>>>(p, bufB);
         count_launch();
-        k_rowsum<<<d, 256, 0, st>>>(p.z, m, d_sz);
+        k_rowsum<<<d, 1024, 0, st>>>(p.z, m, d_sz);
         count_launch();
         SK_CK(cudaGetLastError());
         unsigned long long rbits = 0;
@@ -948,7 +1000,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
       }
       if (!done) return SK_ERR_INEXACT;
     } else {  // OP_SUM
-      k_rowsum<<<d, 256, 0, st>>>(slot(op.dst), m, d_sz);
+      k_rowsum<<<d, 1024, 0, st>>>(slot(op.dst), m, d_sz);
       count_launch();
       k_sort_rows<<<1, 32, 0, st>>>(d_sz, d, d_sorted);
       count_launch();

@@ -1,0 +1,307 @@
+// Batched update: one persistent launch applies many update batches (items), each
+// an Algorithm 2 pass over one relation of one sketch set.  CTAs pull chunks of
+// tuples from a device work counter in item order; a CTA reloads an item's hash
+// coefficients into shared memory only when it moves to another item.  Items with
+// a small d x m accumulate each chunk in an int32 shared-memory sub-sketch that is
+// flushed into the int64 counters at the end of the chunk.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sk_hash.cuh"
+#include "sk_internal.h"
+
+namespace sk {
+namespace {
+
+using namespace dev;
+
+constexpr int kMaxMultiAttrs = 5;   // joined attributes per relation in a batched plan
+
+struct MultiItem {
+  UpdArgs args;
+  int64_t chunk0;   // first global chunk of this item
+  int pow2;
+  int use_smem;
+};
+
+template <int A, bool POW2>
+__device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
+                                            int64_t t0, int64_t t1) {
+  if (use_smem) {
+    const int64_t dm = (int64_t)p.d * (int64_t)p.m;
+    for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) s_sub[j] = 0;
+    __syncthreads();
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) update_tuple<A, POW2, true>(p, s_coef, s_sub, i);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) {
+      const int v = s_sub[j];
+      if (v != 0) atomicAdd(p.ctr + j, (unsigned long long)(int64_t)v);
+    }
+  } else {
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) update_tuple<A, POW2, false>(p, s_coef, s_sub, i);
+  }
+}
+
+template <bool POW2>
+__device__ __forceinline__ void multi_dispatch(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
+                                               int64_t t0, int64_t t1) {
+  switch (p.a) {
+    case 1: multi_chunk<1, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 2: multi_chunk<2, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 3: multi_chunk<3, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 4: multi_chunk<4, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    default: multi_chunk<5, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __restrict__ items, int n_items, int64_t total_chunks,
+                               int64_t chunk, int coef_words, unsigned long long* queue) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_c;
+  __shared__ int s_item;
+  uint64_t* s_coef = (uint64_t*)smem_raw;
+  int* s_sub = (int*)(s_coef + coef_words);
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t c = (int64_t)atomicAdd(queue, 1ull);
+      s_c = c;
+      if (c < total_chunks) {
+        int lo = 0, hi = n_items - 1;   // last item with chunk0 <= c
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].chunk0 <= c) lo = mid; else hi = mid - 1;
+        }
+        s_item = lo;
+      }
+    }
+    __syncthreads();
+    const int64_t c = s_c;
+    if (c >= total_chunks) break;
+    const int it = s_item;
+    const MultiItem& mi = items[it];
+    const UpdArgs& p = mi.args;
+    if (it != cur) {
+      const int nc = p.d * p.row_len;
+      for (int j = threadIdx.x; j < nc; j += blockDim.x) s_coef[j] = p.coef[j];
+      cur = it;
+      __syncthreads();
+    }
+    const int64_t t0 = (c - mi.chunk0) * chunk;
+    const int64_t t1 = min(p.n, t0 + chunk);
+    if (mi.pow2) multi_dispatch<true>(p, mi.use_smem != 0, s_coef, s_sub, t0, t1);
+    else multi_dispatch<false>(p, mi.use_smem != 0, s_coef, s_sub, t0, t1);
+    __syncthreads();
+  }
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+}  // namespace sk
+
+using namespace sk;
+
+struct sk_update_plan {
+  std::vector<sk_update_item> items;
+  std::vector<MultiItem> host;
+  sk_update_plan_config cfg{};
+  MultiItem* d_items = nullptr;
+  unsigned long long* d_queue = nullptr;
+  int n_active = 0;
+  int64_t total_chunks = 0;
+  int coef_words = 0;
+  size_t smem_bytes = 0;
+};
+
+namespace {
+
+sk_status plan_build(sk_update_plan* pl) {
+  pl->host.clear();
+  int64_t chunk0 = 0;
+  int coef_words = 0;
+  int64_t sub_words = 0;
+  const sk_update_plan_config& cfg = pl->cfg;
+  for (const sk_update_item& it : pl->items) {
+    if (it.n_rows == 0) continue;
+    sk_set* s = it.set;
+    const RelPlan& rp = s->rel[it.relation];
+    MultiItem mi;
+    std::memset(&mi, 0, sizeof(mi));
+    UpdArgs& a = mi.args;
+    a.cols = it.dev_cols;
+    a.stride = it.col_stride;
+    a.w = it.dev_weights;
+    a.n = it.n_rows;
+    a.ctr = (unsigned long long*)(s->counters + (size_t)it.relation * s->d * s->m);
+    a.coef = rp.d_coef;
+    a.row_len = rp.coef_row_len;
+    a.d = s->d;
+    a.a = rp.a;
+    for (int t = 0; t < kMaxAttrs; t++) a.deg[t] = rp.deg[t];
+    a.m = (uint64_t)s->m;
+    a.has_dom = 0;
+    a.status = s->d_status;
+    a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(cfg.chunk_tuples, 1);
+    mi.pow2 = (s->m & (s->m - 1)) == 0;
+    const int64_t dm = (int64_t)s->d * s->m;
+    // the int32 sub-sketch must also fit in shared memory next to the coefficients
+    mi.use_smem = (cfg.smem_max_counters > 0 && dm <= cfg.smem_max_counters && dm * 4 <= 160 * 1024) ? 1 : 0;
+    mi.chunk0 = chunk0;
+    chunk0 += (it.n_rows + cfg.chunk_tuples - 1) / cfg.chunk_tuples;
+    coef_words = std::max(coef_words, s->d * rp.coef_row_len);
+    if (mi.use_smem) sub_words = std::max(sub_words, dm);
+    pl->host.push_back(mi);
+  }
+  pl->n_active = (int)pl->host.size();
+  pl->total_chunks = chunk0;
+  pl->coef_words = (coef_words + 1) & ~1;
+  pl->smem_bytes = (size_t)pl->coef_words * 8 + (size_t)sub_words * 4;
+  if (pl->smem_bytes > 200 * 1024) return SK_ERR_INVALID_ARG;
+  if (pl->d_items) {
+    cudaFree(pl->d_items);
+    pl->d_items = nullptr;
+  }
+  if (pl->n_active > 0) {
+    cudaError_t e = cudaMalloc(&pl->d_items, sizeof(MultiItem) * pl->n_active);
+    if (e != cudaSuccess) return set_status_from_cuda(e);
+    e = cudaMemcpy(pl->d_items, pl->host.data(), sizeof(MultiItem) * pl->n_active, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_status_from_cuda(e);
+  }
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sk_status sk_update_plan_create(const sk_update_item* items, int32_t n_items, sk_update_plan** out) {
+  if (!out || n_items < 0 || (n_items > 0 && !items)) return SK_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n_items; i++) {
+    const sk_update_item& it = items[i];
+    if (!it.set || it.relation < 0 || it.relation >= it.set->r || it.n_rows < 0) return SK_ERR_INVALID_ARG;
+    if (it.n_rows > 0 && (!it.dev_cols || it.col_stride < it.n_rows)) return SK_ERR_INVALID_ARG;
+    if (it.set->rel[it.relation].a > kMaxMultiAttrs) return SK_ERR_INVALID_ARG;
+  }
+  sk_update_plan* pl = new (std::nothrow) sk_update_plan();
+  if (!pl) return SK_ERR_NO_MEMORY;
+  pl->items.assign(items, items + n_items);
+  pl->cfg.chunk_tuples = 32768;
+  pl->cfg.threads = 256;
+  pl->cfg.ctas_per_sm = 6;
+  pl->cfg.smem_max_counters = 16384;
+  cudaError_t e = cudaMalloc(&pl->d_queue, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    delete pl;
+    return set_status_from_cuda(e);
+  }
+  sk_status st = plan_build(pl);
+  if (st != SK_OK) {
+    sk_update_plan_destroy(pl);
+    return st;
+  }
+  *out = pl;
+  return SK_OK;
+}
+
+sk_status sk_update_plan_run(sk_update_plan* pl, void* cuda_stream) {
+  if (!pl) return SK_ERR_INVALID_ARG;
+  if (pl->total_chunks == 0) return SK_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  e = cudaFuncSetAttribute(k_update_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  const int64_t want = pl->total_chunks;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * pl->cfg.ctas_per_sm));
+  k_update_multi<<<grid, pl->cfg.threads, pl->smem_bytes, st>>>(pl->d_items, pl->n_active, pl->total_chunks,
+                                                                pl->cfg.chunk_tuples, pl->coef_words, pl->d_queue);
+  count_launch();
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+sk_status sk_update_plan_get_config(const sk_update_plan* pl, sk_update_plan_config* out) {
+  if (!pl || !out) return SK_ERR_INVALID_ARG;
+  *out = pl->cfg;
+  return SK_OK;
+}
+
+sk_status sk_update_plan_set_config(sk_update_plan* pl, const sk_update_plan_config* c) {
+  if (!pl || !c) return SK_ERR_INVALID_ARG;
+  if (c->chunk_tuples < 256 || c->threads < 32 || c->threads > 256 || (c->threads & 31) || c->ctas_per_sm < 1 ||
+      c->ctas_per_sm > 32 || c->smem_max_counters < 0)
+    return SK_ERR_INVALID_ARG;
+  const sk_update_plan_config old = pl->cfg;
+  pl->cfg = *c;
+  sk_status st = plan_build(pl);
+  if (st != SK_OK) {
+    pl->cfg = old;
+    plan_build(pl);
+  }
+  return st;
+}
+
+sk_status sk_update_plan_autotune(sk_update_plan* pl, void* cuda_stream, sk_update_plan_config* best,
+                                  double* best_ms) {
+  if (!pl) return SK_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int chunks[] = {8192, 32768, 131072};
+  const int ctas[] = {4, 8};
+  const int smem[] = {0, 8192, 32768};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SK_ERR_CUDA;
+  sk_update_plan_config bestc = pl->cfg;
+  float bestt = 1e30f;
+  sk_status rs = SK_OK;
+  for (int ch : chunks)
+    for (int ct : ctas)
+      for (int sm : smem) {
+        sk_update_plan_config c{ch, 256, ct, sm};
+        if (sk_update_plan_set_config(pl, &c) != SK_OK) continue;
+        if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;   // warm-up
+        float total = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+          cudaEventRecord(e0, st);
+          if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          total += ms;
+        }
+        if (rs != SK_OK) break;
+        if (total / 3 < bestt) {
+          bestt = total / 3;
+          bestc = c;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs != SK_OK) return rs;
+  sk_status s2 = sk_update_plan_set_config(pl, &bestc);
+  if (best) *best = bestc;
+  if (best_ms) *best_ms = bestt;
+  return s2;
+}
+
+sk_status sk_update_plan_destroy(sk_update_plan* pl) {
+  if (!pl) return SK_OK;
+  if (pl->d_items) cudaFree(pl->d_items);
+  if (pl->d_queue) cudaFree(pl->d_queue);
+  delete pl;
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -19,179 +19,14 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "sk_hash.cuh"
 #include "sk_internal.h"
 
 namespace sk {
 namespace {
 
-struct UpdArgs {
-  const int64_t* cols;
-  int64_t stride;
-  const int64_t* w;
-  int64_t n;
-  unsigned long long* ctr;   // this relation's [d][m]
-  const uint64_t* coef;      // [d][row_len], see RelPlan
-  int row_len;
-  int d;
-  int a;
-  int deg[kMaxAttrs];
-  uint64_t m;
-  int has_dom;
-  int64_t dom[kMaxAttrs];
-  int* status;
-  int64_t smem_wmax;         // |Delta| <= smem_wmax goes to the int32 sub-sketch
-};
+using namespace dev;
 
-__device__ __forceinline__ uint64_t field_of(int64_t key) {
-  const uint64_t k = (uint64_t)key;
-  const uint64_t x = (k & kP61) + (k >> 61);   // 2^61 == 1 (mod p)
-  return x >= kP61 ? x - kP61 : x;
-}
-
-// a * b mod p for a, b < p: the 122-bit product split at bit 61, the high part
-// folded onto the low part (2^61 == 1 mod p), one conditional subtraction.
-__device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b) {
-  const uint64_t lo = a * b;
-  const uint64_t hi = __umul64hi(a, b);
-  const uint64_t r = (lo & kP61) + ((lo >> 61) | (hi << 3));
-  return r >= kP61 ? r - kP61 : r;
-}
-
-__device__ __forceinline__ uint64_t addmod(uint64_t a, uint64_t b) {
-  const uint64_t r = a + b;
-  return r >= kP61 ? r - kP61 : r;
-}
-
-// Narrow-key arithmetic, used when every key of a tuple lies in [0, 2^32) (then the
-// field element is the key itself): Horner steps with a 32-bit multiplier whose
-// results stay "lazy" (congruent mod p, below 2^61 + 2^35) until one final
-// reduction per polynomial.
-//
-// acc * x + c mod p, lazily, for any acc < 2^64, x < 2^32 and c < 2^61; the result is
-// below 2^61 + 2^35.  The 96-bit value acc x + c is formed from two 32x32+32 -> 64
-// multiply-adds, T = lo32(acc) x + lo32(c) and U = hi32(acc) x + hi32(c) (neither
-// overflows), as s 2^32 + lo32(T) with s = U + (T >> 32) < 2^64; folding at bit 61
-// (2^61 == 1 mod p) leaves ((s mod 2^29) 2^32 + lo32(T)) + (s >> 29).
-__device__ __forceinline__ uint64_t mac_narrow(uint64_t acc, uint32_t x, uint64_t c) {
-  const uint64_t T = (uint64_t)(uint32_t)acc * x + (uint32_t)c;
-  const uint64_t U = (uint64_t)(uint32_t)(acc >> 32) * x + (uint32_t)(c >> 32);
-  const uint64_t sv = U + (T >> 32);
-  const uint32_t s0 = (uint32_t)sv, s1 = (uint32_t)(sv >> 32);
-  const uint32_t fl = __funnelshift_r(s0, s1, 29);
-  const uint32_t fh = s1 >> 29;
-  uint32_t r0, r1;
-  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
-      : "=r"(r0), "=r"(r1)
-      : "r"((uint32_t)T), "r"(fl), "r"(s0 & ((1u << 29) - 1u)), "r"(fh));
-  return ((uint64_t)r1 << 32) | r0;
-}
-
-// floor(v / p) for v < 2^63: with v = a 2^61 + b, v / p = a + (a + b) / p and a + b < 2^61 + 4,
-// so the quotient is a or a + 1, and it is a + 1 exactly when b + a + 1 reaches 2^61.
-__device__ __forceinline__ uint32_t mersenne_q(uint64_t v) { return (uint32_t)((v + (v >> 61) + 1) >> 61); }
-
-// floor(v / p) for the outputs of mac_narrow (v < 2^61 + 2^35 < 2p): 1 exactly when
-// v >= p, i.e. when v + 1 reaches 2^61.
-__device__ __forceinline__ uint32_t mersenne_q1(uint64_t v) { return (uint32_t)((v + 1) >> 61); }
-
-// v < 2^63 -> v mod p
-__device__ __forceinline__ uint64_t reduce_lazy(uint64_t v) {
-  const uint64_t r = (v & kP61) + (v >> 61);
-  return r >= kP61 ? r - kP61 : r;
-}
-
-__device__ __forceinline__ void record(int* status, int code) { atomicCAS(status, 0, code); }
-
-template <bool POW2>
-__device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
-  return POW2 ? (v & (m - 1)) : (v % m);
-}
-
-// A = number of attributes when known at compile time (1..4), 0 = runtime a.
-// Algorithm 2 for tuple i: all d rows hashed in registers, one counter update per row
-// (int32 shared-memory sub-sketch when SMEM and |Delta| is small, int64 global otherwise).
-template <int A, bool POW2, bool SMEM>
-__device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s_coef, int* s_sub, int64_t i) {
-  const int na = A > 0 ? A : p.a;
-  uint64_t x[A > 0 ? A : kMaxAttrs];
-  bool ok = true;
-#pragma unroll
-  for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
-    if (A == 0 && u >= na) break;
-    const int64_t key = __ldg(p.cols + (int64_t)u * p.stride + i);
-    if (p.has_dom && (key < 0 || key >= p.dom[u])) ok = false;
-    x[u] = field_of(key);
-  }
-  if (!ok) {
-    record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
-    return;
-  }
-  const int64_t delta = p.w ? __ldg(p.w + i) : 1;
-  const bool small = SMEM && (delta <= p.smem_wmax && delta >= -p.smem_wmax);
-  bool narrow = true;
-#pragma unroll
-  for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
-    if (A == 0 && u >= na) break;
-    narrow = narrow && (x[u] >> 32) == 0;
-  }
-  const uint64_t* cr = s_coef;
-  for (int row = 0; row < p.d; row++, cr += p.row_len) {
-    uint64_t bin = 0;
-    uint32_t sbit = 0;
-    int off = 0;
-    if (narrow) {
-      // Coefficient pairs are 16-byte aligned: the table starts 16-byte aligned and every
-      // attribute block (2 + 4 deg words) and row (a sum of those) has an even length.
-      uint32_t bin32 = 0, sx = 0;
-#pragma unroll
-      for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
-        if (A == 0 && u >= na) break;
-        const uint32_t xu = (uint32_t)x[u];
-        const ulonglong2 bc = *(const ulonglong2*)(cr + off);
-        const uint64_t v = mac_narrow(bc.y, xu, bc.x);
-        if (POW2) {
-          bin32 += (uint32_t)v + mersenne_q1(v);   // == h(x) mod 2^32
-        } else {
-          bin += reduce_lazy(v) % p.m;
-        }
-        off += 2;
-        for (int e = 0; e < p.deg[u]; e++, off += 4) {
-          const ulonglong2 s01 = *(const ulonglong2*)(cr + off);
-          const ulonglong2 s23 = *(const ulonglong2*)(cr + off + 2);
-          uint64_t acc = mac_narrow(s23.y, xu, s23.x);
-          acc = mac_narrow(acc, xu, s01.y);
-          acc = mac_narrow(acc, xu, s01.x);
-          sx ^= (uint32_t)acc ^ mersenne_q1(acc);   // bit 0: parity of acc mod p
-        }
-      }
-      sbit = sx & 1u;
-      if (POW2) bin = bin32;
-    } else {
-#pragma unroll
-      for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
-        if (A == 0 && u >= na) break;
-        const uint64_t xu = x[u];
-        const uint64_t h = addmod(mulmod(cr[off + 1], xu), cr[off]);
-        bin += reduce_m<POW2>(h, p.m);
-        off += 2;
-        for (int e = 0; e < p.deg[u]; e++, off += 4) {
-          uint64_t acc = cr[off + 3];
-          acc = addmod(mulmod(acc, xu), cr[off + 2]);
-          acc = addmod(mulmod(acc, xu), cr[off + 1]);
-          acc = addmod(mulmod(acc, xu), cr[off]);
-          sbit ^= (uint32_t)(acc & 1u);
-        }
-      }
-    }
-    bin = reduce_m<POW2>(bin, p.m);
-    const int64_t v = sbit ? -delta : delta;
-    if (SMEM && small) {
-      atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
-    } else {
-      atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
-    }
-  }
-}
 
 template <int A, bool POW2, bool SMEM>
 __global__ void __launch_bounds__(256) k_update(UpdArgs p) {

@@ -51,10 +51,10 @@ def zipf_cdf(s: float, n: int, device: str) -> torch.Tensor:
     key = (float(s), int(n), str(device))
     c = _CDF_CACHE.get(key)
     if c is None:
-        k = torch.arange(1, n + 1, dtype=torch.float64)
+        k = torch.arange(1, n + 1, dtype=torch.float64, device=device)
         w = k.pow(-float(s))
         c = torch.cumsum(w, 0)
-        c = (c / c[-1]).to(device)
+        c = c / c[-1]
         if len(_CDF_CACHE) > 16:
             _CDF_CACHE.clear()
         _CDF_CACHE[key] = c
@@ -215,3 +215,42 @@ def lognormal_sizes(count: int, median: float, sigma: float, lo: int, hi: int, s
     rng = np.random.default_rng(seed)
     x = rng.lognormal(math.log(median), sigma, size=count)
     return [int(v) for v in np.clip(np.round(x), lo, hi)]
+
+
+@dataclasses.dataclass
+class BatchedSet:
+    """One sketch set of the batched workload: a star query whose relation 0 carries the
+    stream (a join columns) and whose relations 1..a are one-attribute partners, so every
+    column is hashed."""
+    num_join_attrs: List[int]
+    edges: List[Tuple[int, int, int, int]]
+    m: int
+    d: int
+    hash_seed: int
+    relation: Relation
+
+
+def batched(count: int = 256, median_rows: float = 1e5, sigma: float = 1.5, min_rows: int = 1000,
+            max_rows: int = 10_000_000, d: int = 7, log2m: Tuple[int, int] = (10, 18), delete_frac: float = 0.1,
+            seed: int = 42, device: str = "cpu") -> List[BatchedSet]:
+    """count relations, rows lognormal(median_rows, sigma) clipped to [min_rows, max_rows],
+    1-4 int64 join columns each with Zipf s ~ U[0.8, 1.4] over a domain log-uniform in
+    [1e4, 1e7], width m = 2^U{log2m}, d rows, weights +1 with a delete_frac share of
+    earlier-inserted rows deleted (-1) after their insert."""
+    rng = np.random.default_rng(seed)
+    sizes = lognormal_sizes(count, median_rows, sigma, min_rows, max_rows, seed + 1)
+    out = []
+    for i in range(count):
+        a = int(rng.integers(1, 5))
+        n = sizes[i]
+        n_ins = max(1, int(round(n / (1 + delete_frac))))
+        cols = []
+        for c in range(a):
+            s_exp = float(rng.uniform(0.8, 1.4))
+            dom = int(round(10 ** rng.uniform(4, 7)))
+            cols.append(zipf_keys(n_ins, s_exp, dom, sub_seed(seed, i, c), device))
+        rel = with_deletions(Relation(torch.stack(cols)), delete_frac, sub_seed(seed, i, 77))
+        m = 1 << int(rng.integers(log2m[0], log2m[1] + 1))
+        out.append(BatchedSet([a] + [1] * a, [(0, k, 1 + k, 0) for k in range(a)], m, d,
+                              sub_seed(seed, i, 5), rel))
+    return out

@@ -1,0 +1,98 @@
+"""The batched form (sk_update_plan_*): one persistent launch over many update batches
+gives exactly the counters of the item-by-item calls and of the oracle, also when the
+run is captured in a CUDA graph and after autotuning."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2402_15953_gb300 as pkg
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def workload():
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+    return synth.batched(count=40, median_rows=2e4, sigma=1.5, min_rows=100, max_rows=300_000, log2m=(4, 14),
+                         seed=9, device="cuda")
+
+
+def _sets(wl):
+    return [pkg.SketchSet(b.num_join_attrs, b.edges, b.m, b.d, b.hash_seed) for b in wl]
+
+
+def test_plan_equals_item_by_item_and_oracle(workload):
+    ref = _sets(workload)
+    for s, b in zip(ref, workload):
+        s.update(0, b.relation.cols, b.relation.weights)
+    got = _sets(workload)
+    plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(got, workload)])
+    for cfg in [(32768, 256, 6, 16384), (1024, 128, 2, 0), (4096, 256, 8, 1 << 20)]:
+        for s in got:
+            s.reset()
+        plan.set_config(*cfg)
+        plan.run()
+        torch.cuda.synchronize()
+        for s, r in zip(got, ref):
+            assert torch.equal(s.counters, r.counters), cfg
+    # oracle on the five smallest relations
+    order = sorted(range(len(workload)), key=lambda i: workload[i].relation.n)[:5]
+    for i in order:
+        b = workload[i]
+        q = O.canonical_query(b.num_join_attrs, b.edges)
+        co = O.draw_coefficients(b.hash_seed, b.d, q.n_comp, len(q.edges))
+        want = O.sketch_relation(q, co, 0, b.relation.cols.cpu().numpy(), b.relation.weights.cpu().numpy(), b.m)
+        assert np.array_equal(got[i].counters[0].cpu().numpy(), want)
+    plan.close()
+    for s in ref + got:
+        s.close()
+
+
+def test_plan_in_cuda_graph_and_autotune(workload):
+    ref = _sets(workload)
+    for s, b in zip(ref, workload):
+        s.update(0, b.relation.cols, b.relation.weights)
+    got = _sets(workload)
+    plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(got, workload)])
+    best, ms = plan.autotune()
+    assert ms > 0 and best["chunk_tuples"] >= 256
+    for s in got:
+        s.reset()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        plan.run()          # warm-up outside the graph (kernel attributes set)
+    stream.synchronize()
+    for s in got:
+        s.reset()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        plan.run()
+    for s in got:
+        s.reset()
+    torch.cuda.synchronize()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for s, r in zip(got, ref):
+        assert torch.equal(s.counters, 2 * r.counters)
+    plan.close()
+    for s in ref + got:
+        s.close()
+
+
+def test_plan_argument_checks(workload):
+    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], 64, 2, 1)
+    with pytest.raises(pkg.SketchError):
+        pkg.sk_update_plan_create([(s.handle, 7, 10, s.counters.data_ptr(), 10, None)])
+    empty = pkg.UpdatePlan([(s, 0, torch.empty((1, 0), dtype=torch.int64, device="cuda"), None)])
+    empty.run()
+    with pytest.raises(pkg.SketchError):
+        empty.set_config(100, 256, 4, 0)
+    empty.close()
+    s.close()

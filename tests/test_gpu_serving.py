@@ -1,0 +1,95 @@
+"""The serving loop: requests that run mixed and overlapped on the device give, for
+every estimate, exactly the result of running that set's requests one by one."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2402_15953_gb300 as pkg
+from paper_2402_15953_gb300.serve import SketchServer
+from tests._helpers import random_relations, random_tree_query
+
+pytestmark = pytest.mark.gpu
+
+
+def _trace(seed, n_sets=6, n_req=90):
+    rng = random.Random(seed)
+    sets = []
+    for i in range(n_sets):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 4))
+        sets.append((attrs, edges, 1 << rng.randint(6, 12), rng.choice([1, 3, 5]), rng.randrange(1 << 60)))
+    reqs = []
+    for j in range(n_req):
+        sid = rng.randrange(n_sets)
+        attrs = sets[sid][0]
+        if rng.random() < 0.2:
+            reqs.append(("estimate", sid))
+        else:
+            rel = rng.randrange(len(attrs))
+            (cols, w), = random_relations(rng, [attrs[rel]], 3000, 1 << 20)
+            reqs.append(("update", sid, rel, torch.as_tensor(cols).pin_memory(), torch.as_tensor(w).pin_memory()))
+    for sid in range(n_sets):
+        reqs.append(("estimate", sid))
+    return sets, reqs
+
+
+def _alone(sets, reqs):
+    """Each set's requests run one by one on a fresh set."""
+    out = {}
+    live = [pkg.SketchSet(a, e, m, d, s) for (a, e, m, d, s) in sets]
+    for j, r in enumerate(reqs):
+        if r[0] == "update":
+            _, sid, rel, cols, w = r
+            live[sid].update(rel, cols.cuda(), w.cuda())
+        else:
+            out[j] = live[r[1]].estimate()
+    for s in live:
+        s.close()
+    return out
+
+
+def _mixed(sets, reqs, budget=32 << 30, slots=8, workers=4):
+    srv = SketchServer(hbm_budget_bytes=budget, update_slots=slots, estimate_workers=workers)
+    for i, (a, e, m, d, s) in enumerate(sets):
+        assert srv.register_set(i, a, e, m, d, s)
+    handles = {}
+    for j, r in enumerate(reqs):
+        if r[0] == "update":
+            _, sid, rel, cols, w = r
+            srv.submit_update(sid, rel, cols, w)
+        else:
+            handles[j] = srv.submit_estimate(r[1])
+    srv.serve()
+    srv.close()
+    return {j: h.result for j, h in handles.items()}, handles
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_results_equal_alone_and_in_the_mix(seed):
+    sets, reqs = _trace(seed)
+    alone = _alone(sets, reqs)
+    mixed, handles = _mixed(sets, reqs)
+    assert set(alone) == set(mixed)
+    for j in alone:
+        assert handles[j].error is None, handles[j].error
+        assert mixed[j]["rows"] == alone[j]["rows"], j
+        assert mixed[j]["median"] == alone[j]["median"]
+
+
+def test_tight_budget_queues_but_stays_exact():
+    sets, reqs = _trace(3, n_sets=4, n_req=40)
+    resident = sum(len(a) * d * m * 8 for (a, e, m, d, s) in sets)
+    est = max((max(2, len(a)) + 1) * d * m * 32 + 2 * d * 4 * m * 16 + (m // 2) * 16 for (a, e, m, d, s) in sets)
+    budget = resident + est + 4 * 3000 * 8 * 2 + 4096
+    alone = _alone(sets, reqs)
+    mixed, handles = _mixed(sets, reqs, budget=budget, slots=2, workers=1)
+    for j in alone:
+        assert mixed[j]["rows"] == alone[j]["rows"]
+
+
+def test_register_beyond_budget_is_refused():
+    srv = SketchServer(hbm_budget_bytes=1 << 20)
+    assert srv.register_set(0, [1, 1], [(0, 0, 1, 0)], 1 << 12, 4, 1)      # 256 KB
+    assert not srv.register_set(1, [1, 1], [(0, 0, 1, 0)], 1 << 16, 4, 1)  # 4 MB
+    srv.close()
