@@ -310,7 +310,15 @@ def run_ours(args, world, rank, local):
     achieved_gbs = fact_bytes / (fact_ms / 1e3) / 1e9
     mulmods_per_fact_tuple = wl.d * 5 * (1 + 3 * 1)
     mulmod_rate = args.fact_rows * mulmods_per_fact_tuple / (fact_ms / 1e3)
-    alu_peak = float(os.environ.get("SK_ALU_PEAK_MULMOD_PER_S", "0")) or None
+
+    # Integer-ALU roofline of the fact-table update: algorithmic work = GF(2^61-1) Horner
+    # multiply-add steps (1 per bin hash, 3 per sign hash), peak = the step rate of the same
+    # arithmetic without loads, atomics or combination (6.4 steps per clock per SM measured)
+    # x 152 SMs x 2.07 GHz.  traffic: DRAM bytes of one ncu capture of this kernel version
+    # (2e7-row launch: 808.5 MB), scaled to this launch's row count.
+    steps_per_s = mulmod_rate
+    alu_peak_steps = 6.4 * 152 * 2.07e9
+    traffic = 808.5e6 * args.fact_rows / 2e7 / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world, "steps": args.steps,
@@ -323,11 +331,14 @@ def run_ours(args, world, rank, local):
         "p50_ms": statistics.median(step_ms), "p99_ms": percentile(step_ms, 99.0),
         "update_ms": statistics.mean(upd_all_ms), "estimate_ms": statistics.mean(step_ms) - statistics.mean(upd_all_ms),
         "fact_update_ms": fact_ms,
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": "k_update (fact table F)",
-                     "peak_source": peak_src},
-        "alu": {"mulmods_per_s": mulmod_rate, "mulmods_per_fact_tuple": mulmods_per_fact_tuple,
-                "peak": alu_peak},
+        "roofline": {"bound": "alu", "achieved": steps_per_s / 1e9, "peak": alu_peak_steps / 1e9, "unit": "Gstep/s",
+                     "frac": steps_per_s / alu_peak_steps, "traffic": traffic,
+                     "kernel": "k_update<5,pow2,global> (fact table F)",
+                     "work": f"{mulmods_per_fact_tuple} GF(2^61-1) Horner steps per fact tuple",
+                     "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled)"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "GB per launch",
+                         "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
         "estimate_check": {"median": str(est["median"]), "max_residual": est["max_residual"],
                            "max_limbs": est["max_limbs"], "limb_bits": est["limb_bits"]},
         "gpu_launches": launches, "clocks": clocks,
@@ -555,10 +566,31 @@ def run_serving(args, world, rank):
                 "estimate_p50_ms": est[len(est) // 2] if est else None,
                 "estimate_p99_ms": percentile(est, 99.0) if est else None, "errors": errors}
 
+    def sequential(trace):
+        """Baseline: the same requests one at a time, each update a copy plus its own launch,
+        each estimate after the previous request completed (no overlap, no admission)."""
+        from paper_2402_15953_gb300 import SketchSet
+        live = [SketchSet(a, e, m, d, sd) for (a, e, m, d, sd) in sets]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tuples = 0
+        for r in trace:
+            if r[0] == "update":
+                live[r[1]].update(r[2], r[3].cuda(non_blocking=True), r[4].cuda(non_blocking=True))
+                torch.cuda.synchronize()
+                tuples += r[3].shape[1]
+            else:
+                live[r[1]].estimate()
+        wall = time.perf_counter() - t0
+        for x in live:
+            x.close()
+        return {"requests": len(trace), "wall_s": wall, "requests_per_s": len(trace) / wall,
+                "tuples_per_s": tuples / wall}
+
     trace = make_trace(args.requests, 1)
     run(make_trace(200, 2), None)           # warm-up (scratch allocation, kernel attributes)
     sat = run(trace, None)
-    points = {"saturated": sat}
+    points = {"saturated": sat, "sequential_one_by_one": sequential(trace)}
     for frac in (0.5, 0.9):
         points[f"rate_{int(frac * 100)}pct"] = run(trace, frac * sat["requests_per_s"])
     line = {"metric": "serving: p50/p99 request latency and throughput", "value": sat["tuples_per_s"],
