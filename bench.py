@@ -345,7 +345,10 @@ def run_ours(args, world, rank, local):
     }
 
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, s, wl, stream, world)
+        staged = run_e2e(args, s, wl, stream, world)
+        direct = run_e2e_direct(args, s, wl, stream, world)
+        line["e2e"] = direct if direct["value"] >= staged["value"] else staged
+        line["e2e_alternatives"] = {"staged_copies": staged, "direct_host_reads": direct}
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ns = min(args.cpu_sample_tuples, args.fact_rows)
         cols = [c[:, :ns].cpu().numpy() for c in rels]
@@ -408,7 +411,7 @@ def run_e2e(args, s, wl, stream, world):
     d = wl.d
     d2h = 4 * (8 + 3 * d * 32 + 8) + 2 * d * 32 + 4
     return {"value": world * total / dt, "unit": "tuples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": dt * 1e3, "steps": steps}
+            "ms_per_step": dt * 1e3, "steps": steps, "method": "pipelined cudaMemcpyAsync of 8M-row chunks"}
 
 
 def run_batched(args, world, rank):
@@ -603,6 +606,41 @@ def run_serving(args, world, rank):
             "points": points}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_e2e_direct(args, s, wl, stream, world):
+    """Same steps through the C ABI with the key columns in page-locked host memory passed
+    straight to sk_sketch_update_batch: the update kernel reads them across the host link
+    (NVLink-C2C on Grace-Blackwell), so the host-to-device transfer happens inside the
+    kernel; the estimate is read back as usual."""
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    host = [r.cols.cpu().pin_memory() for r in wl.relations]
+    h2d = sum(h.numel() * 8 for h in host)
+    sid = stream.cuda_stream
+
+    def step():
+        s.reset()
+        for k, h in enumerate(host):
+            pkg.sk_sketch_update_batch(s.handle, k, int(h.shape[1]), h.data_ptr(), int(h.stride(0)), None, None, sid)
+        return s.estimate()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    steps = max(3, args.steps // 3)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+    total = sum(h.shape[1] for h in host)
+    d = wl.d
+    d2h = 4 * (256 + (1 + 3 * d) * 8) + 2 * d * 32 + 4
+    return {"value": world * total / dt, "unit": "tuples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": steps, "method": "kernels read pinned host columns directly"}
 
 
 def main():

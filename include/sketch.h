@@ -13,8 +13,9 @@
  * Conventions for every function
  *   - Returns an sk_status: SK_OK (0) or a negative error code; never throws,
  *     never aborts.  sk_status_string() names a code.
- *   - "dev_" pointers are CUDA device pointers (or managed memory) on the
- *     current device; every other pointer is host memory.
+ *   - "dev_" pointers are CUDA device pointers on the current device, managed
+ *     memory, or page-locked host memory (cudaHostAlloc / registered), which the
+ *     kernels then read across the host link; every other pointer is host memory.
  *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it and is asynchronous unless stated.
  *   - The caller owns every buffer it passes (counters, columns, weights) and

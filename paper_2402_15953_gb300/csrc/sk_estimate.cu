@@ -162,19 +162,37 @@ __device__ __forceinline__ void record(int* status, int code) { atomicCAS(status
 // ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
-__global__ void k_leaf(I256* __restrict__ dst, const int64_t* __restrict__ src, int64_t n) {
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step)
-    dst[i] = i256_from_i64(src[i]);
+// max over the block's values of `bits`, added to *out with atomicMax (out may be null)
+__device__ __forceinline__ void block_max_bits(int bits, int* out) {
+  if (!out) return;
+  for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+  if ((threadIdx.x & 31) == 0 && bits > 0) atomicMax(out, bits);
 }
 
-__global__ void k_hadamard(I256* __restrict__ x, const I256* __restrict__ y, int64_t n, int* status) {
+__global__ void k_leaf(I256* __restrict__ dst, const int64_t* __restrict__ src, int64_t n, int* bits_out) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int best = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    const int64_t v = src[i];
+    const uint64_t a = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
+    best = max(best, a ? 64 - __clzll((long long)a) : 0);
+    dst[i] = i256_from_i64(v);
+  }
+  block_max_bits(best, bits_out);
+}
+
+__global__ void k_hadamard(I256* __restrict__ x, const I256* __restrict__ y, int64_t n, int* status,
+                           int* bits_out) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int best = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
     const I256 a = x[i], b = y[i];
     if (i256_bits(a) + i256_bits(b) > 255) record(status, SK_ERR_OVERFLOW);
-    x[i] = i256_mul(a, b);
+    const I256 z = i256_mul(a, b);
+    best = max(best, i256_bits(z));
+    x[i] = z;
   }
+  block_max_bits(best, bits_out);
 }
 
 __global__ void k_maxbits(const I256* __restrict__ v, int64_t n, int* out) {
@@ -416,7 +434,21 @@ struct CorrArgs {
   int nf, ni;
   int* status;
   unsigned long long* residual;   // max |y - rint(y)| as double bits
+  unsigned long long* sums;       // optional [d][3]: row sums mod 2^64 of a, x, z
+  int* zbits;                     // optional: bit length of max |z|
 };
+
+// Adds v (one value of row `row`) to sums[row * 3 + col] mod 2^64; warps whose 32 indices lie
+// in one row (m >= 32) reduce first.
+__device__ __forceinline__ void row_sum_add(unsigned long long* sums, int64_t m, int64_t row, int col,
+                                            unsigned long long v) {
+  if (m >= 32) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sums + row * 3 + col, v);
+  } else {
+    atomicAdd(sums + row * 3 + col, v);
+  }
+}
 
 // Real vector number q of the forward batch: q < La -> limb q of a, else limb q-La of x.
 // Packed complex vector t holds real vectors 2t (real part) and 2t+1 (imaginary part).
@@ -427,6 +459,10 @@ __global__ void k_split(CorrArgs p) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
     const int64_t row = g / p.m, j = g % p.m;
     double2* F = p.F + (row * p.nf) * p.m + j;
+    if (p.sums) {
+      row_sum_add(p.sums, p.m, row, 0, p.a[g].w[0]);
+      row_sum_add(p.sums, p.m, row, 1, p.x[g].w[0]);
+    }
     for (int which = 0; which < 2; which++) {
       I256 v = which == 0 ? p.a[g] : p.x[g];
       const int L = which == 0 ? p.La : p.Lx;
@@ -500,6 +536,7 @@ __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
   const double inv_m = 1.0 / (double)p.m;
   const int ns = p.La + p.Lx - 1;
   double worst = 0.0;
+  int zb = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
     const int64_t row = g / p.m, j = g % p.m;
     const double2* y = Y + (row * p.ni) * p.m + j;
@@ -513,9 +550,12 @@ __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
       z = i256_add(z, i256_shl_i64((int64_t)rv, p.B * s));
     }
     p.z[g] = z;
+    if (p.sums) row_sum_add(p.sums, p.m, row, 2, z.w[0]);
+    zb = max(zb, i256_bits(z));
   }
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
   if ((threadIdx.x & 31) == 0) atomicMax(p.residual, (unsigned long long)__double_as_longlong(worst));
+  block_max_bits(zb, p.zbits);
 }
 
 // ---------------------------------------------------------------------------
@@ -621,168 +661,8 @@ void free_estimator(sk_set* s) {
   s->twiddle_m = 0;
 }
 
-sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
-  const int64_t m = s->m;
-  const int d = s->d;
-  const int64_t dm = (int64_t)d * m;
-  const int logm = ilog2(m);
-  // slots (+1 spare for correlation outputs) and small buffers
-  const int nslots = s->n_slots + 1;
-  const size_t slot_bytes = (size_t)dm * sizeof(I256);
-  const size_t small_off = slot_bytes * nslots;
-  const size_t small_bytes = 4 * SK_MAX_ROWS * sizeof(I256) + 64;
-  SK_CK(ensure(s->scratch, small_off + small_bytes, st));
-  if (s->twiddle_m != m) {
-    if (s->d_twiddle) cudaFree(s->d_twiddle);
-    s->d_twiddle = nullptr;
-    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(m / 2) * sizeof(double2)));
-    s->twiddle_m = m;
-    k_twiddle<<<grid_for(m / 2), 256, 0, st>>>((double2*)s->d_twiddle, m);
-    count_launch();
-    SK_CK(cudaGetLastError());
-  }
-  const double2* tw = (const double2*)s->d_twiddle;
-  char* base = (char*)s->scratch.ptr;
-  std::vector<int> phys(nslots);
-  for (int i = 0; i < nslots; i++) phys[i] = i;
-  auto slot = [&](int i) { return (I256*)(base + slot_bytes * phys[i]); };
-  const int spare = nslots - 1;
-  I256* d_sa = (I256*)(base + small_off);
-  I256* d_sx = d_sa + SK_MAX_ROWS;
-  I256* d_sz = d_sx + SK_MAX_ROWS;
-  I256* d_sorted = d_sz + SK_MAX_ROWS;
-  int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);
-  unsigned long long* d_resid = (unsigned long long*)(d_bits + 4);
-
-  double max_resid = 0.0;
-  int max_limbs = 0, last_B = 0, retries = 0;
-  const int eg = grid_for(dm);
-
-  for (const EstOp& op : s->plan) {
-    if (op.kind == OP_LEAF) {
-      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm);
-      count_launch();
-      SK_CK(cudaGetLastError());
-    } else if (op.kind == OP_HAD) {
-      k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status);
-      count_launch();
-      SK_CK(cudaGetLastError());
-    } else if (op.kind == OP_CORR) {
-      I256* x = slot(op.dst);
-      I256* a = slot(op.src);
-      SK_CK(cudaMemsetAsync(d_bits, 0, 2 * sizeof(int), st));
-      k_maxbits<<<eg, 256, 0, st>>>(a, dm, d_bits);
-      count_launch();
-      k_maxbits<<<eg, 256, 0, st>>>(x, dm, d_bits + 1);
-      count_launch();
-      k_rowsum<<<d, 1024, 0, st>>>(a, m, d_sa);
-      count_launch();
-      k_rowsum<<<d, 1024, 0, st>>>(x, m, d_sx);
-      count_launch();
-      SK_CK(cudaGetLastError());
-      int hb[2];
-      SK_CK(cudaMemcpyAsync(hb, d_bits, sizeof(hb), cudaMemcpyDeviceToHost, st));
-      SK_CK(cudaStreamSynchronize(st));
-      if (hb[0] == 0 || hb[1] == 0) {
-        SK_CK(cudaMemsetAsync(x, 0, slot_bytes, st));
-        continue;
-      }
-      if (hb[0] + hb[1] + logm + 1 > 255) return SK_ERR_OVERFLOW;
-      std::vector<I256> sa(d), sx(d), sz(d);
-      SK_CK(cudaMemcpyAsync(sa.data(), d_sa, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
-      SK_CK(cudaMemcpyAsync(sx.data(), d_sx, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
-      int B = limb_bits_for(m, 1);
-      bool done = false;
-      for (int attempt = 0; attempt < 4 && !done; attempt++) {
-        int La = 0, Lx = 0;
-        for (;;) {
-          La = (hb[0] + 2 + B - 1) / B;
-          Lx = (hb[1] + 2 + B - 1) / B;
-          const int nb = limb_bits_for(m, std::min(La, Lx));
-          if (nb >= B) break;
-          B = nb;
-        }
-        if (attempt > 0) {
-          B = std::max(2, B - 3 * attempt);
-          La = (hb[0] + 2 + B - 1) / B;
-          Lx = (hb[1] + 2 + B - 1) / B;
-        }
-        if (La > kMaxLimbs || Lx > kMaxLimbs) return SK_ERR_INEXACT;
-        CorrArgs p;
-        p.a = a;
-        p.x = x;
-        p.z = slot(spare);
-        p.m = m;
-        p.logm = logm;
-        p.d = d;
-        p.B = B;
-        p.La = La;
-        p.Lx = Lx;
-        p.nf = (La + Lx + 1) / 2;
-        p.ni = (La + Lx) / 2;
-        p.status = s->d_status;
-        p.residual = d_resid;
-        const size_t fbytes = (size_t)d * p.nf * m * sizeof(double2);
-        SK_CK(ensure(s->fft_scratch, 2 * fbytes, st));
-        double2* bufA = (double2*)s->fft_scratch.ptr;
-        double2* bufB = bufA + (size_t)d * p.nf * m;
-        p.F = bufA;
-        SK_CK(cudaMemsetAsync(d_resid, 0, sizeof(unsigned long long), st));
-        k_split<<<eg, 256, 0, st>>>(p);
-        count_launch();
-        SK_CK(cudaGetLastError());
-        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, m, tw, false, st);
-        if (fs != SK_OK) return fs;
-        p.F = bufB;
-        p.G = bufA;
-        k_product<<<eg, 128, 0, st>>>(p);
-        count_launch();
-        SK_CK(cudaGetLastError());
-        fs = fft(bufA, bufB, (int64_t)d * p.ni, m, tw, true, st);
-        if (fs != SK_OK) return fs;
-        k_recombine<<<eg, 256, 0, st>>>(p, bufB);
-        count_launch();
-        k_rowsum<<<d, 1024, 0, st>>>(p.z, m, d_sz);
-        count_launch();
-        SK_CK(cudaGetLastError());
-        unsigned long long rbits = 0;
-        SK_CK(cudaMemcpyAsync(&rbits, d_resid, sizeof(rbits), cudaMemcpyDeviceToHost, st));
-        SK_CK(cudaMemcpyAsync(sz.data(), d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
-        SK_CK(cudaStreamSynchronize(st));
-        double resid;
-        std::memcpy(&resid, &rbits, sizeof(resid));
-        bool ok = resid <= 0.25;
-        for (int r = 0; r < d && ok; r++) ok = i256_eq(sz[r], HostI256::mul(sa[r], sx[r]));
-        max_resid = std::max(max_resid, resid);
-        max_limbs = std::max(max_limbs, std::max(La, Lx));
-        last_B = B;
-        if (ok) {
-          std::swap(phys[op.dst], phys[spare]);
-          done = true;
-        } else {
-          retries++;
-        }
-      }
-      if (!done) return SK_ERR_INEXACT;
-    } else {  // OP_SUM
-      k_rowsum<<<d, 1024, 0, st>>>(slot(op.dst), m, d_sz);
-      count_launch();
-      k_sort_rows<<<1, 32, 0, st>>>(d_sz, d, d_sorted);
-      count_launch();
-      SK_CK(cudaGetLastError());
-    }
-  }
-  std::vector<I256> rows(d), sorted(d);
-  int status = 0;
-  SK_CK(cudaMemcpyAsync(rows.data(), d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
-  SK_CK(cudaMemcpyAsync(sorted.data(), d_sorted, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
-  SK_CK(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  SK_CK(cudaStreamSynchronize(st));
-  if (status != 0) {
-    SK_CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
-    SK_CK(cudaStreamSynchronize(st));
-    return (sk_status)status;
-  }
+// Fills *out from the d row values and their sorted copy.
+void fill_estimate(sk_estimate* out, const I256* rows, const I256* sorted, int d) {
   auto to_double = [](const I256& v) {
     const bool neg = i256_neg_p(v);
     const I256 a = neg ? i256_neg(v) : v;
@@ -801,12 +681,193 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   out->median_f64 = to_double(med);
   out->mid_mean_f64 = (d & 1) ? to_double(sorted[d / 2])
                               : 0.5 * (to_double(sorted[d / 2 - 1]) + to_double(sorted[d / 2]));
-  out->max_residual = max_resid;
-  out->max_limbs = max_limbs;
-  out->limb_bits = last_B;
-  out->corr_steps = s->corr_steps;
-  out->retries = retries;
-  return SK_OK;
+}
+
+// Algorithm 3 over the schedule.  One host round trip per correlation step: before a
+// step the host reads the bit lengths of its two operands (written by the kernels that
+// produced them) together with the previous step's certificate (largest rounding
+// residual and the row sums of a, x and z modulo 2^64, whose identity
+// sum z = (sum a)(sum x) holds exactly in Z/2^64).  A failed certificate restarts the
+// schedule with narrower limbs for that step.
+sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
+  const int64_t m = s->m;
+  const int d = s->d;
+  const int64_t dm = (int64_t)d * m;
+  const int logm = ilog2(m);
+  const int nslots = s->n_slots + 1;
+  const int ncorr = std::max(1, s->corr_steps);
+  const size_t slot_bytes = (size_t)dm * sizeof(I256);
+  const size_t small_off = slot_bytes * nslots;
+  // small buffers: rows, sorted rows (I256 [64] each) | slot bits (int [nslots]) | per step:
+  // residual (u64) and row sums (u64 [d][3])
+  const size_t cert_words = (size_t)ncorr * (1 + 3 * (size_t)d);
+  const size_t small_bytes = 2 * SK_MAX_ROWS * sizeof(I256) + 256 + cert_words * 8 + 64;
+  SK_CK(ensure(s->scratch, small_off + small_bytes, st));
+  if (s->twiddle_m != m) {
+    if (s->d_twiddle) cudaFree(s->d_twiddle);
+    s->d_twiddle = nullptr;
+    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(m / 2) * sizeof(double2)));
+    s->twiddle_m = m;
+    k_twiddle<<<grid_for(m / 2), 256, 0, st>>>((double2*)s->d_twiddle, m);
+    count_launch();
+    SK_CK(cudaGetLastError());
+  }
+  const double2* tw = (const double2*)s->d_twiddle;
+  char* base = (char*)s->scratch.ptr;
+  I256* d_rows = (I256*)(base + small_off);
+  I256* d_sorted = d_rows + SK_MAX_ROWS;
+  int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);                           // [nslots] (<= 64)
+  unsigned long long* d_cert = (unsigned long long*)((char*)d_bits + 256);  // [ncorr][1 + 3d]
+  const int eg = grid_for(dm);
+  if (nslots > 64) return SK_ERR_INVALID_ARG;
+
+  std::vector<int> bmax(ncorr, 64);     // per-step cap on the limb width (lowered on failure)
+  std::vector<unsigned long long> cert((size_t)ncorr * (1 + 3 * (size_t)d));
+  int retries = 0;
+  for (int attempt = 0; attempt < 4; attempt++) {
+    std::vector<int> phys(nslots);
+    for (int i = 0; i < nslots; i++) phys[i] = i;
+    auto slot = [&](int i) { return (I256*)(base + slot_bytes * phys[i]); };
+    const int spare = nslots - 1;
+    SK_CK(cudaMemsetAsync(d_bits, 0, 256, st));
+    SK_CK(cudaMemsetAsync(d_cert, 0, cert_words * 8, st));
+    std::vector<int> step_B(ncorr, 0);
+    double max_resid = 0.0;
+    int max_limbs = 0, last_B = 0, corr = 0;
+    int failed = -1;
+    // checks the certificate of every step < upto whose values are in `cert`
+    auto check = [&](int upto) {
+      for (int t = 0; t < upto && failed < 0; t++) {
+        const unsigned long long* c = cert.data() + (size_t)t * (1 + 3 * d);
+        double resid;
+        std::memcpy(&resid, &c[0], sizeof(resid));
+        max_resid = std::max(max_resid, resid);
+        bool ok = resid <= 0.25;
+        for (int r = 0; r < d && ok; r++) ok = c[1 + 3 * r + 2] == c[1 + 3 * r] * c[1 + 3 * r + 1];
+        if (!ok) failed = t;
+      }
+    };
+    for (const EstOp& op : s->plan) {
+      if (failed >= 0) break;
+      if (op.kind == OP_LEAF) {
+        SK_CK(cudaMemsetAsync(d_bits + phys[op.dst], 0, sizeof(int), st));
+        k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm, d_bits + phys[op.dst]);
+        count_launch();
+        SK_CK(cudaGetLastError());
+      } else if (op.kind == OP_HAD) {
+        SK_CK(cudaMemsetAsync(d_bits + phys[op.dst], 0, sizeof(int), st));
+        k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status, d_bits + phys[op.dst]);
+        count_launch();
+        SK_CK(cudaGetLastError());
+      } else if (op.kind == OP_CORR) {
+        I256* x = slot(op.dst);
+        I256* a = slot(op.src);
+        int hb[64];
+        SK_CK(cudaMemcpyAsync(hb, d_bits, sizeof(int) * nslots, cudaMemcpyDeviceToHost, st));
+        if (corr > 0)
+          SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * (1 + 3 * d) * 8, cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaStreamSynchronize(st));
+        check(corr);
+        if (failed >= 0) break;
+        const int bits_a = hb[phys[op.src]], bits_x = hb[phys[op.dst]];
+        unsigned long long* cert_t = d_cert + (size_t)corr * (1 + 3 * d);
+        if (bits_a == 0 || bits_x == 0) {
+          SK_CK(cudaMemsetAsync(x, 0, slot_bytes, st));
+          SK_CK(cudaMemsetAsync(d_bits + phys[op.dst], 0, sizeof(int), st));
+          corr++;                       // an all-zero step certifies trivially (sums 0, residual 0)
+          continue;
+        }
+        if (bits_a + bits_x + logm + 1 > 255) return SK_ERR_OVERFLOW;
+        int B = std::min(limb_bits_for(m, 1), bmax[corr]);
+        int La = 0, Lx = 0;
+        for (;;) {
+          La = (bits_a + 2 + B - 1) / B;
+          Lx = (bits_x + 2 + B - 1) / B;
+          const int nb = std::min(limb_bits_for(m, std::min(La, Lx)), bmax[corr]);
+          if (nb >= B) break;
+          B = nb;
+        }
+        if (La > kMaxLimbs || Lx > kMaxLimbs) return SK_ERR_INEXACT;
+        CorrArgs p;
+        p.a = a;
+        p.x = x;
+        p.z = slot(spare);
+        p.m = m;
+        p.logm = logm;
+        p.d = d;
+        p.B = B;
+        p.La = La;
+        p.Lx = Lx;
+        p.nf = (La + Lx + 1) / 2;
+        p.ni = (La + Lx) / 2;
+        p.status = s->d_status;
+        p.residual = cert_t;
+        p.sums = cert_t + 1;
+        p.zbits = d_bits + phys[spare];
+        const size_t fbytes = (size_t)d * p.nf * m * sizeof(double2);
+        SK_CK(ensure(s->fft_scratch, 2 * fbytes, st));
+        double2* bufA = (double2*)s->fft_scratch.ptr;
+        double2* bufB = bufA + (size_t)d * p.nf * m;
+        p.F = bufA;
+        SK_CK(cudaMemsetAsync(p.zbits, 0, sizeof(int), st));
+        k_split<<<eg, 256, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, m, tw, false, st);
+        if (fs != SK_OK) return fs;
+        p.F = bufB;
+        p.G = bufA;
+        k_product<<<eg, 128, 0, st>>>(p);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        fs = fft(bufA, bufB, (int64_t)d * p.ni, m, tw, true, st);
+        if (fs != SK_OK) return fs;
+        k_recombine<<<eg, 256, 0, st>>>(p, bufB);
+        count_launch();
+        SK_CK(cudaGetLastError());
+        std::swap(phys[op.dst], phys[spare]);
+        step_B[corr] = B;
+        max_limbs = std::max(max_limbs, std::max(La, Lx));
+        last_B = B;
+        corr++;
+      } else {  // OP_SUM
+        k_rowsum<<<d, 1024, 0, st>>>(slot(op.dst), m, d_rows);
+        count_launch();
+        k_sort_rows<<<1, 32, 0, st>>>(d_rows, d, d_sorted);
+        count_launch();
+        SK_CK(cudaGetLastError());
+      }
+    }
+    if (failed < 0) {
+      I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
+      int status = 0;
+      SK_CK(cudaMemcpyAsync(rows, d_rows, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaMemcpyAsync(sorted, d_sorted, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (corr > 0)
+        SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * (1 + 3 * d) * 8, cudaMemcpyDeviceToHost, st));
+      SK_CK(cudaStreamSynchronize(st));
+      check(corr);
+      if (failed < 0) {
+        if (status != 0) {
+          SK_CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
+          SK_CK(cudaStreamSynchronize(st));
+          return (sk_status)status;
+        }
+        fill_estimate(out, rows, sorted, d);
+        out->max_residual = max_resid;
+        out->max_limbs = max_limbs;
+        out->limb_bits = last_B;
+        out->corr_steps = s->corr_steps;
+        out->retries = retries;
+        return SK_OK;
+      }
+    }
+    // a step failed its certificate: redo everything with narrower limbs there
+    retries++;
+    bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(m, 1)) - 3);
+  }
+  return SK_ERR_INEXACT;
 }
 
 // ===========================================================================
@@ -896,11 +957,11 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
 
   for (const EstOp& op : s->plan) {
     if (op.kind == OP_LEAF) {
-      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm);
+      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm, nullptr);
       count_launch();
       SK_CK(cudaGetLastError());
     } else if (op.kind == OP_HAD) {
-      k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status);
+      k_hadamard<<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dm, s->d_status, nullptr);
       count_launch();
       SK_CK(cudaGetLastError());
     } else if (op.kind == OP_CORR) {
@@ -957,6 +1018,8 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
         p.ni = (La + Lx) / 2;
         p.status = s->d_status;
         p.residual = d_resid;
+        p.sums = nullptr;
+        p.zbits = nullptr;
         const size_t fbytes = align256((size_t)d * p.nf * m * sizeof(double2));
         if (2 * fbytes > fft_room) return SK_ERR_SCRATCH_TOO_SMALL;
         double2* bufA = (double2*)(slot_base + slot_bytes * nslots);
