@@ -24,6 +24,7 @@ struct UpdArgs {
   int64_t dom[kMaxAttrs];
   int* status;
   int64_t smem_wmax;         // |Delta| <= smem_wmax goes to the int32 sub-sketch
+  int agg;                   // warp-aggregate shared-memory counter updates
 };
 
 __device__ __forceinline__ uint64_t field_of(int64_t key) {
@@ -94,23 +95,31 @@ __device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
 // A = number of attributes when known at compile time (1..4), 0 = runtime a.
 // Algorithm 2 for tuple i: all d rows hashed in registers, one counter update per row
 // (int32 shared-memory sub-sketch when SMEM and |Delta| is small, int64 global otherwise).
-template <int A, bool POW2, bool SMEM>
-__device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s_coef, int* s_sub, int64_t i) {
+//
+// AGG (shared-memory path only): the whole warp calls this for 32 consecutive tuples,
+// `live` false past the end; lanes that add to the same shared counter are grouped with
+// __match_any_sync and their values summed with __reduce_add_sync, so each distinct
+// counter receives one atomic per warp (hot keys of skewed columns otherwise serialise
+// on one shared-memory address).  Lanes past the end or with a key outside the declared
+// domain take part with Delta = 0.
+template <int A, bool POW2, bool SMEM, bool AGG = false>
+__device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s_coef, int* s_sub, int64_t i,
+                                             bool live = true) {
   const int na = A > 0 ? A : p.a;
   uint64_t x[A > 0 ? A : kMaxAttrs];
   bool ok = true;
 #pragma unroll
   for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
     if (A == 0 && u >= na) break;
-    const int64_t key = __ldg(p.cols + (int64_t)u * p.stride + i);
-    if (p.has_dom && (key < 0 || key >= p.dom[u])) ok = false;
+    const int64_t key = (!AGG || live) ? __ldg(p.cols + (int64_t)u * p.stride + i) : 0;
+    if (p.has_dom && (!AGG || live) && (key < 0 || key >= p.dom[u])) ok = false;
     x[u] = field_of(key);
   }
   if (!ok) {
     record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
-    return;
+    if (!AGG) return;
   }
-  const int64_t delta = p.w ? __ldg(p.w + i) : 1;
+  const int64_t delta = (AGG && (!live || !ok)) ? 0 : (p.w ? __ldg(p.w + i) : 1);
   const bool small = SMEM && (delta <= p.smem_wmax && delta >= -p.smem_wmax);
   bool narrow = true;
 #pragma unroll
@@ -169,7 +178,14 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
     }
     bin = reduce_m<POW2>(bin, p.m);
     const int64_t v = sbit ? -delta : delta;
-    if (SMEM && small) {
+    if (AGG) {
+      const unsigned lane = threadIdx.x & 31u;
+      const unsigned key = small ? (unsigned)(row * p.m + bin) : 0xffffffffu - lane;
+      const unsigned same = __match_any_sync(0xffffffffu, key);
+      const int sum = __reduce_add_sync(same, small ? (int)v : 0);
+      if (small && lane == (unsigned)(__ffs(same) - 1) && sum != 0) atomicAdd(s_sub + key, sum);
+      if (!small && v != 0) atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
+    } else if (SMEM && small) {
       atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
     } else {
       atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
