@@ -118,7 +118,8 @@ sk_status sk_sketch_bytes(const sk_query* query, int64_t m, int32_t d, size_t* b
  * function per join (SplitMix64 from `seed`, each coefficient an element of
  * GF(2^61 - 1)), uploads them, and zeroes the caller's counters buffer
  * (dev_counters, `bytes` >= sk_sketch_bytes) on cuda_stream.
- * 1 <= m <= 2^30 (the estimator additionally needs m a power of two, 2..2^22);
+ * 1 <= m <= 2^30 (the estimator needs 2 <= m <= 2^22, or <= 2^21 when m is not a
+ * power of two);
  * 1 <= d <= SK_MAX_ROWS.  *out receives the handle.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CYCLIC_QUERY, SK_ERR_DISCONNECTED_QUERY,
  * SK_ERR_SELF_EDGE, SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_BUFFER_TOO_SMALL,
@@ -203,7 +204,9 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
  * Root attribute: attribute 0 of relation 0.  Each circular cross-correlation
  * IFFT(conj(FFT(a)) o FFT(x)) is computed with FP64 FFTs on signed limbs of the
  * exact operands and rounded back to exact integers; Hadamard products and sums
- * are exact signed 256-bit integers.  Requires m a power of two, 2 <= m <= 2^22.
+ * are exact signed 256-bit integers.  2 <= m <= 2^22 for a power of two m; any other
+ * 2 <= m <= 2^21 is handled with zero-padded transforms of the next power of two >= 2m - 1
+ * (the circular correlation mod m is the padded linear correlation folded back).
  * Synchronises cuda_stream and fills *out (host memory).
  * Errors: SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_OVERFLOW, SK_ERR_INEXACT,
  * SK_ERR_KEY_OUT_OF_DOMAIN (from earlier updates), SK_ERR_CUDA, SK_ERR_NO_MEMORY. */

@@ -353,7 +353,8 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream) {
 sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream) {
   if (!set || !out) return SK_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
-  if (set->m < 2 || set->m > (1ll << 22) || (set->m & (set->m - 1))) return SK_ERR_UNSUPPORTED_WIDTH;
+  const bool pow2 = (set->m & (set->m - 1)) == 0;
+  if (set->m < 2 || set->m > (pow2 ? (1ll << 22) : (1ll << 21))) return SK_ERR_UNSUPPORTED_WIDTH;
   return run_estimate(set, out, (cudaStream_t)cuda_stream);
 }
 

@@ -436,13 +436,15 @@ struct CorrArgs {
   unsigned long long* residual;   // max |y - rint(y)| as double bits
   unsigned long long* sums;       // optional [d][3]: row sums mod 2^64 of a, x, z
   int* zbits;                     // optional: bit length of max |z|
+  int64_t M;                      // FFT length: m for power-of-two m, else a power of two >= 2m - 1
 };
 
-// Adds v (one value of row `row`) to sums[row * 3 + col] mod 2^64; warps whose 32 indices lie
-// in one row (m >= 32) reduce first.
-__device__ __forceinline__ void row_sum_add(unsigned long long* sums, int64_t m, int64_t row, int col,
+// Adds v (one value of row `row`) to sums[row * 3 + col] mod 2^64.  With warp_rows the
+// caller guarantees that the 32 lanes of every warp are active and in one row, and the
+// warp reduces first.
+__device__ __forceinline__ void row_sum_add(unsigned long long* sums, bool warp_rows, int64_t row, int col,
                                             unsigned long long v) {
-  if (m >= 32) {
+  if (warp_rows) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(sums + row * 3 + col, v);
   } else {
@@ -452,19 +454,28 @@ __device__ __forceinline__ void row_sum_add(unsigned long long* sums, int64_t m,
 
 // Real vector number q of the forward batch: q < La -> limb q of a, else limb q-La of x.
 // Packed complex vector t holds real vectors 2t (real part) and 2t+1 (imaginary part).
+// Limb split over the FFT length M: positions j >= m (zero padding when m is not a
+// power of two) get zero limbs.
 __global__ void k_split(CorrArgs p) {
-  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t half = 1ll << (p.B - 1), full = 1ll << p.B;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.m, j = g % p.m;
-    double2* F = p.F + (row * p.nf) * p.m + j;
+    const int64_t row = g / p.M, j = g % p.M;
+    double2* F = p.F + (row * p.nf) * p.M + j;
+    const bool in = j < p.m;
+    const int64_t e = row * p.m + j;
     if (p.sums) {
-      row_sum_add(p.sums, p.m, row, 0, p.a[g].w[0]);
-      row_sum_add(p.sums, p.m, row, 1, p.x[g].w[0]);
+      row_sum_add(p.sums, p.M >= 32, row, 0, in ? p.a[e].w[0] : 0ull);
+      row_sum_add(p.sums, p.M >= 32, row, 1, in ? p.x[e].w[0] : 0ull);
+    }
+    if (!in) {
+      const int nreal = p.La + p.Lx;
+      for (int t = 0; t < (nreal + 1) / 2; t++) F[(int64_t)t * p.M] = make_double2(0.0, 0.0);
+      continue;
     }
     for (int which = 0; which < 2; which++) {
-      I256 v = which == 0 ? p.a[g] : p.x[g];
+      I256 v = which == 0 ? p.a[e] : p.x[e];
       const int L = which == 0 ? p.La : p.Lx;
       const int base = which == 0 ? 0 : p.La;
       for (int l = 0; l < L; l++) {
@@ -473,29 +484,29 @@ __global__ void k_split(CorrArgs p) {
         v = i256_add(v, i256_from_i64(-dig));
         v = i256_sar(v, p.B);
         const int q = base + l;
-        double* slot = (double*)(F + (int64_t)(q >> 1) * p.m) + (q & 1);
+        double* slot = (double*)(F + (int64_t)(q >> 1) * p.M) + (q & 1);
         *slot = (double)dig;
       }
       if (v.w[0] | v.w[1] | v.w[2] | v.w[3]) record(p.status, SK_ERR_OVERFLOW);
     }
     const int nreal = p.La + p.Lx;
-    if (nreal & 1) ((double*)(F + (int64_t)(nreal >> 1) * p.m))[1] = 0.0;
+    if (nreal & 1) ((double*)(F + (int64_t)(nreal >> 1) * p.M))[1] = 0.0;
   }
 }
 
 __global__ void k_product(CorrArgs p) {
-  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.m, k = g % p.m;
-    const int64_t mk = (p.m - k) & (p.m - 1);
-    const double2* F = p.F + (row * p.nf) * p.m;
+    const int64_t row = g / p.M, k = g % p.M;
+    const int64_t mk = (p.M - k) & (p.M - 1);
+    const double2* F = p.F + (row * p.nf) * p.M;
     double2 A[kMaxLimbs], X[kMaxLimbs];
     const int nreal = p.La + p.Lx;
     for (int q = 0; q < nreal; q++) {
       const int t = q >> 1;
-      const double2 zk = F[(int64_t)t * p.m + k];
-      const double2 zm = F[(int64_t)t * p.m + mk];
+      const double2 zk = F[(int64_t)t * p.M + k];
+      const double2 zm = F[(int64_t)t * p.M + mk];
       // Z = FFT(u + i v): U[k] = (Z[k] + conj Z[-k]) / 2, V[k] = (Z[k] - conj Z[-k]) / (2i)
       double2 s;
       if ((q & 1) == 0) {
@@ -506,7 +517,7 @@ __global__ void k_product(CorrArgs p) {
       }
       if (q < p.La) A[q] = s; else X[q - p.La] = s;
     }
-    double2* G = p.G + (row * p.ni) * p.m + k;
+    double2* G = p.G + (row * p.ni) * p.M + k;
     const int ns = p.La + p.Lx - 1;
     for (int t = 0; t < p.ni; t++) {
       double2 P[2];
@@ -525,7 +536,7 @@ __global__ void k_product(CorrArgs p) {
         P[h] = make_double2(re, im);
       }
       // pack the two real-output spectra: IFFT(P0 + i P1) = y0 + i y1
-      G[(int64_t)t * p.m] = make_double2(P[0].x - P[1].y, P[0].y + P[1].x);
+      G[(int64_t)t * p.M] = make_double2(P[0].x - P[1].y, P[0].y + P[1].x);
     }
   }
 }
@@ -533,24 +544,30 @@ __global__ void k_product(CorrArgs p) {
 __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
   const int64_t total = (int64_t)p.d * p.m;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  const double inv_m = 1.0 / (double)p.m;
+  const double inv_m = 1.0 / (double)p.M;
+  const bool warp_rows = (p.m & 31) == 0;
+  const bool padded = p.M != p.m;
   const int ns = p.La + p.Lx - 1;
   double worst = 0.0;
   int zb = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
     const int64_t row = g / p.m, j = g % p.m;
-    const double2* y = Y + (row * p.ni) * p.m + j;
+    const double2* y = Y + (row * p.ni) * p.M + j;
     I256 z{{0, 0, 0, 0}};
     for (int s = 0; s < ns; s++) {
-      const double2 c = y[(int64_t)(s >> 1) * p.m];
-      const double v = ((s & 1) ? c.y : c.x) * inv_m;
+      const double2 c = y[(int64_t)(s >> 1) * p.M];
+      double v = ((s & 1) ? c.y : c.x) * inv_m;
+      if (padded && j > 0) {   // circular lag j = linear lag j plus linear lag j - m
+        const double2 c2 = y[(int64_t)(s >> 1) * p.M + (p.M - p.m)];
+        v += ((s & 1) ? c2.y : c2.x) * inv_m;
+      }
       const double rv = rint(v);
       worst = fmax(worst, fabs(v - rv));
       if (fabs(rv) >= 4503599627370496.0) record(p.status, SK_ERR_INEXACT);   // 2^52
       z = i256_add(z, i256_shl_i64((int64_t)rv, p.B * s));
     }
     p.z[g] = z;
-    if (p.sums) row_sum_add(p.sums, p.m, row, 2, z.w[0]);
+    if (p.sums) row_sum_add(p.sums, warp_rows, row, 2, z.w[0]);
     zb = max(zb, i256_bits(z));
   }
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
@@ -694,6 +711,9 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const int d = s->d;
   const int64_t dm = (int64_t)d * m;
   const int logm = ilog2(m);
+  // FFT length: m itself when it is a power of two (circular correlation directly), else a
+  // power of two >= 2m - 1 holding the zero-padded linear correlation, folded back mod m.
+  const int64_t M = (m & (m - 1)) == 0 ? m : (int64_t)1 << ilog2(2 * m - 1);
   const int nslots = s->n_slots + 1;
   const int ncorr = std::max(1, s->corr_steps);
   const size_t slot_bytes = (size_t)dm * sizeof(I256);
@@ -703,12 +723,12 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const size_t cert_words = (size_t)ncorr * (1 + 3 * (size_t)d);
   const size_t small_bytes = 2 * SK_MAX_ROWS * sizeof(I256) + 256 + cert_words * 8 + 64;
   SK_CK(ensure(s->scratch, small_off + small_bytes, st));
-  if (s->twiddle_m != m) {
+  if (s->twiddle_m != M) {
     if (s->d_twiddle) cudaFree(s->d_twiddle);
     s->d_twiddle = nullptr;
-    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(m / 2) * sizeof(double2)));
-    s->twiddle_m = m;
-    k_twiddle<<<grid_for(m / 2), 256, 0, st>>>((double2*)s->d_twiddle, m);
+    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(M / 2) * sizeof(double2)));
+    s->twiddle_m = M;
+    k_twiddle<<<grid_for(M / 2), 256, 0, st>>>((double2*)s->d_twiddle, M);
     count_launch();
     SK_CK(cudaGetLastError());
   }
@@ -778,12 +798,12 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
           continue;
         }
         if (bits_a + bits_x + logm + 1 > 255) return SK_ERR_OVERFLOW;
-        int B = std::min(limb_bits_for(m, 1), bmax[corr]);
+        int B = std::min(limb_bits_for(M, 1), bmax[corr]);
         int La = 0, Lx = 0;
         for (;;) {
           La = (bits_a + 2 + B - 1) / B;
           Lx = (bits_x + 2 + B - 1) / B;
-          const int nb = std::min(limb_bits_for(m, std::min(La, Lx)), bmax[corr]);
+          const int nb = std::min(limb_bits_for(M, std::min(La, Lx)), bmax[corr]);
           if (nb >= B) break;
           B = nb;
         }
@@ -804,23 +824,25 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
         p.residual = cert_t;
         p.sums = cert_t + 1;
         p.zbits = d_bits + phys[spare];
-        const size_t fbytes = (size_t)d * p.nf * m * sizeof(double2);
+        p.M = M;
+        const size_t fbytes = (size_t)d * p.nf * M * sizeof(double2);
         SK_CK(ensure(s->fft_scratch, 2 * fbytes, st));
         double2* bufA = (double2*)s->fft_scratch.ptr;
-        double2* bufB = bufA + (size_t)d * p.nf * m;
+        double2* bufB = bufA + (size_t)d * p.nf * M;
         p.F = bufA;
         SK_CK(cudaMemsetAsync(p.zbits, 0, sizeof(int), st));
-        k_split<<<eg, 256, 0, st>>>(p);
+        const int egM = grid_for((int64_t)d * M);
+        k_split<<<egM, 256, 0, st>>>(p);
         count_launch();
         SK_CK(cudaGetLastError());
-        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, m, tw, false, st);
+        sk_status fs = fft(bufA, bufB, (int64_t)d * p.nf, M, tw, false, st);
         if (fs != SK_OK) return fs;
         p.F = bufB;
         p.G = bufA;
-        k_product<<<eg, 128, 0, st>>>(p);
+        k_product<<<egM, 128, 0, st>>>(p);
         count_launch();
         SK_CK(cudaGetLastError());
-        fs = fft(bufA, bufB, (int64_t)d * p.ni, m, tw, true, st);
+        fs = fft(bufA, bufB, (int64_t)d * p.ni, M, tw, true, st);
         if (fs != SK_OK) return fs;
         k_recombine<<<eg, 256, 0, st>>>(p, bufB);
         count_launch();
@@ -865,7 +887,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
     }
     // a step failed its certificate: redo everything with narrower limbs there
     retries++;
-    bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(m, 1)) - 3);
+    bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(M, 1)) - 3);
   }
   return SK_ERR_INEXACT;
 }
@@ -1020,6 +1042,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
         p.residual = d_resid;
         p.sums = nullptr;
         p.zbits = nullptr;
+        p.M = m;
         const size_t fbytes = align256((size_t)d * p.nf * m * sizeof(double2));
         if (2 * fbytes > fft_room) return SK_ERR_SCRATCH_TOO_SMALL;
         double2* bufA = (double2*)(slot_base + slot_bytes * nslots);

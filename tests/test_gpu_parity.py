@@ -126,6 +126,30 @@ def test_update_hot_key_cache_path(a, d, m, cached, monkeypatch):
     s.close()
 
 
+@pytest.mark.parametrize("agg", ["0", "1"])
+def test_update_shared_memory_path_warp_aggregation(agg, monkeypatch):
+    """Shared-memory sub-sketch path with and without warp-aggregated atomics
+    (SK_WARP_AGG=1): Zipf keys so lanes of a warp often hit the same counter, a domain
+    hint with violations (those tuples are skipped), signed weights."""
+    monkeypatch.setenv("SK_WARP_AGG", agg)
+    n = 100_003
+    rng = np.random.default_rng(5)
+    cols = np.stack([synth.zipf_keys(n, 1.3, 5000, 70 + c).numpy() for c in range(2)])
+    cols[0, ::977] = 6000                       # outside the declared domain
+    w = rng.choice(np.array([-1, 1, 2], dtype=np.int64), size=n)
+    attrs, edges = [2, 1, 1], [(0, 0, 1, 0), (0, 1, 2, 0)]
+    s = pkg.SketchSet(attrs, edges, 256, 5, 31)
+    s.update(0, torch.as_tensor(cols).cuda(), torch.as_tensor(w).cuda(), domain=[5000, 5000])
+    with pytest.raises(pkg.SketchError):
+        s.sync()
+    keep = cols[0] < 5000
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(31, 5, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols[:, keep], w[keep], 256, threads=8)
+    assert np.array_equal(s.counters[0].cpu().numpy(), ref)
+    s.close()
+
+
 def test_chain3_config_exact():
     """Chain R1(A) - R2(A,B) - R3(B), 10^4 rows each, m = 256, d = 5, seed 42: bit-exact
     sketches, exact row estimates and median."""
@@ -161,6 +185,49 @@ def test_estimate_exact_random_queries(m):
         assert est["rows"] == ref.rows, (m, trial, attrs, edges)
         assert est["median"] == ref.median
         s.close()
+
+
+@pytest.mark.parametrize("m", [3, 5, 12, 100, 1000, 10007])
+def test_estimate_exact_non_power_of_two_width(m):
+    """Widths that are not powers of two (the paper's experiments use m = 10^6): zero-padded
+    transforms folded back mod m give the exact Algorithm 3 rows."""
+    rng = random.Random(2000 + m)
+    for trial in range(3 if m < 10000 else 1):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 5))
+        rels = random_relations(rng, attrs, 500 if m < 10000 else 4000, 1 << rng.choice([3, 12, 30]))
+        d = rng.choice([1, 3])
+        seed = rng.randrange(1 << 62)
+        s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        q, co, sk = _oracle(attrs, edges, m, d, seed, rels)
+        assert np.array_equal(s.counters.cpu().numpy(), np.stack(sk))
+        est = s.estimate()
+        ref = O.estimate(q, sk)
+        assert est["rows"] == ref.rows, (m, trial, attrs, edges)
+        s.close()
+
+
+def test_width_one_million_correlation_through_a_one_tuple_relation():
+    """m = 10^6 (Section 4.4's width): R1 with one tuple turns each row estimate into one output
+    of the circular correlation of R3's and R2's sketches, computed directly by the oracle."""
+    attrs, edges = [1, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0)]
+    n = 300_000
+    r2 = torch.stack([synth.zipf_keys(n, 1.2, 1 << 20, 3), synth.zipf_keys(n, 1.2, 1 << 20, 4)])
+    r3 = synth.zipf_keys(n, 1.2, 1 << 20, 5)[None, :].contiguous()
+    m, d = 1_000_000, 3
+    s = pkg.SketchSet(attrs, edges, m, d, 91)
+    s.update(0, torch.tensor([[777]], dtype=torch.int64, device="cuda"))
+    s.update(1, r2.cuda())
+    s.update(2, r3.cuda())
+    est = s.estimate()
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(91, d, q.n_comp, len(q.edges))
+    c2 = O.sketch_relation(q, co, 1, r2.numpy(), None, m, threads=16)
+    c3 = O.sketch_relation(q, co, 2, r3.numpy(), None, m, threads=16)
+    bins, signs = O.tuple_hash(q, co, 0, [777], m)
+    for row in range(d):
+        z = O.correlate(c3[row].tolist(), c2[row].tolist(), threads=16, bins=[int(bins[row])])[0]
+        assert est["rows"][row] == int(signs[row]) * z
+    s.close()
 
 
 def test_identity_hashing_gives_exact_join_size_on_gpu():
@@ -220,7 +287,12 @@ def test_invalid_arguments():
     with pytest.raises(pkg.SketchError) as e:
         pkg.SketchSet([2, 2], [(0, 0, 1, 0), (0, 1, 1, 1)], 16, 2, 1)
     assert e.value.name == "SK_ERR_CYCLIC_QUERY"
-    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], 12, 2, 1)
+    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], (1 << 21) + 1, 1, 1)
+    with pytest.raises(pkg.SketchError) as e:
+        s.estimate()
+    assert e.value.name == "SK_ERR_UNSUPPORTED_WIDTH"
+    s.close()
+    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], 1, 1, 1)
     with pytest.raises(pkg.SketchError) as e:
         s.estimate()
     assert e.value.name == "SK_ERR_UNSUPPORTED_WIDTH"
