@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tuples", type=int, default=1_000_000)
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "serving"],
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "serving", "chain3", "chain8"],
                     help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
                          "launches; serving: request loop latency")
     ap.add_argument("--requests", type=int, default=4000)
@@ -692,6 +692,55 @@ def run_e2e_direct(args, s, wl, stream, world):
             "ms_per_step": dt * 1e3, "steps": steps, "method": "kernels read pinned host columns directly"}
 
 
+def run_small_config(args, world, rank, which):
+    """chain3: R1(A) - R2(A,B) - R3(B), 1e4 rows each, m = 256, d = 5 (launch-latency bound);
+    chain8: 8-relation chain, 1e7 Zipf(1.2) rows each, m = 2^20, d = 16 (estimator at scale).
+    Times the update of all relations and the estimate separately with CUDA events."""
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    import synth
+    from paper_2402_15953_gb300 import build as pkg_build
+    pkg_build.build()
+    wl = synth.chain3(device="cuda") if which == "chain3" else synth.chain(device="cuda")
+    s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+    stream = torch.cuda.current_stream()
+    reps = args.steps if which == "chain3" else max(3, args.steps // 10)
+
+    def upd():
+        s.reset()
+        for k, rel in enumerate(wl.relations):
+            s.update(k, rel.cols)
+
+    for _ in range(args.warmup):
+        upd()
+        est = s.estimate()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    up, es = [], []
+    for _ in range(reps):
+        e[0].record(stream)
+        upd()
+        e[1].record(stream)
+        est = s.estimate()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        up.append(e[0].elapsed_time(e[1]))
+        es.append(e[1].elapsed_time(e[2]))
+    tot = sum(r.n for r in wl.relations)
+    ms = statistics.mean(up) + statistics.mean(es)
+    line = {"metric": f"{which}: update and estimate time", "value": tot / (ms / 1e3), "unit": "tuples/s",
+            "n_gpus": world, "steps": reps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": which, "tuples_per_step": tot, "m": wl.m, "d": wl.d},
+            "update_us": 1e3 * statistics.mean(up), "estimate_us": 1e3 * statistics.mean(es),
+            "estimate_p99_us": 1e3 * percentile(es, 99.0), "estimates_per_s": 1e3 / statistics.mean(es),
+            "median": str(est["median"]), "max_residual": est["max_residual"], "max_limbs": est["max_limbs"],
+            "limb_bits": est["limb_bits"]}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
@@ -701,6 +750,8 @@ def main():
         run_batched(args, world, rank)
     elif args.workload == "serving":
         run_serving(args, world, rank)
+    elif args.workload in ("chain3", "chain8"):
+        run_small_config(args, world, rank, args.workload)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
