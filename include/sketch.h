@@ -213,8 +213,22 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
 sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * sk_sketch_set_estimator: selects how sk_estimate_join computes each circular
+ * cross-correlation (Definition 3.1); both give the identical exact result.
+ *   SK_ESTIMATOR_FFT64 (default): FP64 FFTs on signed limbs, outputs rounded to
+ *     integers and certified (largest distance to an integer <= 1/4, exact row-sum
+ *     identity), redone with narrower limbs if the certificate fails;
+ *   SK_ESTIMATOR_NTT: number-theoretic transforms over GF(2^64 - 2^32 + 1) on signed
+ *     limbs narrow enough that every output lies below q/2 in magnitude, exact by
+ *     construction (GB300's integer pipes are much faster than its FP64 pipe).
+ * The environment variable SK_ESTIMATOR=ntt selects the NTT for sets created after it
+ * is set.  Errors: SK_ERR_INVALID_ARG. */
+enum { SK_ESTIMATOR_FFT64 = 0, SK_ESTIMATOR_NTT = 1 };
+sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator);
+
+/* ---------------------------------------------------------------------------
  * sk_estimate_join_noalloc: the same estimate as sk_estimate_join (identical rows,
- * median and diagnostics), for callers that cannot allocate device memory while
+ * median and diagnostics; always with the FP64 FFT backend), for callers that cannot allocate device memory while
  * they estimate -- e.g. code running in a host callback or driver hook that must
  * not enter the CUDA allocator, a process whose device memory is fully held by
  * another pool, or a latency-critical path that forbids allocation.  No

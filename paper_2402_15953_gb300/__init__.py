@@ -81,7 +81,7 @@ class sk_update_plan_config(ctypes.Structure):
 EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_sketch_merge",
            "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
            "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
-           "sk_estimate_join_noalloc", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_get_config",
+           "sk_estimate_join_noalloc", "sk_sketch_set_estimator", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_get_config",
            "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy"]
 
 _lib = None
@@ -105,6 +105,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_sketch_merge.argtypes = [vp, vp, vp]
     L.sk_estimate_join.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
     L.sk_estimate_join_noalloc.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
+    L.sk_sketch_set_estimator.argtypes = [vp, i32]
     L.sk_sync.argtypes = [vp, vp]
     L.sk_sketch_destroy.argtypes = [vp]
     L.sk_status_string.argtypes = [i32]
@@ -186,6 +187,14 @@ def sk_sync(handle: int, stream: int) -> None:
 
 def sk_sketch_destroy(handle: int) -> None:
     _check(load().sk_sketch_destroy(handle), "sk_sketch_destroy")
+
+
+ESTIMATORS = {"fft64": 0, "ntt": 1}
+
+
+def sk_sketch_set_estimator(handle: int, estimator: str) -> None:
+    """estimator: "fft64" (FP64 FFT, certified rounding) or "ntt" (GF(2^64 - 2^32 + 1) transform)."""
+    _check(load().sk_sketch_set_estimator(handle, ESTIMATORS[estimator]), "sk_sketch_set_estimator")
 
 
 def sk_sketch_reset(handle: int, stream: int) -> None:
@@ -314,6 +323,9 @@ class SketchSet:
 
     def reset(self) -> None:
         sk_sketch_reset(self.handle, self._stream())
+
+    def set_estimator(self, estimator: str) -> None:
+        sk_sketch_set_estimator(self.handle, estimator)
 
     def coefficients(self) -> List[List[int]]:
         return sk_get_coefficients(self.handle)

@@ -2,6 +2,7 @@
 // notation), hash-function sampling (Algorithm 1 lines 1-2), the Algorithm 3
 // schedule, and dispatch to the update / merge / estimate kernels.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <new>
@@ -326,6 +327,8 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
     return st;
   }
   build_plan(s);
+  const char* ev = std::getenv("SK_ESTIMATOR");
+  if (ev && std::strcmp(ev, "ntt") == 0) s->estimator = SK_ESTIMATOR_NTT;
   *out = s;
   return SK_OK;
 }
@@ -363,6 +366,12 @@ sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_str
   std::memset(out, 0, sizeof(*out));
   if (set->m < 2 || set->m > (1ll << 22) || (set->m & (set->m - 1))) return SK_ERR_UNSUPPORTED_WIDTH;
   return run_estimate_noalloc(set, out, (cudaStream_t)cuda_stream);
+}
+
+sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator) {
+  if (!set || (estimator != SK_ESTIMATOR_FFT64 && estimator != SK_ESTIMATOR_NTT)) return SK_ERR_INVALID_ARG;
+  set->estimator = estimator;
+  return SK_OK;
 }
 
 sk_status sk_sketch_reset(sk_set* set, void* cuda_stream) {

@@ -262,68 +262,134 @@ __global__ void k_twiddle(double2* tw, int64_t n) {
   }
 }
 
-// W_n^e for 0 <= e < n from the half table
-__device__ __forceinline__ double2 twid(const double2* __restrict__ tw, int64_t e, int64_t half, bool inv) {
-  double2 w;
-  if (e < half) {
-    w = tw[e];
-  } else {
-    w = tw[e - half];
-    w.x = -w.x;
-    w.y = -w.y;
-  }
-  if (inv) w.y = -w.y;
-  return w;
-}
-
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// In-place radix-2 DIT FFTs of `cnt` vectors of length 2^logL stored back to back in
-// shared memory, input already in bit-reversed order.  tw is the half table of
-// W_N^t; a length-L transform uses W_L^e = W_N^(e * N / L), twstride = N / L.
-__device__ void smem_fft(double2* s, int cnt, int logL, const double2* __restrict__ tw, int64_t twstride,
-                         bool inv) {
+// ---------------------------------------------------------------------------
+// Arithmetic of the Goldilocks prime field GF(q), q = 2^64 - 2^32 + 1, used by the
+// number-theoretic transform.  2^64 = 2^32 - 1 and 2^96 = -1 (mod q), so a 128-bit
+// product hi 2^64 + lo with hi = hh 2^32 + hl reduces to lo - hh + hl (2^32 - 1).
+// Inputs are canonical (< q); outputs are canonical.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGL = 0xFFFFFFFF00000001ull;
+constexpr uint64_t kGLEps = 0xFFFFFFFFull;   // 2^64 mod q
+
+__host__ __device__ __forceinline__ uint64_t gl_add(uint64_t a, uint64_t b) {
+  uint64_t s = a + b;
+  if (s < a) s += kGLEps;               // wrapped past 2^64: add 2^64 mod q
+  return s >= kGL ? s - kGL : s;
+}
+
+__host__ __device__ __forceinline__ uint64_t gl_sub(uint64_t a, uint64_t b) {
+  uint64_t d = a - b;
+  if (a < b) d -= kGLEps;               // borrowed 2^64: subtract 2^64 - q
+  return d;
+}
+
+__host__ __device__ __forceinline__ uint64_t gl_mul(uint64_t a, uint64_t b) {
+  const uint64_t lo = a * b;
+  const uint64_t hi = mulhi64(a, b);
+  const uint64_t hh = hi >> 32, hl = hi & kGLEps;
+  uint64_t t = lo - hh;
+  if (lo < hh) t -= kGLEps;
+  const uint64_t u = hl * kGLEps;
+  uint64_t r = t + u;
+  if (r < u) r += kGLEps;
+  return r >= kGL ? r - kGL : r;
+}
+
+__host__ __device__ __forceinline__ uint64_t gl_pow(uint64_t b, uint64_t e) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1) r = gl_mul(r, b);
+    b = gl_mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Transforms.  One radix-2 DIT machinery serves two arithmetics:
+//   CplxOps: complex FP64, twiddles W_n^t = exp(-2 pi i t / n) (inverse: conjugates);
+//   GlOps:   GF(q), twiddles w^t for a primitive n-th root of unity w (the inverse
+//            transform is handed the table of w^-t).
+// Both satisfy W^(n/2) = -1, which the four-step twiddle uses.
+// ---------------------------------------------------------------------------
+struct CplxOps {
+  using T = double2;
+  static __device__ __forceinline__ T mul(T a, T b) { return cmul(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ T neg(T a) { return make_double2(-a.x, -a.y); }
+  static __device__ __forceinline__ T tw(const T* tab, int64_t i, bool inv) {
+    T w = tab[i];
+    if (inv) w.y = -w.y;
+    return w;
+  }
+  // W_4h^(pos + h) = W_4h^pos * W_4^1: -i times w (forward), +i times w (inverse)
+  static __device__ __forceinline__ T rot4(T w, bool inv, T) {
+    return inv ? make_double2(-w.y, w.x) : make_double2(w.y, -w.x);
+  }
+};
+
+struct GlOps {
+  using T = uint64_t;
+  static __device__ __forceinline__ T mul(T a, T b) { return gl_mul(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return gl_add(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return gl_sub(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return a ? kGL - a : 0; }
+  static __device__ __forceinline__ T tw(const T* tab, int64_t i, bool) { return tab[i]; }
+  static __device__ __forceinline__ T rot4(T w, bool, T r4) { return gl_mul(w, r4); }
+};
+
+// w^e for 0 <= e < n from the half table
+template <class Ops>
+__device__ __forceinline__ typename Ops::T twid(const typename Ops::T* __restrict__ tw, int64_t e, int64_t half,
+                                                bool inv) {
+  return e < half ? Ops::tw(tw, e, inv) : Ops::neg(Ops::tw(tw, e - half, inv));
+}
+
+// In-place radix-2 DIT transforms of `cnt` vectors of length 2^logL stored back to back
+// in shared memory, input already in bit-reversed order.  tw is the half table of the
+// length-N transform; a length-L transform uses w_L^e = w_N^(e * N / L), twstride = N / L.
+// r4 is w_N^(N/4) (GlOps only; complex uses -i).
+template <class Ops>
+__device__ void smem_xform(typename Ops::T* s, int cnt, int logL, const typename Ops::T* __restrict__ tw,
+                           int64_t twstride, bool inv, typename Ops::T r4) {
+  using T = typename Ops::T;
   const int L = 1 << logL;
   const int halfL = L >> 1;
   const int total = cnt * halfL;
   int st = 0;
   // Pairs of radix-2 stages (half sizes h and 2h) fused: the four elements b, b+h, b+2h,
   // b+3h (b = group * 4h + pos, pos < h) are closed under both stages.  Stage one
-  // pairs (b, b+h), (b+2h, b+3h) with W_2h^pos; stage two pairs (b, b+2h) with
-  // W_4h^pos and (b+h, b+3h) with W_4h^(pos+h) = W_4h^pos * W_4^1 = -i W_4h^pos
-  // (+i for the inverse).
+  // pairs (b, b+h), (b+2h, b+3h) with w_2h^pos; stage two pairs (b, b+2h) with
+  // w_4h^pos and (b+h, b+3h) with w_4h^(pos+h) = w_4h^pos * w_4.
   if (logL >= 2) {
     const int quarterL = L >> 2;
     const int total4 = cnt * quarterL;
     for (; st + 1 < logL; st += 2) {
       const int h = 1 << st;
-      const int64_t t1 = (int64_t)(L >> (st + 1)) * twstride;   // W_2h^pos = tw[pos * t1]
-      const int64_t t2 = (int64_t)(L >> (st + 2)) * twstride;   // W_4h^pos = tw[pos * t2]
+      const int64_t t1 = (int64_t)(L >> (st + 1)) * twstride;   // w_2h^pos = tw[pos * t1]
+      const int64_t t2 = (int64_t)(L >> (st + 2)) * twstride;   // w_4h^pos = tw[pos * t2]
       for (int b4 = threadIdx.x; b4 < total4; b4 += blockDim.x) {
         const int v = b4 >> (logL - 2);
         const int jj = b4 & (quarterL - 1);
         const int grp = jj >> st, pos = jj & (h - 1);
         const int i0 = v * L + grp * 4 * h + pos;
-        double2 w1 = tw[(int64_t)pos * t1];
-        double2 w2 = tw[(int64_t)pos * t2];
-        if (inv) {
-          w1.y = -w1.y;
-          w2.y = -w2.y;
-        }
-        const double2 w3 = inv ? make_double2(-w2.y, w2.x) : make_double2(w2.y, -w2.x);
-        const double2 a0 = s[i0], a1 = s[i0 + h], a2 = s[i0 + 2 * h], a3 = s[i0 + 3 * h];
-        const double2 t01 = cmul(a1, w1), t23 = cmul(a3, w1);
-        const double2 b0 = make_double2(a0.x + t01.x, a0.y + t01.y);
-        const double2 b1 = make_double2(a0.x - t01.x, a0.y - t01.y);
-        const double2 b2 = make_double2(a2.x + t23.x, a2.y + t23.y);
-        const double2 b3 = make_double2(a2.x - t23.x, a2.y - t23.y);
-        const double2 u2 = cmul(b2, w2), u3 = cmul(b3, w3);
-        s[i0] = make_double2(b0.x + u2.x, b0.y + u2.y);
-        s[i0 + 2 * h] = make_double2(b0.x - u2.x, b0.y - u2.y);
-        s[i0 + h] = make_double2(b1.x + u3.x, b1.y + u3.y);
-        s[i0 + 3 * h] = make_double2(b1.x - u3.x, b1.y - u3.y);
+        const T w1 = Ops::tw(tw, (int64_t)pos * t1, inv);
+        const T w2 = Ops::tw(tw, (int64_t)pos * t2, inv);
+        const T w3 = Ops::rot4(w2, inv, r4);
+        const T a0 = s[i0], a1 = s[i0 + h], a2 = s[i0 + 2 * h], a3 = s[i0 + 3 * h];
+        const T t01 = Ops::mul(a1, w1), t23 = Ops::mul(a3, w1);
+        const T b0 = Ops::add(a0, t01), b1 = Ops::sub(a0, t01);
+        const T b2 = Ops::add(a2, t23), b3 = Ops::sub(a2, t23);
+        const T u2 = Ops::mul(b2, w2), u3 = Ops::mul(b3, w3);
+        s[i0] = Ops::add(b0, u2);
+        s[i0 + 2 * h] = Ops::sub(b0, u2);
+        s[i0 + h] = Ops::add(b1, u3);
+        s[i0 + 3 * h] = Ops::sub(b1, u3);
       }
       __syncthreads();
     }
@@ -337,12 +403,11 @@ __device__ void smem_fft(double2* s, int cnt, int logL, const double2* __restric
       const int grp = jj >> st, pos = jj & (h - 1);
       const int i0 = v * L + grp * 2 * h + pos;
       const int i1 = i0 + h;
-      double2 w = tw[(int64_t)pos * tstep];
-      if (inv) w.y = -w.y;
-      const double2 a = s[i0];
-      const double2 t = cmul(s[i1], w);
-      s[i0] = make_double2(a.x + t.x, a.y + t.y);
-      s[i1] = make_double2(a.x - t.x, a.y - t.y);
+      const T w = Ops::tw(tw, (int64_t)pos * tstep, inv);
+      const T a = s[i0];
+      const T t = Ops::mul(s[i1], w);
+      s[i0] = Ops::add(a, t);
+      s[i1] = Ops::sub(a, t);
     }
     __syncthreads();
   }
@@ -351,9 +416,13 @@ __device__ void smem_fft(double2* s, int cnt, int logL, const double2* __restric
 __device__ __forceinline__ int bitrev(int i, int bits) { return (int)(__brev((unsigned)i) >> (32 - bits)); }
 
 // whole transforms of length L = 2^logL <= 4096, vpc vectors per block
-__global__ void k_fft_small(const double2* __restrict__ in, double2* __restrict__ out, int64_t batch, int logL,
-                            int vpc, const double2* __restrict__ tw, int64_t twstride, bool inv) {
-  extern __shared__ double2 sm[];
+template <class Ops>
+__global__ void k_xf_small(const typename Ops::T* __restrict__ in, typename Ops::T* __restrict__ out, int64_t batch,
+                           int logL, int vpc, const typename Ops::T* __restrict__ tw, int64_t twstride, bool inv,
+                           typename Ops::T r4) {
+  using T = typename Ops::T;
+  extern __shared__ __align__(16) unsigned char xf_smem[];
+  T* sm = (T*)xf_smem;
   const int L = 1 << logL;
   const int64_t v0 = (int64_t)blockIdx.x * vpc;
   const int64_t rem = batch - v0;
@@ -363,57 +432,73 @@ __global__ void k_fft_small(const double2* __restrict__ in, double2* __restrict_
     sm[v * L + bitrev(i, logL)] = in[(v0 + v) * L + i];
   }
   __syncthreads();
-  smem_fft(sm, cnt, logL, tw, twstride, inv);
+  smem_xform<Ops>(sm, cnt, logL, tw, twstride, inv, r4);
   for (int idx = threadIdx.x; idx < cnt * L; idx += blockDim.x) out[(v0 * L) + idx] = sm[idx];
 }
 
 // four-step, pass 1: length-R transforms down the columns of the R x C view
-// (element n1 * C + n2), then the twiddle W_N^(n2 k1); in place.
-__global__ void k_fft_cols(double2* __restrict__ buf, int logR, int logC, int cb, const double2* __restrict__ tw,
-                           bool inv) {
-  extern __shared__ double2 sm[];
+// (element n1 * C + n2), then the twiddle w_N^(n2 k1); in place.
+template <class Ops>
+__global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC, int cb,
+                          const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
+  using T = typename Ops::T;
+  extern __shared__ __align__(16) unsigned char xf_smem[];
+  T* sm = (T*)xf_smem;
   const int R = 1 << logR, C = 1 << logC;
   const int64_t N = (int64_t)R * C;
   const int blocks_per_vec = C / cb;
   const int64_t vec = blockIdx.x / blocks_per_vec;
   const int c0 = (blockIdx.x % blocks_per_vec) * cb;
-  double2* v = buf + vec * N;
+  T* v = buf + vec * N;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
     const int c = idx % cb, n1 = idx / cb;
     sm[c * R + bitrev(n1, logR)] = v[(int64_t)n1 * C + c0 + c];
   }
   __syncthreads();
-  smem_fft(sm, cb, logR, tw, C, inv);
+  smem_xform<Ops>(sm, cb, logR, tw, C, inv, r4);
   const int64_t half = N >> 1;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
     const int c = idx % cb, k1 = idx / cb;
     const int64_t n2 = c0 + c;
-    const double2 w = twid(tw, (n2 * k1) & (N - 1), half, inv);
-    v[(int64_t)k1 * C + n2] = cmul(sm[c * R + k1], w);
+    const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
+    v[(int64_t)k1 * C + n2] = Ops::mul(sm[c * R + k1], w);
   }
 }
 
 // four-step, pass 2: length-C transforms along the rows k1, written to the
 // natural-order output X[k1 + R k2]; out of place.
-__global__ void k_fft_rows(const double2* __restrict__ in, double2* __restrict__ out, int logR, int logC, int rb,
-                           const double2* __restrict__ tw, bool inv) {
-  extern __shared__ double2 sm[];
+template <class Ops>
+__global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::T* __restrict__ out, int logR,
+                          int logC, int rb, const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
+  using T = typename Ops::T;
+  extern __shared__ __align__(16) unsigned char xf_smem[];
+  T* sm = (T*)xf_smem;
   const int R = 1 << logR, C = 1 << logC;
   const int64_t N = (int64_t)R * C;
   const int blocks_per_vec = R / rb;
   const int64_t vec = blockIdx.x / blocks_per_vec;
   const int r0 = (blockIdx.x % blocks_per_vec) * rb;
-  const double2* vi = in + vec * N;
-  double2* vo = out + vec * N;
+  const T* vi = in + vec * N;
+  T* vo = out + vec * N;
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
     const int rr = idx / C, n2 = idx % C;
     sm[rr * C + bitrev(n2, logC)] = vi[(int64_t)(r0 + rr) * C + n2];
   }
   __syncthreads();
-  smem_fft(sm, rb, logC, tw, R, inv);
+  smem_xform<Ops>(sm, rb, logC, tw, R, inv, r4);
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
     const int rr = idx % rb, k2 = idx / rb;
     vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[rr * C + k2];
+  }
+}
+
+// GF(q) twiddle tables for a length-n transform: tw[t] = w^t and itw[t] = w^-t, t < n/2.
+__global__ void k_gl_twiddle(uint64_t* tw, uint64_t* itw, int64_t n, uint64_t w, uint64_t winv) {
+  const int64_t half = n >> 1;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += step) {
+    tw[t] = gl_pow(w, (uint64_t)t);
+    itw[t] = gl_pow(winv, (uint64_t)t);
   }
 }
 
@@ -576,6 +661,102 @@ __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
 }
 
 // ---------------------------------------------------------------------------
+// Exact correlation by number-theoretic transform over GF(q), q = 2^64 - 2^32 + 1.
+// Operands are split into signed B-bit limbs as for the FP64 path; each limb vector is
+// transformed (w a primitive M-th root of unity); for every limb sum s the product
+// sum_{l + l' = s} A_l(w^-k) X_l'(w^k) is formed (A at index M - k) and transformed
+// back.  B is chosen so that every output satisfies |y_s| <= pairs m 2^(2B-2) < 2^62 <
+// q / 2, so the residue determines y_s exactly: no rounding, exact by construction.
+// ---------------------------------------------------------------------------
+struct NttArgs {
+  const I256* a;
+  const I256* x;
+  I256* z;
+  uint64_t* F;       // [d][nl][M] limb residues / spectra
+  uint64_t* G;       // [d][ns][M] products / outputs
+  int64_t m, M;
+  int d, B, La, Lx, nl, ns;
+  int* status;
+  unsigned long long* sums;   // [d][3] row sums mod 2^64 of a, x, z
+  int* zbits;
+  uint64_t minv;              // M^-1 mod q
+};
+
+__global__ void k_nsplit(NttArgs p) {
+  const int64_t total = (int64_t)p.d * p.M;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t half = 1ll << (p.B - 1), full = 1ll << p.B;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.M, j = g % p.M;
+    uint64_t* F = p.F + (row * p.nl) * p.M + j;
+    const bool in = j < p.m;
+    const int64_t e = row * p.m + j;
+    row_sum_add(p.sums, p.M >= 32, row, 0, in ? p.a[e].w[0] : 0ull);
+    row_sum_add(p.sums, p.M >= 32, row, 1, in ? p.x[e].w[0] : 0ull);
+    if (!in) {
+      for (int t = 0; t < p.nl; t++) F[(int64_t)t * p.M] = 0;
+      continue;
+    }
+    for (int which = 0; which < 2; which++) {
+      I256 v = which == 0 ? p.a[e] : p.x[e];
+      const int L = which == 0 ? p.La : p.Lx;
+      const int base = which == 0 ? 0 : p.La;
+      for (int l = 0; l < L; l++) {
+        int64_t dig = (int64_t)(v.w[0] & (uint64_t)(full - 1));
+        if (dig >= half) dig -= full;
+        v = i256_add(v, i256_from_i64(-dig));
+        v = i256_sar(v, p.B);
+        F[(int64_t)(base + l) * p.M] = dig >= 0 ? (uint64_t)dig : kGL - (uint64_t)(-dig);
+      }
+      if (v.w[0] | v.w[1] | v.w[2] | v.w[3]) record(p.status, SK_ERR_OVERFLOW);
+    }
+  }
+}
+
+__global__ void k_nproduct(NttArgs p) {
+  const int64_t total = (int64_t)p.d * p.M;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.M, k = g % p.M;
+    const int64_t mk = (p.M - k) & (p.M - 1);
+    const uint64_t* F = p.F + (row * p.nl) * p.M;
+    uint64_t A[kMaxLimbs], X[kMaxLimbs];
+    for (int l = 0; l < p.La; l++) A[l] = F[(int64_t)l * p.M + mk];
+    for (int l = 0; l < p.Lx; l++) X[l] = F[(int64_t)(p.La + l) * p.M + k];
+    uint64_t* G = p.G + (row * p.ns) * p.M + k;
+    for (int s = 0; s < p.ns; s++) {
+      const int l0 = max(0, s - (p.Lx - 1)), l1 = min(s, p.La - 1);
+      uint64_t acc = 0;
+      for (int l = l0; l <= l1; l++) acc = gl_add(acc, gl_mul(A[l], X[s - l]));
+      G[(int64_t)s * p.M] = gl_mul(acc, p.minv);
+    }
+  }
+}
+
+__global__ void k_nrecombine(NttArgs p, const uint64_t* __restrict__ Y) {
+  const int64_t total = (int64_t)p.d * p.m;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const bool warp_rows = (p.m & 31) == 0;
+  const bool padded = p.M != p.m;
+  int zb = 0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / p.m, j = g % p.m;
+    const uint64_t* y = Y + (row * p.ns) * p.M + j;
+    I256 z{{0, 0, 0, 0}};
+    for (int s = 0; s < p.ns; s++) {
+      uint64_t r = y[(int64_t)s * p.M];
+      if (padded && j > 0) r = gl_add(r, y[(int64_t)s * p.M + (p.M - p.m)]);
+      const int64_t v = r > (kGL >> 1) ? -(int64_t)(kGL - r) : (int64_t)r;
+      z = i256_add(z, i256_shl_i64(v, p.B * s));
+    }
+    p.z[g] = z;
+    row_sum_add(p.sums, warp_rows, row, 2, z.w[0]);
+    zb = max(zb, i256_bits(z));
+  }
+  block_max_bits(zb, p.zbits);
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
 int grid_for(int64_t n, int threads = 256) {
@@ -632,34 +813,43 @@ cudaError_t ensure(Scratch& s, size_t bytes, cudaStream_t st) {
     if (_e != cudaSuccess) return set_status_from_cuda(_e); \
   } while (0)
 
-// Forward (inv = false) or inverse (unnormalised) FFT of `batch` vectors of
-// length m held in src; the result is written to dst, src is clobbered.
-sk_status fft(double2* src, double2* dst, int64_t batch, int64_t m, const double2* tw, bool inv, cudaStream_t st) {
+// Forward (inv = false) or inverse (unnormalised) transform of `batch` vectors of
+// length m held in src; the result is written to dst, src is clobbered.  Complex FP64
+// with the W table (conjugated for the inverse), or GF(q) with the w^t / w^-t table.
+template <class Ops>
+sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64_t m, const typename Ops::T* tw,
+                bool inv, typename Ops::T r4, cudaStream_t st) {
+  using T = typename Ops::T;
   const int logm = ilog2(m);
+  const int esz = (int)sizeof(T);
   if (logm <= 12) {
     const int L = (int)m;
     const int vpc = (int)std::max<int64_t>(1, std::min<int64_t>(4096 / L, batch));
     const int64_t grid = (batch + vpc - 1) / vpc;
-    const size_t smem = (size_t)vpc * L * sizeof(double2);
-    SK_CK(cudaFuncSetAttribute(k_fft_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fft_small<<<(unsigned)grid, 256, smem, st>>>(src, dst, batch, logm, vpc, tw, 1, inv);
+    const size_t smem = (size_t)vpc * L * esz;
+    SK_CK(cudaFuncSetAttribute(k_xf_small<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_xf_small<Ops><<<(unsigned)grid, 256, smem, st>>>(src, dst, batch, logm, vpc, tw, 1, inv, r4);
     count_launch();
     return set_status_from_cuda(cudaGetLastError());
   }
   const int logR = logm / 2, logC = logm - logR;
   const int R = 1 << logR, C = 1 << logC;
   const int budget = R >= 1024 ? (128 << 10) : (64 << 10);
-  int cb = std::max(1, std::min(C, budget / (R * (int)sizeof(double2))));
-  int rb = std::max(1, std::min(R, budget / (C * (int)sizeof(double2))));
-  const size_t smc = (size_t)cb * R * sizeof(double2), smr = (size_t)rb * C * sizeof(double2);
-  SK_CK(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-  SK_CK(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-  k_fft_cols<<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv);
+  int cb = std::max(1, std::min(C, budget / (R * esz)));
+  int rb = std::max(1, std::min(R, budget / (C * esz)));
+  const size_t smc = (size_t)cb * R * esz, smr = (size_t)rb * C * esz;
+  SK_CK(cudaFuncSetAttribute(k_xf_cols<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  SK_CK(cudaFuncSetAttribute(k_xf_rows<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  k_xf_cols<Ops><<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv, r4);
   count_launch();
   SK_CK(cudaGetLastError());
-  k_fft_rows<<<(unsigned)(batch * (R / rb)), 512, smr, st>>>(src, dst, logR, logC, rb, tw, inv);
+  k_xf_rows<Ops><<<(unsigned)(batch * (R / rb)), 512, smr, st>>>(src, dst, logR, logC, rb, tw, inv, r4);
   count_launch();
   return set_status_from_cuda(cudaGetLastError());
+}
+
+sk_status fft(double2* src, double2* dst, int64_t batch, int64_t m, const double2* tw, bool inv, cudaStream_t st) {
+  return xform<CplxOps>(src, dst, batch, m, tw, inv, make_double2(0.0, 0.0), st);
 }
 
 struct HostI256 {
@@ -672,10 +862,86 @@ void free_estimator(sk_set* s) {
   if (s->scratch.ptr) cudaFree(s->scratch.ptr);
   if (s->fft_scratch.ptr) cudaFree(s->fft_scratch.ptr);
   if (s->d_twiddle) cudaFree(s->d_twiddle);
+  if (s->d_gl_tw) cudaFree(s->d_gl_tw);
+  s->d_gl_tw = nullptr;
+  s->gl_m = 0;
   s->scratch = Scratch();
   s->fft_scratch = Scratch();
   s->d_twiddle = nullptr;
   s->twiddle_m = 0;
+}
+
+// One exact correlation step z = a (star) x through the GF(q) transform.
+sk_status corr_ntt(sk_set* s, const I256* a, const I256* x, I256* z, int* zbits, unsigned long long* cert, int bits_a,
+                   int bits_x, int64_t m, int64_t M, cudaStream_t st, int* max_limbs, int* last_B) {
+  const int d = s->d;
+  const int logM = ilog2(M);
+  if (s->gl_m != M) {
+    if (s->d_gl_tw) cudaFree(s->d_gl_tw);
+    s->d_gl_tw = nullptr;
+    SK_CK(cudaMalloc(&s->d_gl_tw, (size_t)M * sizeof(uint64_t)));   // [w^t | w^-t], t < M/2
+    const uint64_t w = gl_pow(7, (kGL - 1) / (uint64_t)M);          // 7 generates GF(q)*
+    if (M >= 2 && gl_pow(w, (uint64_t)M / 2) != kGL - 1) return SK_ERR_INEXACT;   // not a primitive root
+    const uint64_t winv = gl_pow(w, kGL - 2);
+    s->gl_r4 = M >= 4 ? gl_pow(w, (uint64_t)M / 4) : 1;
+    s->gl_r4inv = M >= 4 ? gl_pow(winv, (uint64_t)M / 4) : 1;
+    s->gl_minv = gl_pow((uint64_t)M, kGL - 2);
+    k_gl_twiddle<<<grid_for(M / 2), 256, 0, st>>>(s->d_gl_tw, s->d_gl_tw + M / 2, M, w, winv);
+    count_launch();
+    SK_CK(cudaGetLastError());
+    s->gl_m = M;
+  }
+  // widest limbs with every output below 2^62: pairs * m * 2^(2B-2) < 2^62
+  int B = 30, La = 0, Lx = 0;
+  for (; B >= 2; B--) {
+    La = (bits_a + 2 + B - 1) / B;
+    Lx = (bits_x + 2 + B - 1) / B;
+    const int pairs = std::min(La, Lx);
+    if (ilog2(pairs) + ilog2(m) + 2 * B - 2 <= 61) break;
+  }
+  if (La > kMaxLimbs || Lx > kMaxLimbs || B < 2) return SK_ERR_INEXACT;
+  NttArgs p;
+  p.a = a;
+  p.x = x;
+  p.z = z;
+  p.m = m;
+  p.M = M;
+  p.d = d;
+  p.B = B;
+  p.La = La;
+  p.Lx = Lx;
+  p.nl = La + Lx;
+  p.ns = La + Lx - 1;
+  p.status = s->d_status;
+  p.sums = cert + 1;
+  p.zbits = zbits;
+  p.minv = s->gl_minv;
+  const size_t words = (size_t)d * p.nl * M;
+  SK_CK(ensure(s->fft_scratch, 2 * words * sizeof(uint64_t), st));
+  uint64_t* bufA = (uint64_t*)s->fft_scratch.ptr;
+  uint64_t* bufB = bufA + words;
+  const int egM = grid_for((int64_t)d * M);
+  p.F = bufA;
+  SK_CK(cudaMemsetAsync(zbits, 0, sizeof(int), st));
+  k_nsplit<<<egM, 256, 0, st>>>(p);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  sk_status fs = xform<GlOps>(bufA, bufB, (int64_t)d * p.nl, M, s->d_gl_tw, false, s->gl_r4, st);
+  if (fs != SK_OK) return fs;
+  p.F = bufB;
+  p.G = bufA;
+  k_nproduct<<<egM, 128, 0, st>>>(p);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  fs = xform<GlOps>(bufA, bufB, (int64_t)d * p.ns, M, s->d_gl_tw + M / 2, true, s->gl_r4inv, st);
+  if (fs != SK_OK) return fs;
+  k_nrecombine<<<grid_for((int64_t)d * m), 256, 0, st>>>(p, bufB);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  *max_limbs = std::max(*max_limbs, std::max(La, Lx));
+  *last_B = B;
+  (void)logM;
+  return SK_OK;
 }
 
 // Fills *out from the d row values and their sorted copy.
@@ -798,6 +1064,15 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
           continue;
         }
         if (bits_a + bits_x + logm + 1 > 255) return SK_ERR_OVERFLOW;
+        if (s->estimator == SK_ESTIMATOR_NTT) {
+          sk_status ns = corr_ntt(s, a, x, slot(spare), d_bits + phys[spare], cert_t, bits_a, bits_x, m, M, st,
+                                  &max_limbs, &last_B);
+          if (ns != SK_OK) return ns;
+          std::swap(phys[op.dst], phys[spare]);
+          step_B[corr] = last_B;
+          corr++;
+          continue;
+        }
         int B = std::min(limb_bits_for(M, 1), bmax[corr]);
         int La = 0, Lx = 0;
         for (;;) {

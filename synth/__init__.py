@@ -51,10 +51,12 @@ def zipf_cdf(s: float, n: int, device: str) -> torch.Tensor:
     key = (float(s), int(n), str(device))
     c = _CDF_CACHE.get(key)
     if c is None:
-        k = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+        # built on the CPU: a float64 cumulative sum on the GPU is not bit-reproducible
+        # across runs, which would move a few sampled keys across bucket boundaries
+        k = torch.arange(1, n + 1, dtype=torch.float64)
         w = k.pow(-float(s))
         c = torch.cumsum(w, 0)
-        c = c / c[-1]
+        c = (c / c[-1]).to(device)
         if len(_CDF_CACHE) > 16:
             _CDF_CACHE.clear()
         _CDF_CACHE[key] = c

@@ -230,6 +230,40 @@ def test_width_one_million_correlation_through_a_one_tuple_relation():
     s.close()
 
 
+@pytest.mark.parametrize("m", [2, 8, 12, 64, 1000, 1024, 1 << 13, 1 << 14])
+def test_estimate_exact_ntt_backend(m):
+    """The GF(2^64 - 2^32 + 1) transform backend gives the oracle's exact rows (power-of-two
+    widths, single-pass and four-step transforms, and zero-padded other widths)."""
+    rng = random.Random(3000 + m)
+    for trial in range(4 if m <= 1024 else 2):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 5))
+        rels = random_relations(rng, attrs, 400 if m <= 1024 else 3000, 1 << rng.choice([3, 12, 30]))
+        d = rng.choice([1, 2, 5])
+        seed = rng.randrange(1 << 62)
+        s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        s.set_estimator("ntt")
+        q, co, sk = _oracle(attrs, edges, m, d, seed, rels)
+        est = s.estimate()
+        ref = O.estimate(q, sk)
+        assert est["rows"] == ref.rows, (m, trial, attrs, edges)
+        assert est["max_residual"] == 0.0
+        s.close()
+
+
+def test_ntt_and_fft_backends_agree_on_the_star_and_chain8_shapes():
+    for wl in (synth.star(n_fact=2_000_000, n_dim=200_000, m=1 << 16, d=3, device="cuda"),
+               synth.chain(r=8, n=200_000, m=1 << 14, d=2, device="cuda")):
+        s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+        for k, rel in enumerate(wl.relations):
+            s.update(k, rel.cols)
+        a = s.estimate()
+        s.set_estimator("ntt")
+        b = s.estimate()
+        assert a["rows"] == b["rows"] and a["median"] == b["median"]
+        s.close()
+    assert pkg.load().sk_sketch_set_estimator(None, 1) == pkg.SK_ERR_INVALID_ARG
+
+
 def test_identity_hashing_gives_exact_join_size_on_gpu():
     """With injective test hashes (bin x * R_q, sign +1) the GPU estimate is the exact join size."""
     rng = random.Random(7)
