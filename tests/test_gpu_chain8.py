@@ -75,7 +75,23 @@ def test_chain8_full_estimate_linearity(chain8_full):
     s.close()
 
 
-def test_correlation_at_width_2_20_through_a_one_tuple_relation(chain8_full):
+def test_chain8_full_fft_and_ntt_backends_agree(chain8_full):
+    """At full size (estimates near 10^46, operands split into up to 10 limbs) the certified
+    FP64 FFT and the exact GF(q) transform give the same 16 rows."""
+    wl = chain8_full
+    s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+    for k, rel in enumerate(wl.relations):
+        s.update(k, rel.cols)
+    a = s.estimate()
+    s.set_estimator("ntt")
+    b = s.estimate()
+    assert a["rows"] == b["rows"] and a["median"] == b["median"]
+    assert a["max_limbs"] >= 6
+    s.close()
+
+
+@pytest.mark.parametrize("backend", ["fft64", "ntt"])
+def test_correlation_at_width_2_20_through_a_one_tuple_relation(chain8_full, backend):
     """R1(A) with one tuple, R2(A, B) and R3(B) with 1e7 rows each: the row estimate is
     s * (c3 star c2)[h], one output of an m = 2^20 correlation of two large sketches,
     which the oracle computes directly."""
@@ -86,6 +102,7 @@ def test_correlation_at_width_2_20_through_a_one_tuple_relation(chain8_full):
     one = torch.tensor([[12345]], dtype=torch.int64, device="cuda")
     d, m = 4, 1 << 20
     s = pkg.SketchSet(attrs, edges, m, d, 77)
+    s.set_estimator(backend)
     s.update(0, one)
     s.update(1, r2)
     s.update(2, r3)
