@@ -51,9 +51,16 @@ def parse_args():
                     help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
                          "launches; serving: request loop latency")
     ap.add_argument("--requests", type=int, default=4000)
+    ap.add_argument("--no-domains", action="store_true",
+                    help="do not declare the key domains (every tuple is hashed; no key tables)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not overlap step i's estimate with step i+1's update")
     return ap.parse_args()
+
+
+def declared_domains(args, wl):
+    """Per relation, the key domains the workload declares (None: undeclared)."""
+    return [None] * wl.r if args.no_domains else wl.domains
 
 
 def workload_name(args) -> str:
@@ -255,13 +262,14 @@ def run_ours(args, world, rank, local):
     total = sum(int(c.shape[1]) for c in rels)
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, device=dev)
     stream = torch.cuda.current_stream()
+    doms = declared_domains(args, wl)
 
     def step(ev=None):
         s.reset()
         for k, c in enumerate(rels):
             if ev is not None and k == 0:
                 ev[0].record(stream)
-            s.update(k, c)
+            s.update(k, c, domain=doms[k])
             if ev is not None and k == 0:
                 ev[1].record(stream)
         if ev is not None:
@@ -338,7 +346,7 @@ def run_ours(args, world, rank, local):
                         cur = sets[i % 2]
                         cur.reset()
                         for kk, c in enumerate(rels):
-                            cur.update(kk, c)
+                            cur.update(kk, c, domain=doms[kk])
                         evs2[i % 2].record(upd)
                 if i >= 1:
                     with torch.cuda.stream(est_stream):
@@ -366,16 +374,50 @@ def run_ours(args, world, rank, local):
     fact_ms = statistics.mean(upd_fact_ms)
     achieved_gbs = fact_bytes / (fact_ms / 1e3) / 1e9
     mulmods_per_fact_tuple = wl.d * 5 * (1 + 3 * 1)
-    mulmod_rate = args.fact_rows * mulmods_per_fact_tuple / (fact_ms / 1e3)
-
-    # Integer-ALU roofline of the fact-table update: algorithmic work = GF(2^61-1) Horner
-    # multiply-add steps (1 per bin hash, 3 per sign hash), peak = the step rate of the same
-    # arithmetic without loads, atomics or combination (6.4 steps per clock per SM measured)
-    # x 152 SMs x 2.07 GHz.  traffic: DRAM bytes of one ncu capture of this kernel version
-    # (2e7-row launch: 808.5 MB), scaled to this launch's row count.
-    steps_per_s = mulmod_rate
-    alu_peak_steps = 6.4 * 152 * 2.07e9
-    traffic = 808.5e6 * args.fact_rows / 2e7 / 1e9
+    fact_s = fact_ms / 1e3
+    tables = not args.no_domains
+    if tables:
+        # The fact-table update call is two launches, timed together: k_key_table hashes the
+        # 5 x 1e6 declared domain keys once (d rows each) and k_update_tab runs the 1e8 tuples
+        # (5 key loads, 5 gathers of 32-byte records, 9 counter atomics each).
+        # HBM roofline (algorithmic bytes = the 40 key bytes per tuple; tables and sketch are
+        # meant to stay in L2).  traffic = DRAM bytes of one ncu capture of k_update_tab at
+        # 2e7 rows (1.588 GB, record misses included) scaled to this row count, plus the
+        # table write (5e6 records x 32 B).
+        # L2 roofline, the bound that binds: L2 tag lookups per tuple from the same capture
+        # (16.41 = 9 atomics + key and record reads + lookups forwarded between the two dies'
+        # L2 halves) against 188 slices x 1 lookup per cycle x 2.016 GHz.
+        traffic = 1.588e9 * args.fact_rows / 2e7 / 1e9 + 5 * 1_000_000 * 32 / 1e9
+        kernel = "k_key_table + k_update_tab<5,pow2,global,narrow,v8> (fact table F)"
+        l2_req_per_tuple = 16.41
+        l2_peak = 188 * 2.016e9
+        l2_rate = l2_req_per_tuple * args.fact_rows / fact_s
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kernel,
+                    "work": "40 key bytes per fact tuple (5 int64 columns)",
+                    "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled, + table write)",
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+        extra = {"roofline_l2": {"bound": "l2_tag_lookups", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
+                                 "unit": "G lookups/s", "frac": l2_rate / l2_peak,
+                                 "per_tuple": l2_req_per_tuple, "kernel": kernel,
+                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 81 % of peak"}}
+    else:
+        # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
+        # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the
+        # step rate of the same arithmetic without loads, atomics or combination (6.4 steps
+        # per clock per SM measured) x 152 SMs x 2.07 GHz.  traffic: DRAM bytes of one ncu
+        # capture of k_update (2e7-row launch: 808.5 MB), scaled to this launch's row count.
+        steps_per_s = args.fact_rows * mulmods_per_fact_tuple / fact_s
+        alu_peak_steps = 6.4 * 152 * 2.07e9
+        traffic = 808.5e6 * args.fact_rows / 2e7 / 1e9
+        roofline = {"bound": "alu", "achieved": steps_per_s / 1e9, "peak": alu_peak_steps / 1e9, "unit": "Gstep/s",
+                    "frac": steps_per_s / alu_peak_steps, "traffic": traffic,
+                    "kernel": "k_update<5,pow2,global> (fact table F)",
+                    "work": f"{mulmods_per_fact_tuple} GF(2^61-1) Horner steps per fact tuple",
+                    "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled)"}
+        extra = {"roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "GB per launch",
+                                  "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}}
 
     serial = {"ms_per_step": ms_per_step, "value": value, "gpu_launches": launches}
     if pipe is not None and pipe["value"] > value:
@@ -386,6 +428,7 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": workload_name(args), "relations": 6, "tuples_per_step": total, "m": wl.m, "d": wl.d,
+                   "key_domains": "declared [0, 1e6) per column" if tables else "undeclared",
                    "l2": "inputs (4.2 GB of keys) larger than L2; no flush needed",
                    "parallelism": f"replicas x{world}",
                    "pipelined": pipe is not None and value == pipe["value"]},
@@ -397,14 +440,7 @@ def run_ours(args, world, rank, local):
         "estimate_ntt": {"estimate_ms": ntt_ms, "identical_rows": ntt_same,
                          "step_ms_with_ntt": statistics.mean(upd_all_ms) + ntt_ms,
                          "note": "sk_sketch_set_estimator(SK_ESTIMATOR_NTT); the headline uses the FP64 FFT"},
-        "roofline": {"bound": "alu", "achieved": steps_per_s / 1e9, "peak": alu_peak_steps / 1e9, "unit": "Gstep/s",
-                     "frac": steps_per_s / alu_peak_steps, "traffic": traffic,
-                     "kernel": "k_update<5,pow2,global> (fact table F)",
-                     "work": f"{mulmods_per_fact_tuple} GF(2^61-1) Horner steps per fact tuple",
-                     "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled)"},
-        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "GB per launch",
-                         "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "roofline": roofline, **extra,
         "estimate_check": {"median": str(est["median"]), "max_residual": est["max_residual"],
                            "max_limbs": est["max_limbs"], "limb_bits": est["limb_bits"]},
         "gpu_launches": launches, "clocks": clocks,
@@ -441,6 +477,7 @@ def run_e2e(args, s, wl, stream, world):
     for e in free_ev:
         e.record(stream)
     h2d = sum(h.numel() * 8 for h in host)
+    doms = declared_domains(args, wl)
 
     def step():
         s.reset()
@@ -457,7 +494,7 @@ def run_e2e(args, s, wl, stream, world):
                     ready = torch.cuda.Event()
                     ready.record(copy_stream)
                 stream.wait_event(ready)
-                s.update(k, b[:a, : i1 - i0])
+                s.update(k, b[:a, : i1 - i0], domain=doms[k])
                 free_ev[slot].record(stream)
                 slot ^= 1
         return s.estimate()
@@ -685,11 +722,13 @@ def run_e2e_direct(args, s, wl, stream, world):
     host = [r.cols.cpu().pin_memory() for r in wl.relations]
     h2d = sum(h.numel() * 8 for h in host)
     sid = stream.cuda_stream
+    doms = declared_domains(args, wl)
 
     def step():
         s.reset()
         for k, h in enumerate(host):
-            pkg.sk_sketch_update_batch(s.handle, k, int(h.shape[1]), h.data_ptr(), int(h.stride(0)), None, None, sid)
+            pkg.sk_sketch_update_batch(s.handle, k, int(h.shape[1]), h.data_ptr(), int(h.stride(0)), None, doms[k],
+                                       sid)
         return s.estimate()
 
     for _ in range(max(1, args.warmup)):
@@ -723,11 +762,12 @@ def run_small_config(args, world, rank, which):
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
     stream = torch.cuda.current_stream()
     reps = args.steps if which == "chain3" else max(3, args.steps // 10)
+    doms = declared_domains(args, wl)
 
     def upd():
         s.reset()
         for k, rel in enumerate(wl.relations):
-            s.update(k, rel.cols)
+            s.update(k, rel.cols, domain=doms[k])
 
     for _ in range(args.warmup):
         upd()

@@ -101,7 +101,7 @@ typedef struct {
   double max_residual;   /* max |y - round(y)| over every FFT output rounded to an integer */
   int32_t max_limbs;     /* largest number of limbs an operand of a correlation was split into */
   int32_t limb_bits;     /* limb width B of the last correlation step */
-  int32_t corr_steps;    /* correlation steps per row (Algorithm 3's FFT lines) */
+  int32_t corr_steps;    /* correlation steps per row (Algorithm 3's FFT-based correlations) */
   int32_t retries;       /* steps redone with narrower limbs after a failed certificate */
   sk_i256 row[SK_MAX_ROWS];
 } sk_estimate;
@@ -113,7 +113,7 @@ typedef struct {
 sk_status sk_sketch_bytes(const sk_query* query, int64_t m, int32_t d, size_t* bytes);
 
 /* ---------------------------------------------------------------------------
- * sk_sketch_create: Algorithm 1 lines 1-2 and the initialisation of Section 3.2.
+ * sk_sketch_create: the sampling step of Algorithm 1 and the initialisation of Section 3.2.
  * Validates the query, draws per row one bin function per component and one sign
  * function per join (SplitMix64 from `seed`, each coefficient an element of
  * GF(2^61 - 1)), uploads them, and zeroes the caller's counters buffer
@@ -138,6 +138,15 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
  * the field as (uint64)key mod (2^61 - 1).  domain_hint (host array of |Omega|
  * exclusive upper bounds, or NULL) declares 0 <= key < bound; tuples with a key
  * outside it are skipped and SK_ERR_KEY_OUT_OF_DOMAIN is recorded.
+ * With declared domains whose bounds are at most 2^31, the call may first hash
+ * every domain key once per attribute into a table (per key and row: the bin
+ * and the sign parity, 16 or 32 bits) and then update by table lookups; it does
+ * so when the domains are small against the batch (sum of bounds * 4 <=
+ * n_rows * |Omega|) and the relation's d * m * 8-byte sketch is at most 32 MiB
+ * (environment: SK_KEY_TABLE=0 never, =1 whenever the bounds allow).  The table
+ * (sum of bounds * 16 or 32 bytes when m <= 2^16 and d <= 14) comes from the device's
+ * stream-ordered pool and is released on cuda_stream at the end of the call; if
+ * it cannot be allocated the call hashes per tuple.  Results are identical.
  * Asynchronous on cuda_stream; the columns and weights must stay valid until it
  * completes.  n_rows == 0 is a no-op.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */

@@ -1,5 +1,5 @@
 // Host side of the C ABI: query validation and canonical numbering (Section 2.6
-// notation), hash-function sampling (Algorithm 1 lines 1-2), the Algorithm 3
+// notation), hash-function sampling (Algorithm 1, its sampling step), the Algorithm 3
 // schedule, and dispatch to the update / merge / estimate kernels.
 #include <algorithm>
 #include <cstdlib>

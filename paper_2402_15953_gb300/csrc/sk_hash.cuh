@@ -193,5 +193,252 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Key tables.  When a relation's keys come with declared domains [0, dom_u) and the
+// batch is much longer than the domains, the per-attribute hash results are computed
+// once per domain key instead of once per tuple.  The record of (attribute u, key x)
+// holds, for every row, the bin h_comp(u)(x) mod m and the parity of the product of
+// the signs of u's joins (set = sign -1).  A tuple then combines its A records with the
+// same sum-mod-m and sign product as update_tuple (Eqs. 2-3), so every counter update
+// is identical.  Two record formats:
+//   - narrow (m <= 2^16, d <= 32): d uint16 bins from byte 0, the d sign bits in the
+//     record's last 32-bit word; round_up(2d + 4, 16) bytes (32 for d <= 14);
+//   - wide: d uint32 words, bin in bits 0..30 and sign in bit 31, zero-padded to a
+//     multiple of 16 bytes.
+// ---------------------------------------------------------------------------
+struct TabArgs {
+  uint32_t* tbl;                 // [sum_u dom_u][rvec * 4] 32-bit words
+  int64_t base[kMaxAttrs + 1];   // first record of attribute u; base[a] = total records
+  int off[kMaxAttrs];            // coefficient offset of attribute u within a row
+  int rvec;                      // record length in 16-byte vectors
+  int narrow;                    // record format
+};
+
+__host__ __device__ inline int key_record_vectors(int d, bool narrow) {
+  return narrow ? (2 * d + 4 + 15) / 16 : (4 * d + 15) / 16;
+}
+
+// bin mod m and sign parity of attribute u's functions for one row at key x (< 2^32)
+template <bool POW2>
+__device__ __forceinline__ uint32_t key_row_hash(const UpdArgs& p, const uint64_t* c, int deg, uint32_t x,
+                                                 uint32_t* parity) {
+  const ulonglong2 bc = *(const ulonglong2*)c;
+  const uint64_t v = mac_narrow(bc.y, x, bc.x);
+  uint32_t h;
+  if (POW2) h = ((uint32_t)v + mersenne_q1(v)) & (uint32_t)(p.m - 1);
+  else h = (uint32_t)(reduce_lazy(v) % p.m);
+  uint32_t sx = 0;
+  for (int k = 0; k < deg; k++) {
+    const ulonglong2 s01 = *(const ulonglong2*)(c + 2 + 4 * k);
+    const ulonglong2 s23 = *(const ulonglong2*)(c + 4 + 4 * k);
+    uint64_t acc = mac_narrow(s23.y, x, s23.x);
+    acc = mac_narrow(acc, x, s01.y);
+    acc = mac_narrow(acc, x, s01.x);
+    sx ^= (uint32_t)acc ^ mersenne_q1(acc);
+  }
+  *parity = sx & 1u;
+  return h;
+}
+
+// Record of attribute u for key x (< 2^31: the field element is the key itself).
+template <bool POW2>
+__device__ __forceinline__ void key_record(const UpdArgs& p, const TabArgs& t, const uint64_t* s_coef, int u,
+                                           uint32_t x, uint32_t* out) {
+  const int deg = p.deg[u];
+  const uint64_t* cr = s_coef + t.off[u];
+  const int nw = 4 * t.rvec;
+  uint32_t mask = 0;
+  for (int w0 = 0; w0 < nw; w0 += 4) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int wi = w0 + j;
+      uint32_t e = 0;
+      if (t.narrow) {
+        if (wi == nw - 1) {
+          e = mask;
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const int row = 2 * wi + h;
+            if (row < p.d) {
+              uint32_t par;
+              const uint32_t b = key_row_hash<POW2>(p, cr + (int64_t)row * p.row_len, deg, x, &par);
+              e |= b << (16 * h);
+              mask |= par << row;
+            }
+          }
+        }
+      } else if (wi < p.d) {
+        uint32_t par;
+        const uint32_t b = key_row_hash<POW2>(p, cr + (int64_t)wi * p.row_len, deg, x, &par);
+        e = b | (par << 31);
+      }
+      w[j] = e;
+    }
+    *(uint4*)(out + w0) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <bool SMEM>
+__device__ __forceinline__ void scatter_row(const UpdArgs& p, int* s_sub, bool small, int row, uint32_t bin,
+                                            int64_t v) {
+  if (SMEM && small) atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
+  else atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
+}
+
+// Key-column load for the key-table kernel: the columns are streamed once, so they are
+// kept out of L1 and marked first to leave L2 (the tables and the sketch stay cached).
+__device__ __forceinline__ int64_t ld_key_stream(const int64_t* ptr) {
+  int64_t v;
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
+// One 32-byte record with a single 256-bit load.  Only for records of exactly two
+// 16-byte vectors: the table base is 256-byte aligned, so every record is 32-byte aligned.
+__device__ __forceinline__ void ld_record32(const uint4* ptr, uint32_t (&w)[8]) {
+  asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+      : "l"(ptr));
+}
+
+// Algorithm 2 for tuple i through the key tables (declared domains are required).
+// V8: records are 32 bytes (rvec == 2) and each is read with one load.
+template <int A, bool POW2, bool SMEM, bool NARROW, bool V8 = false>
+__device__ __forceinline__ void update_tuple_tab(const UpdArgs& p, const TabArgs& t, int* s_sub, int64_t i) {
+  const int na = A > 0 ? A : p.a;
+  constexpr int AM = A > 0 ? A : kMaxAttrs;
+  const uint4* rec[AM];
+  bool ok = true;
+#pragma unroll
+  for (int u = 0; u < AM; u++) {
+    if (A == 0 && u >= na) break;
+    const int64_t key = ld_key_stream(p.cols + (int64_t)u * p.stride + i);
+    if (key < 0 || key >= p.dom[u]) ok = false;
+    rec[u] = (const uint4*)t.tbl + (t.base[u] + (ok ? key : 0)) * t.rvec;
+  }
+  if (!ok) {
+    record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
+    return;
+  }
+  const int64_t delta = p.w ? __ldg(p.w + i) : 1;
+  const bool small = SMEM && (delta <= p.smem_wmax && delta >= -p.smem_wmax);
+  const uint32_t m32 = (uint32_t)p.m;
+  if (V8 && NARROW) {
+    // d <= 14: bins in words 0..6, sign mask in word 7
+    uint32_t b[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, sg = 0;
+#pragma unroll
+    for (int u = 0; u < AM; u++) {
+      if (A == 0 && u >= na) break;
+      uint32_t w[8];
+      ld_record32(rec[u], w);
+      sg ^= w[7];
+#pragma unroll
+      for (int j = 0; j < 14; j++) {
+        b[j] += (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+        if (!POW2 && b[j] >= m32) b[j] -= m32;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 14; j++) {
+      if (j >= p.d) break;
+      const uint32_t bin = POW2 ? (b[j] & (m32 - 1)) : b[j];
+      scatter_row<SMEM>(p, s_sub, small, j, bin, ((sg >> j) & 1u) ? -delta : delta);
+    }
+  } else if (V8) {
+    // d <= 8: one word per row
+    uint32_t b[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int u = 0; u < AM; u++) {
+      if (A == 0 && u >= na) break;
+      uint32_t w[8];
+      ld_record32(rec[u], w);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        if (POW2) {
+          b[j] += w[j];
+        } else {
+          b[j] += w[j] & 0x7fffffffu;
+          if (b[j] >= m32) b[j] -= m32;
+        }
+        sg[j] ^= w[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (j >= p.d) break;
+      const uint32_t bin = POW2 ? (b[j] & (m32 - 1)) : b[j];
+      scatter_row<SMEM>(p, s_sub, small, j, bin, (sg[j] >> 31) ? -delta : delta);
+    }
+  } else if (NARROW) {
+    // the last vector of every record carries the sign mask; keep it
+    const int last = t.rvec - 1;
+    uint4 tail[AM];
+    uint32_t sg = 0;
+#pragma unroll
+    for (int u = 0; u < AM; u++) {
+      if (A == 0 && u >= na) break;
+      tail[u] = __ldg(rec[u] + last);
+      sg ^= tail[u].w;
+    }
+    for (int c = 0; c <= last; c++) {
+      uint32_t b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int u = 0; u < AM; u++) {
+        if (A == 0 && u >= na) break;
+        const uint4 q = c == last ? tail[u] : __ldg(rec[u] + c);
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const uint32_t e = (wd[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+          if (POW2) {
+            b[j] += e;
+          } else {
+            b[j] += e;
+            if (b[j] >= m32) b[j] -= m32;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int row = 8 * c + j;
+        if (row >= p.d) break;
+        const uint32_t bin = POW2 ? (b[j] & (m32 - 1)) : b[j];
+        scatter_row<SMEM>(p, s_sub, small, row, bin, ((sg >> row) & 1u) ? -delta : delta);
+      }
+    }
+  } else {
+    for (int c = 0; c < t.rvec; c++) {
+      uint32_t b[4] = {0, 0, 0, 0}, sg[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int u = 0; u < AM; u++) {
+        if (A == 0 && u >= na) break;
+        const uint4 q = __ldg(rec[u] + c);
+        const uint32_t e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          if (POW2) {
+            b[j] += e[j];   // sign bits carry out above the masked bin bits
+          } else {
+            b[j] += e[j] & 0x7fffffffu;
+            if (b[j] >= m32) b[j] -= m32;
+          }
+          sg[j] ^= e[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int row = 4 * c + j;
+        if (row >= p.d) break;
+        const uint32_t bin = POW2 ? (b[j] & (m32 - 1)) : b[j];
+        scatter_row<SMEM>(p, s_sub, small, row, bin, (sg[j] >> 31) ? -delta : delta);
+      }
+    }
+  }
+}
+
 }  // namespace dev
 }  // namespace sk

@@ -1,0 +1,172 @@
+"""Key-table update path (declared key domains): bit-exact against the oracle.
+
+With SK_KEY_TABLE=1 every update that declares domains goes through the per-domain-key
+tables; with 0 it hashes per tuple.  Both must give the oracle's sketches, including
+for tuples outside the declared domain (reported and skipped), widths that are and are
+not powers of two, the shared-memory and global-atomic scatter, both record formats
+(16-bit bins for m <= 2^16 and d <= 32, at the record-length boundaries d = 14 / 15;
+32-bit otherwise), d not a multiple of the record vector, and relations with more
+attributes than the fixed-arity kernels."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2402_15953_gb300 as pkg
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+
+
+def _star(a):
+    return [a] + [1] * a, [(0, i, 1 + i, 0) for i in range(a)]
+
+
+def _run(attrs, edges, m, d, seed, cols, w, dom):
+    s = pkg.SketchSet(attrs, edges, m, d, seed)
+    s.update(0, torch.as_tensor(cols).cuda(), None if w is None else torch.as_tensor(w).cuda(), domain=dom)
+    bad = bool(((cols < 0) | (cols >= np.array(dom)[:, None])).any())
+    if bad:
+        with pytest.raises(pkg.SketchError):
+            s.sync()
+    else:
+        s.sync()
+    got = s.counters[0].cpu().numpy()
+    s.close()
+    return got
+
+
+MODES = {"direct": ("0", "1"), "table": ("1", "1"), "table-16B-loads": ("1", "0")}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("a,d,m", [(1, 1, 64), (2, 3, 1000), (3, 9, 1 << 16), (5, 9, 1 << 16), (5, 7, 77777),
+                                    (4, 64, 1 << 12), (7, 5, 1 << 14), (2, 13, 256), (3, 14, 1 << 16),
+                                    (2, 15, 4096), (3, 32, 2048), (6, 9, 65535), (2, 5, 1 << 18),
+                                    (2, 9, 50000)])
+def test_key_table_bit_exact(mode, a, d, m, monkeypatch):
+    """mode: per-tuple hashing; key tables with 32-byte records read by one 256-bit load
+    where they apply; key tables read in 16-byte loads only (SK_TAB_V8=0)."""
+    monkeypatch.setenv("SK_KEY_TABLE", MODES[mode][0])
+    monkeypatch.setenv("SK_TAB_V8", MODES[mode][1])
+    rng = np.random.default_rng(a * 1000 + d)
+    n = 200_003
+    doms = [int(x) for x in rng.integers(50, 5000, size=a)]
+    cols = np.stack([synth.zipf_keys(n, 1.1, doms[u], 17 + u).numpy() for u in range(a)])
+    w = rng.choice(np.array([-3, -1, 1, 1, 2], dtype=np.int64), size=n)
+    attrs, edges = _star(a)
+    got = _run(attrs, edges, m, d, 99 + a, cols, w, doms)
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(99 + a, d, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols, w, m, threads=16)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_key_table_domain_violations_and_edges(mode, monkeypatch):
+    """Keys -1, dom and beyond are skipped and reported; keys 0 and dom - 1 (the table's
+    first and last records) count."""
+    monkeypatch.setenv("SK_KEY_TABLE", MODES[mode][0])
+    monkeypatch.setenv("SK_TAB_V8", MODES[mode][1])
+    rng = np.random.default_rng(3)
+    n = 50_000
+    doms = [1000, 1 << 20]
+    cols = np.stack([rng.integers(0, doms[0], n), rng.integers(0, doms[1], n)]).astype(np.int64)
+    cols[0, :7] = [0, 999, -1, 1000, 5000, 0, 999]
+    cols[1, :7] = [0, (1 << 20) - 1, 5, 6, 7, -(1 << 40), (1 << 20)]
+    attrs, edges = _star(2)
+    for m in (512, 1 << 17):
+        got = _run(attrs, edges, m, 6, 5, cols, None, doms)
+        keep = (cols[0] >= 0) & (cols[0] < doms[0]) & (cols[1] >= 0) & (cols[1] < doms[1])
+        q = O.canonical_query(attrs, edges)
+        co = O.draw_coefficients(5, 6, q.n_comp, len(q.edges))
+        ref = O.sketch_relation(q, co, 0, cols[:, keep], None, m, threads=16)
+        assert np.array_equal(got, ref), m
+
+
+def test_key_table_shared_attribute_queries(monkeypatch):
+    """Random tree queries where one attribute sits in several joins (its record carries
+    the product of those signs) and components span three relations; every relation of
+    the query is updated through the tables."""
+    monkeypatch.setenv("SK_KEY_TABLE", "1")
+    from tests._helpers import random_tree_query
+    rng = random.Random(11)
+    for trial in range(6):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 5), share_prob=0.6)
+        m = rng.choice([256, 1000, 1 << 15])
+        d = rng.choice([1, 4, 5, 11])
+        seed = rng.randrange(1 << 60)
+        s = pkg.SketchSet(attrs, edges, m, d, seed)
+        rels = []
+        for k, a in enumerate(attrs):
+            n = rng.randint(1000, 30000)
+            dom = [rng.randint(1, 3000) for _ in range(a)]
+            cols = np.stack([np.array([rng.randrange(x) for _ in range(n)], dtype=np.int64) for x in dom])
+            w = np.array([rng.choice([-1, 1, 2]) for _ in range(n)], dtype=np.int64)
+            s.update(k, torch.as_tensor(cols).cuda(), torch.as_tensor(w).cuda(), domain=dom)
+            rels.append((cols, w))
+        s.sync()
+        got = s.counters.cpu().numpy()
+        q = O.canonical_query(attrs, edges)
+        co = O.draw_coefficients(seed, d, q.n_comp, len(q.edges))
+        sk = O.sketch_all(q, co, rels, m)
+        for k in range(len(attrs)):
+            assert np.array_equal(got[k], sk[k]), (trial, k)
+        s.close()
+
+
+def test_key_table_auto_matches_direct_on_star_shape(monkeypatch):
+    """The default choice (tables when the domains are small against the batch) and the
+    per-tuple path give the same sketch on a 2e6-row (ragged last CTA), 5-column Zipf(1.1)
+    fact table."""
+    n, dom = 2_000_003, 100_000
+    cols = torch.stack([synth.zipf_keys(n, 1.1, dom, 500 + u, device="cuda") for u in range(5)])
+    attrs, edges = _star(5)
+    out = []
+    monkeypatch.delenv("SK_TAB_V8", raising=False)
+    for mode in ("", "0"):
+        monkeypatch.setenv("SK_KEY_TABLE", mode)
+        s = pkg.SketchSet(attrs, edges, 1 << 16, 9, 42)
+        s.update(0, cols, domain=[dom] * 5)
+        s.sync()
+        out.append(s.counters[0].cpu().numpy())
+        s.close()
+    assert np.array_equal(out[0], out[1])
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(42, 9, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co[[0, 8]], 0, cols.cpu().numpy(), None, 1 << 16, threads=16)
+    assert np.array_equal(out[0][0], ref[0]) and np.array_equal(out[0][8], ref[1])
+
+
+def test_key_table_from_page_locked_host_columns(monkeypatch):
+    """Columns and weights in page-locked host memory passed straight to the C ABI (the
+    kernels read them across the host link); the tables stay in device memory."""
+    monkeypatch.setenv("SK_KEY_TABLE", "1")
+    monkeypatch.delenv("SK_TAB_V8", raising=False)
+    n, doms = 300_001, [4000, 700, 90000]
+    cols = torch.stack([synth.zipf_keys(n, 1.2, x, 40 + u) for u, x in enumerate(doms)]).pin_memory()
+    w = torch.randint(-2, 3, (n,), dtype=torch.int64, generator=torch.Generator().manual_seed(9)).pin_memory()
+    attrs, edges = _star(3)
+    ref = None
+    for host in (True, False):
+        s = pkg.SketchSet(attrs, edges, 1 << 15, 9, 8)
+        c, ww = (cols, w) if host else (cols.cuda(), w.cuda())
+        pkg.sk_sketch_update_batch(s.handle, 0, n, c.data_ptr(), int(c.stride(0)), ww.data_ptr(), doms,
+                                   torch.cuda.current_stream().cuda_stream)
+        s.sync()
+        got = s.counters[0].cpu().numpy()
+        s.close()
+        if ref is None:
+            q = O.canonical_query(attrs, edges)
+            co = O.draw_coefficients(8, 9, q.n_comp, len(q.edges))
+            ref = O.sketch_relation(q, co, 0, cols.numpy(), w.numpy(), 1 << 15, threads=16)
+        assert np.array_equal(got, ref), host

@@ -130,8 +130,10 @@ def test_update_hot_key_cache_path(a, d, m, cached, monkeypatch):
 def test_update_shared_memory_path_warp_aggregation(agg, monkeypatch):
     """Shared-memory sub-sketch path with and without warp-aggregated atomics
     (SK_WARP_AGG=1): Zipf keys so lanes of a warp often hit the same counter, a domain
-    hint with violations (those tuples are skipped), signed weights."""
+    hint with violations (those tuples are skipped), signed weights.  Key tables are
+    turned off so the declared domain does not route the batch around the hashing kernel."""
     monkeypatch.setenv("SK_WARP_AGG", agg)
+    monkeypatch.setenv("SK_KEY_TABLE", "0")
     n = 100_003
     rng = np.random.default_rng(5)
     cols = np.stack([synth.zipf_keys(n, 1.3, 5000, 70 + c).numpy() for c in range(2)])
