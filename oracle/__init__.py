@@ -20,6 +20,7 @@ What each function follows:
   median_lower         median trick of Section 3.3 and the l = 5 medians of
                        Section 4.1
   exact_join_size      E[X] of Theorem 3.1 (the true join cardinality)
+  subquery             Section 3.4 (sub-queries for plan enumeration; sketch reuse)
 
 Every row of every estimate uses its own, independently drawn hash functions
 ("l i.i.d. estimates", Section 3.3).
@@ -495,6 +496,80 @@ def estimate(q: Query, sketches: Sequence[np.ndarray], root: int = 0, threads: i
     rr = list(range(d)) if rows is None else list(rows)
     vals = [estimate_row(q, [s[row].tolist() for s in sketches], root, threads) for row in rr]
     return Estimate(vals, median_lower(vals), mid_mean(vals))
+
+
+# --------------------------------------------------------------------------
+# sub-queries of one query (Section 3.4: plan enumeration)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SubQuery:
+    """One sub-query S of a query Q, given by a subset of Q's joins.
+
+    query      S in canonical numbering (canonical_query of its own relations/joins)
+    relations  the Q relation behind each S relation, ascending
+    keep       for each S relation, the attribute positions of its Q relation that S joins,
+               ascending (the columns an S relation's batch is made of)
+    coeffs     uint64 [d][2 * n_comp(S) + 4 * |E(S)|] in S's layout
+    """
+    query: Query
+    relations: List[int]
+    keep: List[List[int]]
+    coeffs: np.ndarray
+
+
+def subquery(num_join_attrs: Sequence[int], edges: Sequence[Tuple[int, int, int, int]], coeffs: np.ndarray,
+             chosen: Sequence[int]) -> SubQuery:
+    """The sub-query S of Q = (num_join_attrs, edges) made of the joins edges[i], i in chosen,
+    with hash functions inherited from Q's coefficients (the reading taken for the sketch
+    reuse of Section 3.4):
+      - each component of S takes the bin function of the component of Q containing it;
+      - a component of S with one join takes the sign function of the first join (lowest
+        canonical index) of the component of Q containing it; a component of S with two or
+        more joins takes, for each of its joins, the sign function Q gives that join.
+    In Figure 3, the two-way sub-queries {0, 1} and {1, 3} then sketch relation R1 (its
+    attribute 1) identically, which is the reuse the paper describes.  Because Q's relations
+    form a tree, a connected S has at most one component inside any component of Q, so the
+    functions S uses for different joins stay independent and Theorem 3.1 applies to S."""
+    q = canonical_query(num_join_attrs, edges)
+    picked = [tuple(int(v) for v in edges[i]) for i in sorted(set(int(i) for i in chosen))]
+    if not picked:
+        raise QueryError("INVALID", "a sub-query needs at least one join")
+    rels = sorted({e[0] for e in picked} | {e[2] for e in picked})
+    rel_new = {k: i for i, k in enumerate(rels)}
+    keep = [sorted({e[1] for e in picked if e[0] == k} | {e[3] for e in picked if e[2] == k}) for k in rels]
+    attr_new = {(k, a): j for k, ks in zip(rels, keep) for j, a in enumerate(ks)}
+    sub_edges = [(rel_new[ra], attr_new[(ra, aa)], rel_new[rb], attr_new[(rb, ab)]) for (ra, aa, rb, ab) in picked]
+    qs = canonical_query([len(ks) for ks in keep], sub_edges)
+    # global attribute of S -> global attribute of Q
+    to_q = [q.attr(rels[qs.rel_of[us]], keep[qs.rel_of[us]][us - qs.offsets[qs.rel_of[us]]]) for us in range(qs.w)]
+    # first join of every component of Q
+    first_join = {}
+    for jq, (u, v) in enumerate(q.edges):
+        first_join.setdefault(q.comp_of[u], jq)
+    joins_in_comp = [0] * qs.n_comp
+    for (us, vs) in qs.edges:
+        joins_in_comp[qs.comp_of[us]] += 1
+    d = coeffs.shape[0]
+    out = np.zeros((d, 2 * qs.n_comp + 4 * len(qs.edges)), dtype=np.uint64)
+    for c in range(qs.n_comp):
+        us = next(u for u in range(qs.w) if qs.comp_of[u] == c)
+        cq = q.comp_of[to_q[us]]
+        out[:, 2 * c:2 * c + 2] = coeffs[:, 2 * cq:2 * cq + 2]
+    for j, (us, vs) in enumerate(qs.edges):
+        u, v = to_q[us], to_q[vs]
+        if joins_in_comp[qs.comp_of[us]] == 1:
+            jq = first_join[q.comp_of[u]]
+        else:
+            jq = q.edges.index((min(u, v), max(u, v)))
+        out[:, 2 * qs.n_comp + 4 * j:2 * qs.n_comp + 4 * j + 4] = \
+            coeffs[:, 2 * q.n_comp + 4 * jq:2 * q.n_comp + 4 * jq + 4]
+    return SubQuery(qs, rels, keep, out)
+
+
+def subquery_relations(sq: SubQuery, relations) -> list:
+    """The batches of S's relations: each keeps the columns of its Q relation that S joins."""
+    return [(np.asarray(relations[k][0])[ks], relations[k][1]) for k, ks in zip(sq.relations, sq.keep)]
 
 
 # --------------------------------------------------------------------------
