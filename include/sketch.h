@@ -302,6 +302,92 @@ sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t c
  * (all sets, all devices), for accounting of GPU work. */
 int64_t sk_launch_count(void);
 
+/* ---------------------------------------------------------------------------
+ * Sub-query families (Section 3.4, integration with query optimizers).  A plan
+ * enumerator needs the cardinality of many sub-queries of one query Q; the
+ * sketches of all of them are built in one pass over each relation's tuples, and
+ * a relation's sketch is shared by every sub-query that sees the same view of it.
+ *
+ * A sub-query S is a non-empty subset of Q's joins (indices into query->edges)
+ * whose relations are connected.  Its relations are those its joins touch (in
+ * ascending order of their index in Q, which is S's relation numbering in the
+ * results), each keeping the attributes S joins (ascending).  Hash functions are
+ * drawn for Q exactly as sk_sketch_create draws them from `seed`, and S inherits
+ * them: each component of S takes the bin function of the component of Q that
+ * contains it; a component of S with one join takes the sign function of the
+ * first join (lowest canonical index) of its component of Q; a component of S
+ * with several joins takes each join's own sign function.  (With this choice the
+ * two-way sub-queries {0,1} and {1,3} of Figure 3 share relation R1's sketch, as
+ * the paper describes; S = Q gives exactly sk_sketch_create's functions.)  The
+ * view of relation R_k in S is, for every attribute S joins, the set of sign
+ * functions its value is hashed with; sub-queries with equal views of R_k share
+ * one d x m sketch.  The library owns the family's counters (views x d x m int64
+ * in device memory).
+ * ------------------------------------------------------------------------- */
+typedef struct sk_family sk_family;
+
+/* Largest number of views one relation may have in a family, and of sign
+ * functions ("slots": its joins plus its component's first join) its attributes
+ * may use together. */
+#define SK_MAX_VIEWS 64
+#define SK_MAX_SLOTS 64
+
+/* sk_family_create: n_sub sub-queries; sub-query i is the joins
+ * sub_edges[sub_offsets[i] .. sub_offsets[i+1]) (indices into query->edges,
+ * sub_offsets has n_sub + 1 entries, sub_offsets[0] = 0).  m, d, seed as for
+ * sk_sketch_create (the estimate needs 2 <= m <= 2^22, or <= 2^21 when m is not
+ * a power of two).  The counters are zeroed on cuda_stream.
+ * Errors: SK_ERR_INVALID_ARG (empty, repeated or out-of-range joins, a
+ * disconnected sub-query, too many views or slots), query validation codes,
+ * SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_NO_MEMORY, SK_ERR_CUDA. */
+sk_status sk_family_create(const sk_query* query, int32_t n_sub, const int32_t* sub_offsets,
+                           const int32_t* sub_edges, int64_t m, int32_t d, uint64_t seed, void* cuda_stream,
+                           sk_family** out);
+
+/* sk_family_update_batch: Algorithm 2 for a batch of Q's relation `relation`,
+ * laid out as for sk_sketch_update_batch (all |Omega(R_k)| columns of Q).  One
+ * pass hashes every tuple once per row and adds it to every view of R_k (each
+ * view with its own bin sum and sign product).  A relation in no sub-query is a
+ * no-op.  Domain violations are recorded and reported by sk_family_sync.
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_rows, const int64_t* dev_cols,
+                                 int64_t col_stride, const int64_t* dev_weights, const int64_t* domain_hint,
+                                 void* cuda_stream);
+
+/* sk_family_estimate: Algorithm 3 and the median for every sub-query; out has
+ * n_sub entries, entry i for sub-query i (as sk_estimate_join).  The sub-queries
+ * are estimated concurrently on the family's worker streams, which first wait
+ * for the work already queued on cuda_stream; the call returns when every
+ * estimate is on the host.  Returns the first error of any sub-query.
+ * Errors: as sk_estimate_join. */
+sk_status sk_family_estimate(sk_family* fam, sk_estimate* out, void* cuda_stream);
+
+/* sk_family_set_estimator: the correlation arithmetic of every sub-query (as
+ * sk_sketch_set_estimator). */
+sk_status sk_family_set_estimator(sk_family* fam, int32_t estimator);
+
+/* sk_family_info: number of sub-queries, total views (distinct sketches) and the
+ * bytes of counters they take.  Any output may be NULL. */
+sk_status sk_family_info(const sk_family* fam, int32_t* n_sub, int32_t* n_views, size_t* counter_bytes);
+
+/* sk_family_view: for relation rel_s of sub-query sub (S's numbering), the
+ * relation of Q it is and the index of its view (the same index for every
+ * sub-query sharing that sketch).  Errors: SK_ERR_INVALID_ARG. */
+sk_status sk_family_view(const sk_family* fam, int32_t sub, int32_t rel_s, int32_t* q_relation, int32_t* view);
+
+/* sk_family_copy_sketch: copies the d x m counters of relation rel_s of
+ * sub-query sub into host_out (int64 [d][m]) after the work queued on
+ * cuda_stream; synchronous.  Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_family_copy_sketch(const sk_family* fam, int32_t sub, int32_t rel_s, int64_t* host_out,
+                                void* cuda_stream);
+
+/* sk_family_reset: zeroes every view on cuda_stream.  sk_family_sync: waits for
+ * cuda_stream and returns (and clears) the first device-side error of the
+ * family's updates.  sk_family_destroy: frees the family. */
+sk_status sk_family_reset(sk_family* fam, void* cuda_stream);
+sk_status sk_family_sync(sk_family* fam, void* cuda_stream);
+sk_status sk_family_destroy(sk_family* fam);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,7 +82,10 @@ EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_
            "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
            "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
            "sk_estimate_join_noalloc", "sk_sketch_set_estimator", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_get_config",
-           "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy"]
+           "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy",
+           "sk_family_create", "sk_family_update_batch", "sk_family_estimate", "sk_family_set_estimator",
+           "sk_family_info", "sk_family_view", "sk_family_copy_sketch", "sk_family_reset", "sk_family_sync",
+           "sk_family_destroy"]
 
 _lib = None
 
@@ -121,6 +124,17 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_update_plan_set_config.argtypes = [vp, ctypes.POINTER(sk_update_plan_config)]
     L.sk_update_plan_autotune.argtypes = [vp, vp, ctypes.POINTER(sk_update_plan_config), ctypes.POINTER(ctypes.c_double)]
     L.sk_update_plan_destroy.argtypes = [vp]
+    L.sk_family_create.argtypes = [qp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), i64, i32, u64, vp,
+                                   ctypes.POINTER(vp)]
+    L.sk_family_update_batch.argtypes = [vp, i32, i64, vp, i64, vp, vp, vp]
+    L.sk_family_estimate.argtypes = [vp, ctypes.POINTER(sk_estimate), vp]
+    L.sk_family_set_estimator.argtypes = [vp, i32]
+    L.sk_family_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(sz)]
+    L.sk_family_view.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.sk_family_copy_sketch.argtypes = [vp, i32, i32, ctypes.POINTER(i64), vp]
+    L.sk_family_reset.argtypes = [vp, vp]
+    L.sk_family_sync.argtypes = [vp, vp]
+    L.sk_family_destroy.argtypes = [vp]
     L.sk_launch_count.argtypes = []
     L.sk_launch_count.restype = i64
     for name in EXPORTS:
@@ -384,6 +398,149 @@ class UpdatePlan:
     def close(self) -> None:
         if self.handle is not None:
             sk_update_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- sub-query families (Section 3.4) ---------------------------------------------------
+
+def sk_family_create(query: sk_query, subqueries: Sequence[Sequence[int]], m: int, d: int, seed: int,
+                     stream: int) -> int:
+    offs = [0]
+    flat: List[int] = []
+    for sub in subqueries:
+        flat.extend(int(i) for i in sub)
+        offs.append(len(flat))
+    oa = (ctypes.c_int32 * len(offs))(*offs)
+    ea = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+    h = ctypes.c_void_p(0)
+    _check(load().sk_family_create(ctypes.byref(query), len(subqueries), oa, ea, m, d,
+                                   seed & 0xFFFF_FFFF_FFFF_FFFF, stream, ctypes.byref(h)), "sk_family_create")
+    return h.value
+
+
+def sk_family_update_batch(handle: int, relation: int, n_rows: int, dev_cols: int, col_stride: int,
+                           dev_weights: Optional[int], domain_hint: Optional[Sequence[int]], stream: int) -> None:
+    dom = None
+    if domain_hint is not None:
+        dom = (ctypes.c_int64 * len(domain_hint))(*[int(v) for v in domain_hint])
+    _check(load().sk_family_update_batch(handle, relation, n_rows, dev_cols, col_stride, dev_weights or None,
+                                         ctypes.cast(dom, ctypes.c_void_p) if dom is not None else None, stream),
+           "sk_family_update_batch")
+
+
+def sk_family_info(handle: int) -> Tuple[int, int, int]:
+    n, v, b = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_size_t(0)
+    _check(load().sk_family_info(handle, ctypes.byref(n), ctypes.byref(v), ctypes.byref(b)), "sk_family_info")
+    return n.value, v.value, b.value
+
+
+def sk_family_estimate(handle: int, stream: int):
+    n = sk_family_info(handle)[0]
+    out = (sk_estimate * n)()
+    _check(load().sk_family_estimate(handle, out, stream), "sk_family_estimate")
+    return out
+
+
+def sk_family_set_estimator(handle: int, estimator: str) -> None:
+    _check(load().sk_family_set_estimator(handle, ESTIMATORS[estimator]), "sk_family_set_estimator")
+
+
+def sk_family_view(handle: int, sub: int, rel_s: int) -> Tuple[int, int]:
+    q, v = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().sk_family_view(handle, sub, rel_s, ctypes.byref(q), ctypes.byref(v)), "sk_family_view")
+    return q.value, v.value
+
+
+def sk_family_copy_sketch(handle: int, sub: int, rel_s: int, d: int, m: int, stream: int):
+    import numpy as np
+    out = np.zeros((d, m), dtype=np.int64)
+    _check(load().sk_family_copy_sketch(handle, sub, rel_s, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        stream), "sk_family_copy_sketch")
+    return out
+
+
+def sk_family_reset(handle: int, stream: int) -> None:
+    _check(load().sk_family_reset(handle, stream), "sk_family_reset")
+
+
+def sk_family_sync(handle: int, stream: int) -> None:
+    _check(load().sk_family_sync(handle, stream), "sk_family_sync")
+
+
+def sk_family_destroy(handle: int) -> None:
+    _check(load().sk_family_destroy(handle), "sk_family_destroy")
+
+
+def _estimate_dict(e) -> dict:
+    rows = [e.row[i].value() for i in range(e.d)]
+    return {"median": e.median.value(), "rows": rows, "fits_i64": bool(e.fits_i64), "median_i64": e.median_i64,
+            "median_f64": e.median_f64, "mid_mean_f64": e.mid_mean_f64, "max_residual": e.max_residual,
+            "max_limbs": e.max_limbs, "limb_bits": e.limb_bits, "corr_steps": e.corr_steps, "retries": e.retries}
+
+
+class SketchFamily:
+    """The sketches of many sub-queries of one query (plan enumeration, Section 3.4): each
+    sub-query is a list of indices into `edges`; relations are updated once, with Q's
+    columns, and every sub-query is estimated by estimate()."""
+
+    def __init__(self, num_join_attrs: Sequence[int], edges: Sequence[Tuple[int, int, int, int]],
+                 subqueries: Sequence[Sequence[int]], m: int, d: int, seed: int):
+        import torch
+        self._torch = torch
+        self.num_join_attrs = list(num_join_attrs)
+        self.edges = [tuple(e) for e in edges]
+        self.subqueries = [list(s) for s in subqueries]
+        self.m, self.d, self.seed = int(m), int(d), int(seed)
+        self.query, self._keep = make_query(self.num_join_attrs, self.edges)
+        self.handle = None
+        self.handle = sk_family_create(self.query, self.subqueries, self.m, self.d, self.seed, self._stream())
+
+    def _stream(self) -> int:
+        return self._torch.cuda.current_stream().cuda_stream
+
+    def update(self, relation: int, cols, weights=None, domain: Optional[Sequence[int]] = None) -> None:
+        t = self._torch
+        assert cols.dtype == t.int64 and cols.is_cuda and cols.dim() == 2
+        n = int(cols.shape[1])
+        assert n == 0 or cols.stride(1) == 1
+        wp = None
+        if weights is not None:
+            assert weights.dtype == t.int64 and weights.is_cuda and weights.is_contiguous()
+            wp = weights.data_ptr()
+        sk_family_update_batch(self.handle, relation, n, cols.data_ptr(), int(cols.stride(0)) if n else 0, wp,
+                               domain, self._stream())
+
+    def estimate(self) -> List[dict]:
+        return [_estimate_dict(e) for e in sk_family_estimate(self.handle, self._stream())]
+
+    def info(self) -> dict:
+        n, v, b = sk_family_info(self.handle)
+        return {"subqueries": n, "views": v, "counter_bytes": b}
+
+    def view(self, sub: int, rel_s: int) -> Tuple[int, int]:
+        return sk_family_view(self.handle, sub, rel_s)
+
+    def sketch(self, sub: int, rel_s: int):
+        return sk_family_copy_sketch(self.handle, sub, rel_s, self.d, self.m, self._stream())
+
+    def set_estimator(self, estimator: str) -> None:
+        sk_family_set_estimator(self.handle, estimator)
+
+    def reset(self) -> None:
+        sk_family_reset(self.handle, self._stream())
+
+    def sync(self) -> None:
+        sk_family_sync(self.handle, self._stream())
+
+    def close(self) -> None:
+        if self.handle is not None:
+            sk_family_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

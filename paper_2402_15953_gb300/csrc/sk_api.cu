@@ -47,13 +47,7 @@ struct SplitMix64 {
   }
 };
 
-struct Canon {
-  int r = 0;
-  std::vector<int> num_join_attrs, offsets, rel_of, comp_of;
-  std::vector<std::pair<int, int>> edges;
-  std::vector<std::vector<int>> gamma, incident;
-  int n_comp = 0;
-};
+using Canon = QueryInfo;
 
 int find_root(std::vector<int>& parent, int x) {
   while (parent[x] != x) {
@@ -238,6 +232,51 @@ void free_set(sk_set* s) {
 }
 
 }  // namespace
+
+sk_status query_info(const sk_query* q, QueryInfo* out) { return canonicalize(q, out); }
+
+std::vector<uint64_t> draw_coefficients(uint64_t seed, int d, int row_len) {
+  SplitMix64 rng{seed};
+  std::vector<uint64_t> v((size_t)d * row_len);
+  for (auto& x : v) x = rng.field_element();
+  return v;
+}
+
+sk_status make_estimation_set(const QueryInfo& c, int64_t m, int d, uint64_t seed, std::vector<uint64_t> h_coef,
+                              std::vector<int64_t*> rel_ctr, sk_set** out) {
+  *out = nullptr;
+  if ((int)rel_ctr.size() != c.r) return SK_ERR_INVALID_ARG;
+  sk_set* s = new (std::nothrow) sk_set();
+  if (!s) return SK_ERR_NO_MEMORY;
+  s->r = c.r;
+  s->m = m;
+  s->d = d;
+  s->seed = seed;
+  s->num_join_attrs = c.num_join_attrs;
+  s->offsets = c.offsets;
+  s->rel_of = c.rel_of;
+  s->comp_of = c.comp_of;
+  s->edges = c.edges;
+  s->gamma = c.gamma;
+  s->incident = c.incident;
+  s->n_comp = c.n_comp;
+  s->coef_row_len = 2 * c.n_comp + 4 * (int)c.edges.size();
+  s->h_coef = std::move(h_coef);
+  s->rel_ctr = std::move(rel_ctr);
+  cudaGetDevice(&s->device);
+  cudaError_t e = cudaMalloc(&s->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_set(s);
+    return set_status_from_cuda(e);
+  }
+  build_plan(s);
+  *out = s;
+  return SK_OK;
+}
+
+void destroy_set(sk_set* s) { free_set(s); }
+
 }  // namespace sk
 
 using namespace sk;
@@ -303,12 +342,11 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
   s->coef_row_len = 2 * c.n_comp + 4 * (int)c.edges.size();
   s->counters = (int64_t*)dev_counters;
   s->counter_bytes = need;
+  for (int k = 0; k < c.r; k++) s->rel_ctr.push_back(s->counters + (size_t)k * d * m);
   cudaGetDevice(&s->device);
   // Algorithm 1, SampleBinHashes / SampleSignHashes: per row, (b0, b1) for every
   // component, then (s0, s1, s2, s3) for every join, in canonical order.
-  SplitMix64 rng{seed};
-  s->h_coef.resize((size_t)d * s->coef_row_len);
-  for (auto& v : s->h_coef) v = rng.field_element();
+  s->h_coef = draw_coefficients(seed, d, s->coef_row_len);
   cudaError_t e = cudaMalloc(&s->d_status, sizeof(int));
   if (e != cudaSuccess) {
     free_set(s);

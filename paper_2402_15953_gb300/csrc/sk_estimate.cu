@@ -760,13 +760,12 @@ __global__ void k_nrecombine(NttArgs p, const uint64_t* __restrict__ Y) {
 // host orchestration
 // ---------------------------------------------------------------------------
 int grid_for(int64_t n, int threads = 256) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {   // thread-safe one-time initialisation
+    int dev = 0, x = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, dev);
+    return x > 0 ? x : 1;
+  }();
   int64_t g = (n + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
 }
@@ -1037,7 +1036,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
       if (failed >= 0) break;
       if (op.kind == OP_LEAF) {
         SK_CK(cudaMemsetAsync(d_bits + phys[op.dst], 0, sizeof(int), st));
-        k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm, d_bits + phys[op.dst]);
+        k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->rel_ctr[op.rel], dm, d_bits + phys[op.dst]);
         count_launch();
         SK_CK(cudaGetLastError());
       } else if (op.kind == OP_HAD) {
@@ -1254,7 +1253,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
 
   for (const EstOp& op : s->plan) {
     if (op.kind == OP_LEAF) {
-      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->counters + (size_t)op.rel * dm, dm, nullptr);
+      k_leaf<<<eg, 256, 0, st>>>(slot(op.dst), s->rel_ctr[op.rel], dm, nullptr);
       count_launch();
       SK_CK(cudaGetLastError());
     } else if (op.kind == OP_HAD) {

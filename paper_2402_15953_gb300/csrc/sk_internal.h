@@ -42,6 +42,16 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+// Canonical numbering of a query (Section 2.6 notation): attributes numbered relation by
+// relation, joins (u, v) with u < v sorted, components numbered by smallest attribute.
+struct QueryInfo {
+  int r = 0;
+  std::vector<int> num_join_attrs, offsets, rel_of, comp_of;
+  std::vector<std::pair<int, int>> edges;
+  std::vector<std::vector<int>> gamma, incident;
+  int n_comp = 0;
+};
+
 }  // namespace sk
 
 struct sk_set {
@@ -58,6 +68,7 @@ struct sk_set {
   std::vector<uint64_t> h_coef;                // [d][coef_row_len]
   std::vector<sk::RelPlan> rel;                // per relation
   int64_t* counters = nullptr;                 // caller-owned int64 [r][d][m]
+  std::vector<int64_t*> rel_ctr;               // per relation: its d x m counters (the estimator reads these)
   size_t counter_bytes = 0;
   int* d_status = nullptr;                     // first device-side error, 0 = none
   std::vector<sk::EstOp> plan;                 // Algorithm 3 schedule
@@ -88,5 +99,12 @@ void free_estimator(sk_set* s);
 // sk_api.cu
 sk_status set_status_from_cuda(cudaError_t e);
 void count_launch(int n = 1);   // adds to the process-wide kernel-launch counter
+sk_status query_info(const sk_query* q, QueryInfo* out);   // validation + canonical numbering
+// Algorithm 1's draw: d rows of row_len field elements from SplitMix64(seed)
+std::vector<uint64_t> draw_coefficients(uint64_t seed, int d, int row_len);
+// A set used only for estimation: its relations' counters are rel_ctr (owned elsewhere).
+sk_status make_estimation_set(const QueryInfo& c, int64_t m, int d, uint64_t seed, std::vector<uint64_t> h_coef,
+                              std::vector<int64_t*> rel_ctr, sk_set** out);
+void destroy_set(sk_set* s);
 
 }  // namespace sk

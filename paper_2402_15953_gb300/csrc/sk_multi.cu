@@ -98,13 +98,12 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
 }
 
 int sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {   // thread-safe one-time initialisation
+    int dev = 0, x = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+    cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, dev);
+    return x > 0 ? x : 1;
+  }();
   return n;
 }
 

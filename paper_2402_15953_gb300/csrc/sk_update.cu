@@ -414,13 +414,12 @@ size_t key_table_max_bytes() {
 }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  static const int n = [] {   // thread-safe one-time initialisation
+    int dev = 0, x = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
+    cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, dev);
+    return x > 0 ? x : 1;
+  }();
   return n;
 }
 
