@@ -47,7 +47,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tuples", type=int, default=1_000_000)
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "serving", "chain3", "chain8"],
+    ap.add_argument("--workload", default="star",
+                    choices=["star", "batched", "serving", "chain3", "chain8", "subqueries"],
                     help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
                          "launches; serving: request loop latency")
     ap.add_argument("--requests", type=int, default=4000)
@@ -798,6 +799,102 @@ def run_small_config(args, world, rank, which):
         print(json.dumps(line), flush=True)
 
 
+def run_subqueries(args, world, rank):
+    """Plan enumeration (Section 3.4): the star join F(K1..K4) x D1..D4 (F 2e7 rows, 4 Zipf(1.1)
+    columns over [0, 1e6); D_i 1e6 uniform rows; m = 2^16, d = 9) and all 15 of its connected
+    sub-queries (every non-empty subset of the 4 joins).  A step resets the sketches, updates
+    every relation and estimates every sub-query.  Family: one sk_family (one pass per relation,
+    19 shared view sketches, sub-queries estimated on worker streams).  Against: one
+    SketchSet per sub-query (47 relation sketches, each relation updated once per sub-query it
+    is in, estimates one after another)."""
+    import itertools
+
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    import synth
+    from paper_2402_15953_gb300 import build as pkg_build
+    pkg_build.build()
+    n_fact, n_dim, k = 20_000_000, 1_000_000, 4
+    wl = synth.star(n_fact=n_fact, n_dim=n_dim, k=k, seed=42 + rank, device="cuda")
+    subs = [list(c) for size in range(1, k + 1) for c in itertools.combinations(range(k), size)]
+    stream = torch.cuda.current_stream()
+    total = sum(r.n for r in wl.relations)
+
+    fam = pkg.SketchFamily(wl.num_join_attrs, wl.edges, subs, wl.m, wl.d, wl.hash_seed)
+
+    def fam_step():
+        fam.reset()
+        for kk, rel in enumerate(wl.relations):
+            fam.update(kk, rel.cols)
+        return fam.estimate()
+
+    # one SketchSet per sub-query, over the columns that sub-query joins
+    naive = []
+    for sub in subs:
+        dims = [1 + j for j in sub]
+        attrs = [len(sub)] + [1] * len(sub)
+        edges = [(0, t, 1 + t, 0) for t in range(len(sub))]
+        fcols = wl.relations[0].cols[sub].contiguous() if len(sub) < k else wl.relations[0].cols
+        naive.append((pkg.SketchSet(attrs, edges, wl.m, wl.d, wl.hash_seed),
+                      [fcols] + [wl.relations[dd].cols for dd in dims]))
+
+    def naive_step():
+        outs = []
+        for sset, cols in naive:
+            sset.reset()
+            for kk, c in enumerate(cols):
+                sset.update(kk, c)
+            outs.append(sset.estimate())
+        return outs
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps, out
+
+    reps = max(3, args.steps // 3)
+    launches0 = pkg.sk_launch_count()
+    fam_ms, fam_out = timed(fam_step, reps)
+    launches = (pkg.sk_launch_count() - launches0) // (reps + max(1, args.warmup))
+    # update alone (device time)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fam.reset()
+        for kk, rel in enumerate(wl.relations):
+            fam.update(kk, rel.cols)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fam_upd_ms = e0.elapsed_time(e1) / reps
+    naive_ms, naive_out = timed(naive_step, reps)
+    info = fam.info()
+    same_full = fam_out[-1]["rows"] == naive_out[-1]["rows"]
+    line = {"metric": "sub-query family: estimates/s of all connected sub-queries with their updates",
+            "value": world * len(subs) / (fam_ms / 1e3), "unit": "sub-query estimates/s", "n_gpus": world,
+            "steps": reps, "warmup": args.warmup, "ms_per_step": fam_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"star F(K1..K{k}) {n_fact:.0e} rows Zipf 1.1 over [0,1e6), D_i {n_dim:.0e} "
+                                   f"uniform; m=65536, d=9; all {len(subs)} connected sub-queries",
+                       "tuples_per_step": total},
+            "family": {"ms_per_step": fam_ms, "update_ms": fam_upd_ms, "estimate_ms": fam_ms - fam_upd_ms,
+                       "views": info["views"], "counter_bytes": info["counter_bytes"],
+                       "gpu_launches_per_step": launches},
+            "one_set_per_subquery": {"ms_per_step": naive_ms, "relation_sketches": sum(len(c) for _, c in naive)},
+            "speedup": naive_ms / fam_ms,
+            "full_query_rows_equal_plain_set": same_full}
+    for sset, _ in naive:
+        sset.close()
+    fam.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
@@ -809,6 +906,8 @@ def main():
         run_serving(args, world, rank)
     elif args.workload in ("chain3", "chain8"):
         run_small_config(args, world, rank, args.workload)
+    elif args.workload == "subqueries":
+        run_subqueries(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
