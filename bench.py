@@ -450,8 +450,10 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         staged = run_e2e(args, s, wl, stream, world)
         direct = run_e2e_direct(args, s, wl, stream, world)
-        line["e2e"] = direct if direct["value"] >= staged["value"] else staged
-        line["e2e_alternatives"] = {"staged_copies": staged, "direct_host_reads": direct}
+        direct_p = run_e2e_direct_pipelined(args, wl, world)
+        alts = {"staged_copies": staged, "direct_host_reads": direct, "direct_host_reads_pipelined": direct_p}
+        line["e2e"] = max(alts.values(), key=lambda x: x["value"])
+        line["e2e_alternatives"] = alts
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         ns = min(args.cpu_sample_tuples, args.fact_rows)
         cols = [c[:, :ns].cpu().numpy() for c in rels]
@@ -747,6 +749,56 @@ def run_e2e_direct(args, s, wl, stream, world):
     d2h = 4 * (256 + (1 + 3 * d) * 8) + 2 * d * 32 + 4
     return {"value": world * total / dt, "unit": "tuples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": dt * 1e3, "steps": steps, "method": "kernels read pinned host columns directly"}
+
+
+def run_e2e_direct_pipelined(args, wl, world):
+    """As run_e2e_direct, with two sketch sets so that step i's estimate (device work plus its
+    read-back) runs while step i+1's update kernels read the next batch across the host link:
+    every step still moves all of its key columns from host memory and reads back its
+    estimate inside the timed region."""
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    host = [r.cols.cpu().pin_memory() for r in wl.relations]
+    h2d = sum(h.numel() * 8 for h in host)
+    doms = declared_domains(args, wl)
+    sets = [pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed) for _ in range(2)]
+    upd, est = torch.cuda.Stream(), torch.cuda.Stream()
+    done = [torch.cuda.Event() for _ in range(2)]
+
+    def run(k_steps):
+        outs = []
+        for i in range(k_steps + 1):
+            if i < k_steps:
+                with torch.cuda.stream(upd):
+                    cur = sets[i % 2]
+                    cur.reset()
+                    for k, h in enumerate(host):
+                        pkg.sk_sketch_update_batch(cur.handle, k, int(h.shape[1]), h.data_ptr(), int(h.stride(0)),
+                                                   None, doms[k], upd.cuda_stream)
+                    done[i % 2].record(upd)
+            if i >= 1:
+                with torch.cuda.stream(est):
+                    est.wait_event(done[(i - 1) % 2])
+                    outs.append(sets[(i - 1) % 2].estimate())
+        return outs
+
+    run(max(1, args.warmup))
+    torch.cuda.synchronize()
+    barrier(world)
+    steps = max(3, args.steps // 3)
+    t0 = time.perf_counter()
+    outs = run(steps)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+    for x in sets:
+        x.close()
+    total = sum(h.shape[1] for h in host)
+    d = wl.d
+    d2h = 4 * (256 + (1 + 3 * d) * 8) + 2 * d * 32 + 4
+    return {"value": world * total / dt, "unit": "tuples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": steps, "estimates": len(outs),
+            "method": "kernels read pinned host columns directly; step i's estimate overlaps step i+1's reads"}
 
 
 def run_small_config(args, world, rank, which):
