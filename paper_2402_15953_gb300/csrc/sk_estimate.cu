@@ -759,13 +759,18 @@ __global__ void k_nrecombine(NttArgs p, const uint64_t* __restrict__ Y) {
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
-int grid_for(int64_t n, int threads = 256) {
+int num_sms() {
   static const int sms = [] {   // thread-safe one-time initialisation
     int dev = 0, x = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, dev);
     return x > 0 ? x : 1;
   }();
+  return sms;
+}
+
+int grid_for(int64_t n, int threads = 256) {
+  const int sms = num_sms();
   int64_t g = (n + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
 }
@@ -836,6 +841,11 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   const int budget = R >= 1024 ? (128 << 10) : (64 << 10);
   int cb = std::max(1, std::min(C, budget / (R * esz)));
   int rb = std::max(1, std::min(R, budget / (C * esz)));
+  // narrower tiles until the grid gives every SM two CTAs (a small batch of vectors would
+  // otherwise leave SMs idle); at least 4 columns per tile keep the column loads sector-wide
+  const int64_t want = 2 * (int64_t)num_sms();
+  while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
+  while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
   const size_t smc = (size_t)cb * R * esz, smr = (size_t)rb * C * esz;
   SK_CK(cudaFuncSetAttribute(k_xf_cols<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
   SK_CK(cudaFuncSetAttribute(k_xf_rows<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
