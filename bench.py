@@ -66,6 +66,13 @@ def declared_domains(args, wl):
     return [None] * wl.r if args.no_domains else wl.domains
 
 
+def star_config(args, total: int) -> dict:
+    """The workload description both arms print (the same keys and values)."""
+    return {"workload": workload_name(args), "relations": 6, "tuples_per_step": total, "m": 65536, "d": 9,
+            "key_domains": "undeclared" if args.no_domains else "declared [0, 1e6) per column",
+            "l2": "inputs (4.2 GB of keys) larger than L2; no flush needed"}
+
+
 def workload_name(args) -> str:
     return (f"star join F(K1..K5) x D1..D5: F {args.fact_rows:.0e} rows Zipf s=1.1 over [0,1e6), "
             f"D_i {args.dim_rows:.0e} rows uniform over [0,1e6); m=65536, d=9, seed 42")
@@ -241,7 +248,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "tuples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "tuples_per_step": total},
+            "config": star_config(args, total),
             "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": desc, "value": val, "unit": "tuples/s"},
             "e2e": {"value": val, "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -431,9 +438,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "relations": 6, "tuples_per_step": total, "m": wl.m, "d": wl.d,
-                   "key_domains": "declared [0, 1e6) per column" if tables else "undeclared",
-                   "l2": "inputs (4.2 GB of keys) larger than L2; no flush needed",
+        "config": {**star_config(args, total),
                    "parallelism": f"replicas x{world}",
                    "pipelined": pipe is not None and value == pipe["value"]},
         "serial_steps": serial, "pipelined_steps": pipe,

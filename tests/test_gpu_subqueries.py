@@ -137,3 +137,25 @@ def test_invalid_subqueries():
     fam = pkg.SketchFamily(attrs, edges, [[0, 1], [1, 2]], 64, 3, 1)
     assert fam.info()["subqueries"] == 2
     fam.close()
+
+
+def test_six_attribute_relation_and_view_limit():
+    """A star whose fact relation joins 6 attributes (the update kernel's runtime-arity
+    path), d = 13, sub-queries of one to six joins; then a 7-dimension star asking for all
+    127 sub-queries, which gives the fact relation more views than SK_MAX_VIEWS allows."""
+    rng = random.Random(21)
+    k = 6
+    attrs, edges = [k] + [1] * k, [(0, t, 1 + t, 0) for t in range(k)]
+    subs = [[0], [5], [1, 2], [0, 3, 5], [1, 2, 3, 4], list(range(k))]
+    rels = _relations(rng, attrs, 3000, 25)
+    fam, _ = _check_family(attrs, edges, subs, rels, 512, 13, 31337)
+    fam.close()
+    k = 7
+    attrs, edges = [k] + [1] * k, [(0, t, 1 + t, 0) for t in range(k)]
+    subs = [s for s in connected_subsets(attrs, edges)]
+    assert len(subs) == 127
+    with pytest.raises(pkg.SketchError):
+        pkg.SketchFamily(attrs, edges, subs, 64, 3, 1)
+    fam = pkg.SketchFamily(attrs, edges, subs[:64], 64, 3, 1)
+    assert fam.info()["subqueries"] == 64
+    fam.close()
