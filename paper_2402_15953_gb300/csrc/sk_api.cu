@@ -18,6 +18,19 @@ static std::atomic<int64_t> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+cudaError_t allow_dynamic_smem(const void* func) {
+  static const int optin = [] {   // thread-safe one-time initialisation
+    int dev = 0, x = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return x > 0 ? x : 48 * 1024;
+  }();
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 sk_status set_status_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return SK_OK;
   if (e == cudaErrorMemoryAllocation) return SK_ERR_NO_MEMORY;

@@ -831,7 +831,7 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
     const int vpc = (int)std::max<int64_t>(1, std::min<int64_t>(4096 / L, batch));
     const int64_t grid = (batch + vpc - 1) / vpc;
     const size_t smem = (size_t)vpc * L * esz;
-    SK_CK(cudaFuncSetAttribute(k_xf_small<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SK_CK(allow_dynamic_smem((const void*)k_xf_small<Ops>));
     k_xf_small<Ops><<<(unsigned)grid, 256, smem, st>>>(src, dst, batch, logm, vpc, tw, 1, inv, r4);
     count_launch();
     return set_status_from_cuda(cudaGetLastError());
@@ -847,8 +847,8 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
   while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
   const size_t smc = (size_t)cb * R * esz, smr = (size_t)rb * C * esz;
-  SK_CK(cudaFuncSetAttribute(k_xf_cols<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-  SK_CK(cudaFuncSetAttribute(k_xf_rows<Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  SK_CK(allow_dynamic_smem((const void*)k_xf_cols<Ops>));
+  SK_CK(allow_dynamic_smem((const void*)k_xf_rows<Ops>));
   k_xf_cols<Ops><<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv, r4);
   count_launch();
   SK_CK(cudaGetLastError());

@@ -99,6 +99,12 @@ void free_estimator(sk_set* s);
 // sk_api.cu
 sk_status set_status_from_cuda(cudaError_t e);
 void count_launch(int n = 1);   // adds to the process-wide kernel-launch counter
+// Raises kernel func's dynamic shared-memory limit to the most it can have: the device's
+// opt-in limit per block less the kernel's static shared memory.  Every kernel always gets
+// this one value: the attribute is process-wide per kernel, so per-call sizes would let a
+// concurrent caller (estimate worker threads) lower it between another thread's set and
+// launch, failing that launch.  Launches still request only what they use.
+cudaError_t allow_dynamic_smem(const void* func);
 sk_status query_info(const sk_query* q, QueryInfo* out);   // validation + canonical numbering
 // Algorithm 1's draw: d rows of row_len field elements from SplitMix64(seed)
 std::vector<uint64_t> draw_coefficients(uint64_t seed, int d, int row_len);

@@ -221,7 +221,7 @@ sk_status sk_update_plan_run(sk_update_plan* pl, void* cuda_stream) {
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return set_status_from_cuda(e);
-  e = cudaFuncSetAttribute(k_update_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes);
+  e = allow_dynamic_smem((const void*)k_update_multi);
   if (e != cudaSuccess) return set_status_from_cuda(e);
   const int64_t want = pl->total_chunks;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * pl->cfg.ctas_per_sm));

@@ -110,7 +110,7 @@ cudaError_t launch_tab(const UpdArgs& a, const TabArgs& t, int grid, size_t smem
   auto kern = t.narrow ? (v8 ? k_update_tab<A, POW2, SMEM, true, true> : k_update_tab<A, POW2, SMEM, true, false>)
                        : (v8 ? k_update_tab<A, POW2, SMEM, false, true> : k_update_tab<A, POW2, SMEM, false, false>);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem((const void*)kern);
     if (e != cudaSuccess) return e;
   }
   kern<<<grid, 256, smem, st>>>(a, t);
@@ -145,7 +145,7 @@ int update_grid_per_sm(int resident) {
 template <int A, bool POW2, bool SMEM>
 cudaError_t launch_one(const UpdArgs& a, int grid, size_t smem, cudaStream_t st) {
   auto kern = k_update<A, POW2, SMEM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   if (grid <= 0) {
     int per_sm = 0;
@@ -362,7 +362,7 @@ size_t cached_smem_bytes(int A, int d, int row_len, int log2s, int warps) {
 template <int A>
 cudaError_t launch_cached(const UpdArgs& a, int grid, int threads, size_t smem, CacheLayout c, cudaStream_t st) {
   auto kern = k_update_cached<A>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   kern<<<grid, threads, smem, st>>>(a, c);
   count_launch();
@@ -484,7 +484,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
         a.smem_wmax = 0;
         auto kb = pow2 ? k_key_table<true> : k_key_table<false>;
         e = cudaSuccess;
-        if (coef_bytes > 48 * 1024) e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coef_bytes);
+        if (coef_bytes > 48 * 1024) e = allow_dynamic_smem((const void*)kb);
         if (e == cudaSuccess) {
           const int bgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 32);
           kb<<<bgrid, 256, coef_bytes, st>>>(a, t);
