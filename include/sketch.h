@@ -226,7 +226,9 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
  * cross-correlation (Definition 3.1); both give the identical exact result.
  *   SK_ESTIMATOR_FFT64 (default): FP64 FFTs on signed limbs, outputs rounded to
  *     integers and certified (largest distance to an integer <= 1/4, exact row-sum
- *     identity), redone with narrower limbs if the certificate fails;
+ *     identity and, for power-of-two m, Z(w) = A(1/w) X(w) modulo 2^64 - 2^32 + 1 at
+ *     a random primitive m-th root of unity w), redone with narrower limbs if the
+ *     certificate fails;
  *   SK_ESTIMATOR_NTT: number-theoretic transforms over GF(2^64 - 2^32 + 1) on signed
  *     limbs narrow enough that every output lies below q/2 in magnitude, exact by
  *     construction (GB300's integer pipes are much faster than its FP64 pipe).

@@ -16,9 +16,10 @@
 // nearest integer and recombines z = sum_s 2^(B s) round(y_s) exactly.  B is
 // picked from a worst-case rounding-error model so the FFT error stays far below
 // 1/2; each step is then certified a posteriori: the largest distance of an
-// output to its nearest integer must be <= 1/4 and, per row, the exact identity
-// sum_j z_j = (sum_j a_j)(sum_j x_j) must hold.  A failed certificate redoes
-// the step with narrower limbs.
+// output to its nearest integer must be <= 1/4, per row the exact identity
+// sum_j z_j = (sum_j a_j)(sum_j x_j) must hold mod 2^64 and, for power-of-two m,
+// Z(w) = A(1/w) X(w) mod 2^64 - 2^32 + 1 at a random primitive m-th root of unity w.
+// A failed certificate redoes the step with narrower limbs.
 //
 // FFTs: radix-2 decimation-in-time in shared memory; widths up to 2^12 in one
 // pass, wider ones (up to 2^22) as a four-step transform m = R x C (column FFTs
@@ -490,6 +491,78 @@ __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::
     const int rr = idx % rb, k2 = idx / rb;
     vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[rr * C + k2];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation certificate of an FP64 correlation step (power-of-two m).  For z = a star x
+// (Definition 3.1) and any m-th root of unity w in GF(q), q = 2^64 - 2^32 + 1,
+//   sum_j z_j w^j = sum_i a_i w^-i * sum_k x_k w^k        (w^m = 1, k = i + j mod m),
+// so Z(w) = A(1/w) X(w).  With w a random primitive m-th root, a wrong z_j passes with
+// probability at most (m - 1) / q.  Each block sums one chunk of one row (consecutive
+// threads read consecutive elements); k_eval_final adds the chunks.
+// ---------------------------------------------------------------------------
+struct EvalArgs {
+  const I256* a;
+  const I256* x;
+  const I256* z;
+  int64_t m;
+  int nchunk;
+  uint64_t w, winv;            // w and 1/w
+  uint64_t wstep, winvstep;    // w^blockDim and its inverse
+  uint64_t e1, e2, e3, e4;     // 2^64k mod q, k = 1..4
+  uint64_t* part;              // [d][nchunk][3]
+};
+
+__device__ __forceinline__ uint64_t gl_canon(uint64_t v) { return v >= kGL ? v - kGL : v; }
+
+// a signed 256-bit value mod q
+__device__ __forceinline__ uint64_t i256_mod_gl(const I256& v, const EvalArgs& p) {
+  uint64_t r = gl_canon(v.w[0]);
+  r = gl_add(r, gl_mul(gl_canon(v.w[1]), p.e1));
+  r = gl_add(r, gl_mul(gl_canon(v.w[2]), p.e2));
+  r = gl_add(r, gl_mul(gl_canon(v.w[3]), p.e3));
+  if ((int64_t)v.w[3] < 0) r = gl_sub(r, p.e4);   // two's complement: value = unsigned - 2^256
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_eval_partial(EvalArgs p) {
+  __shared__ uint64_t red[3][256];
+  const int row = blockIdx.x / p.nchunk, c = blockIdx.x % p.nchunk;
+  const int64_t clen = p.m / p.nchunk;
+  const int64_t j0 = (int64_t)c * clen + threadIdx.x;
+  const int64_t j1 = (int64_t)(c + 1) * clen;
+  uint64_t sa = 0, sx = 0, sz = 0;
+  if (j0 < j1) {
+    uint64_t pw = gl_pow(p.w, (uint64_t)j0), pi = gl_pow(p.winv, (uint64_t)j0);
+    const int64_t base = (int64_t)row * p.m;
+    for (int64_t j = j0; j < j1; j += blockDim.x) {
+      sa = gl_add(sa, gl_mul(i256_mod_gl(p.a[base + j], p), pi));
+      sx = gl_add(sx, gl_mul(i256_mod_gl(p.x[base + j], p), pw));
+      sz = gl_add(sz, gl_mul(i256_mod_gl(p.z[base + j], p), pw));
+      pw = gl_mul(pw, p.wstep);
+      pi = gl_mul(pi, p.winvstep);
+    }
+  }
+  red[0][threadIdx.x] = sa;
+  red[1][threadIdx.x] = sx;
+  red[2][threadIdx.x] = sz;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int k = 0; k < 3; k++) red[k][threadIdx.x] = gl_add(red[k][threadIdx.x], red[k][threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) p.part[((int64_t)row * p.nchunk + c) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// out[row * 3 + k] = sum over chunks of part[row][chunk][k] (k: A(1/w), X(w), Z(w))
+__global__ void k_eval_final(const uint64_t* part, int d, int nchunk, unsigned long long* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * d) return;
+  const int row = t / 3, k = t % 3;
+  uint64_t sum = 0;
+  for (int c = 0; c < nchunk; c++) sum = gl_add(sum, part[((int64_t)row * nchunk + c) * 3 + k]);
+  out[row * 3 + k] = sum;
 }
 
 // GF(q) twiddle tables for a length-n transform: tw[t] = w^t and itw[t] = w^-t, t < n/2.
@@ -978,8 +1051,9 @@ void fill_estimate(sk_estimate* out, const I256* rows, const I256* sorted, int d
 // Algorithm 3 over the schedule.  One host round trip per correlation step: before a
 // step the host reads the bit lengths of its two operands (written by the kernels that
 // produced them) together with the previous step's certificate (largest rounding
-// residual and the row sums of a, x and z modulo 2^64, whose identity
-// sum z = (sum a)(sum x) holds exactly in Z/2^64).  A failed certificate restarts the
+// residual, the row sums of a, x and z modulo 2^64, whose identity
+// sum z = (sum a)(sum x) holds exactly in Z/2^64, and the row evaluations A(1/w), X(w),
+// Z(w) modulo q for power-of-two m).  A failed certificate restarts the
 // schedule with narrower limbs for that step.
 sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const int64_t m = s->m;
@@ -994,9 +1068,11 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const size_t slot_bytes = (size_t)dm * sizeof(I256);
   const size_t small_off = slot_bytes * nslots;
   // small buffers: rows, sorted rows (I256 [64] each) | slot bits (int [nslots]) | per step:
-  // residual (u64) and row sums (u64 [d][3])
-  const size_t cert_words = (size_t)ncorr * (1 + 3 * (size_t)d);
-  const size_t small_bytes = 2 * SK_MAX_ROWS * sizeof(I256) + 256 + cert_words * 8 + 64;
+  // residual (u64), row sums (u64 [d][3]) and row evaluations (u64 [d][3]) | evaluation
+  // partials (u64 [d][nchunk][3], at most 3 * 1024)
+  const size_t cw = 1 + 6 * (size_t)d;   // certificate words per step
+  const size_t cert_words = (size_t)ncorr * cw;
+  const size_t small_bytes = 2 * SK_MAX_ROWS * sizeof(I256) + 256 + cert_words * 8 + 3 * 1024 * 8 + 64;
   SK_CK(ensure(s->scratch, small_off + small_bytes, st));
   if (s->twiddle_m != M) {
     if (s->d_twiddle) cudaFree(s->d_twiddle);
@@ -1012,14 +1088,41 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   I256* d_rows = (I256*)(base + small_off);
   I256* d_sorted = d_rows + SK_MAX_ROWS;
   int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);                           // [nslots] (<= 64)
-  unsigned long long* d_cert = (unsigned long long*)((char*)d_bits + 256);  // [ncorr][1 + 3d]
+  unsigned long long* d_cert = (unsigned long long*)((char*)d_bits + 256);  // [ncorr][cw]
+  uint64_t* d_part = (uint64_t*)(d_cert + cert_words);                       // [d][nchunk][3]
   const int eg = grid_for(dm);
   if (nslots > 64) return SK_ERR_INVALID_ARG;
+  // evaluation certificate: FP64 path with a power-of-two m (an m-th root of unity exists in
+  // GF(q) for m | 2^32); chunks per row so that the d rows give up to 1024 blocks
+  const bool eval_cert = s->estimator == SK_ESTIMATOR_FFT64 && M == m && logm <= 32;
+  int nchunk = 1;
+  while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
 
   std::vector<int> bmax(ncorr, 64);     // per-step cap on the limb width (lowered on failure)
-  std::vector<unsigned long long> cert((size_t)ncorr * (1 + 3 * (size_t)d));
+  std::vector<unsigned long long> cert(cert_words);
   int retries = 0;
   for (int attempt = 0; attempt < 4; attempt++) {
+    EvalArgs ev;
+    if (eval_cert) {
+      // a random primitive m-th root of unity: (7^((q-1)/m))^r with r odd
+      uint64_t z = s->seed ^ (0x9E3779B97F4A7C15ull * (++s->eval_draws));
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const uint64_t r = (z % (uint64_t)m) | 1ull;
+      const uint64_t wm = gl_pow(7, (kGL - 1) / (uint64_t)m);
+      ev.w = gl_pow(wm, r);
+      ev.winv = gl_pow(ev.w, kGL - 2);
+      ev.wstep = gl_pow(ev.w, 256);
+      ev.winvstep = gl_pow(ev.winv, 256);
+      ev.e1 = kGLEps;
+      ev.e2 = gl_mul(ev.e1, ev.e1);
+      ev.e3 = gl_mul(ev.e2, ev.e1);
+      ev.e4 = gl_mul(ev.e3, ev.e1);
+      ev.m = m;
+      ev.nchunk = nchunk;
+      ev.part = d_part;
+    }
     std::vector<int> phys(nslots);
     for (int i = 0; i < nslots; i++) phys[i] = i;
     auto slot = [&](int i) { return (I256*)(base + slot_bytes * phys[i]); };
@@ -1030,15 +1133,20 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
     double max_resid = 0.0;
     int max_limbs = 0, last_B = 0, corr = 0;
     int failed = -1;
-    // checks the certificate of every step < upto whose values are in `cert`
+    // checks the certificate of every step < upto whose values are in `cert`: residual,
+    // row sums mod 2^64 and (FP64, power-of-two m) Z(w) = A(1/w) X(w) mod q per row; an
+    // uncertified step (GF(q), zero operands) holds zeros there, which pass
     auto check = [&](int upto) {
       for (int t = 0; t < upto && failed < 0; t++) {
-        const unsigned long long* c = cert.data() + (size_t)t * (1 + 3 * d);
+        const unsigned long long* c = cert.data() + (size_t)t * cw;
         double resid;
         std::memcpy(&resid, &c[0], sizeof(resid));
         max_resid = std::max(max_resid, resid);
         bool ok = resid <= 0.25;
         for (int r = 0; r < d && ok; r++) ok = c[1 + 3 * r + 2] == c[1 + 3 * r] * c[1 + 3 * r + 1];
+        const unsigned long long* e = c + 1 + 3 * d;
+        for (int r = 0; r < d && ok; r++)
+          ok = e[3 * r + 2] == (unsigned long long)(((unsigned __int128)e[3 * r] * e[3 * r + 1]) % kGL);
         if (!ok) failed = t;
       }
     };
@@ -1060,12 +1168,12 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
         int hb[64];
         SK_CK(cudaMemcpyAsync(hb, d_bits, sizeof(int) * nslots, cudaMemcpyDeviceToHost, st));
         if (corr > 0)
-          SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * (1 + 3 * d) * 8, cudaMemcpyDeviceToHost, st));
+          SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * cw * 8, cudaMemcpyDeviceToHost, st));
         SK_CK(cudaStreamSynchronize(st));
         check(corr);
         if (failed >= 0) break;
         const int bits_a = hb[phys[op.src]], bits_x = hb[phys[op.dst]];
-        unsigned long long* cert_t = d_cert + (size_t)corr * (1 + 3 * d);
+        unsigned long long* cert_t = d_cert + (size_t)corr * cw;
         if (bits_a == 0 || bits_x == 0) {
           SK_CK(cudaMemsetAsync(x, 0, slot_bytes, st));
           SK_CK(cudaMemsetAsync(d_bits + phys[op.dst], 0, sizeof(int), st));
@@ -1131,6 +1239,15 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
         k_recombine<<<eg, 256, 0, st>>>(p, bufB);
         count_launch();
         SK_CK(cudaGetLastError());
+        if (eval_cert) {
+          ev.a = a;
+          ev.x = x;
+          ev.z = p.z;
+          k_eval_partial<<<d * nchunk, 256, 0, st>>>(ev);
+          k_eval_final<<<(3 * d + 255) / 256, 256, 0, st>>>(d_part, d, nchunk, cert_t + 1 + 3 * d);
+          count_launch(2);
+          SK_CK(cudaGetLastError());
+        }
         std::swap(phys[op.dst], phys[spare]);
         step_B[corr] = B;
         max_limbs = std::max(max_limbs, std::max(La, Lx));
@@ -1151,7 +1268,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
       SK_CK(cudaMemcpyAsync(sorted, d_sorted, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
       SK_CK(cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
       if (corr > 0)
-        SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * (1 + 3 * d) * 8, cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaMemcpyAsync(cert.data(), d_cert, (size_t)corr * cw * 8, cudaMemcpyDeviceToHost, st));
       SK_CK(cudaStreamSynchronize(st));
       check(corr);
       if (failed < 0) {

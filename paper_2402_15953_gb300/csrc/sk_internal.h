@@ -82,6 +82,7 @@ struct sk_set {
   uint64_t* d_gl_tw = nullptr;                 // GF(q) twiddles [w^t | w^-t] for the NTT length
   int64_t gl_m = 0;
   uint64_t gl_r4 = 1, gl_r4inv = 1, gl_minv = 1;
+  uint64_t eval_draws = 0;                     // evaluation points drawn for certificates
 };
 
 namespace sk {

@@ -202,3 +202,27 @@ def test_unbiased_and_variance_bound(shape):
         norms *= float((counts.astype(np.float64) ** 2).sum())
     bound = (1.0 / m) * 3 ** (q.r - 1) * norms
     assert var <= 1.2 * bound, (var, bound)
+
+
+def test_correlation_evaluation_identity_mod_goldilocks():
+    """The identity behind the GPU's evaluation certificate: for z = a star x (Definition 3.1)
+    and an m-th root of unity w modulo q = 2^64 - 2^32 + 1, sum z_j w^j = A(1/w) X(w).  Checked
+    on exact oracle correlations (operands beyond 2^64, negative values) at primitive roots
+    w = (7^((q-1)/m))^r, r odd; changing one output by 1 breaks it."""
+    q = (1 << 64) - (1 << 32) + 1
+    rng = random.Random(2024)
+    for m in [2, 8, 64, 256]:
+        a = [rng.randrange(-(1 << 90), 1 << 90) for _ in range(m)]
+        x = [rng.randrange(-(1 << 70), 1 << 70) for _ in range(m)]
+        z = O.correlate(a, x)
+        for _ in range(3):
+            r = rng.randrange(m) | 1
+            w = pow(pow(7, (q - 1) // m, q), r, q)
+            assert pow(w, m, q) == 1 and (m == 1 or pow(w, m // 2, q) != 1)
+            wi = pow(w, q - 2, q)
+            lhs = sum(zj * pow(w, j, q) for j, zj in enumerate(z)) % q
+            rhs = (sum(ai * pow(wi, i, q) for i, ai in enumerate(a)) * sum(xk * pow(w, k, q) for k, xk in enumerate(x))) % q
+            assert lhs == rhs
+            bad = list(z)
+            bad[rng.randrange(m)] += 1
+            assert sum(zj * pow(w, j, q) for j, zj in enumerate(bad)) % q != rhs
