@@ -223,7 +223,7 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * sk_sketch_set_estimator: selects how sk_estimate_join computes each circular
- * cross-correlation (Definition 3.1); both give the identical exact result.
+ * cross-correlation (Definition 3.1); all give the identical exact result.
  *   SK_ESTIMATOR_FFT64 (default): FP64 FFTs on signed limbs, outputs rounded to
  *     integers and certified (largest distance to an integer <= 1/4, exact row-sum
  *     identity and, for power-of-two m, Z(w) = A(1/w) X(w) modulo 2^64 - 2^32 + 1 at
@@ -231,10 +231,18 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
  *     certificate fails;
  *   SK_ESTIMATOR_NTT: number-theoretic transforms over GF(2^64 - 2^32 + 1) on signed
  *     limbs narrow enough that every output lies below q/2 in magnitude, exact by
- *     construction (GB300's integer pipes are much faster than its FP64 pipe).
- * The environment variable SK_ESTIMATOR=ntt selects the NTT for sets created after it
- * is set.  Errors: SK_ERR_INVALID_ARG. */
-enum { SK_ESTIMATOR_FFT64 = 0, SK_ESTIMATOR_NTT = 1 };
+ *     construction (GB300's integer pipes are much faster than its FP64 pipe);
+ *   SK_ESTIMATOR_FUSED: for queries whose components all have exactly two attributes
+ *     (chains, stars) and power-of-two m, no correlation steps at all: with the
+ *     relations two-coloured along the components, X = (1/m) sum_nu prod_k C_k(+-nu)
+ *     (C_k the DFT of relation k's row), evaluated modulo 31-bit primes c 2^22 + 1
+ *     and recombined by the Chinese remainder theorem, with enough primes that their
+ *     product exceeds 8 prod_k ||c_k||_1 >= 8 |X| (exact).  Other queries and widths,
+ *     and bounds beyond 9 primes, are estimated as with SK_ESTIMATOR_NTT.  In the
+ *     result, max_limbs is the number of primes and limb_bits 0.
+ * The environment variable SK_ESTIMATOR=ntt (or =fused) selects that arithmetic for
+ * sets created after it is set.  Errors: SK_ERR_INVALID_ARG. */
+enum { SK_ESTIMATOR_FFT64 = 0, SK_ESTIMATOR_NTT = 1, SK_ESTIMATOR_FUSED = 2 };
 sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator);
 
 /* ---------------------------------------------------------------------------

@@ -203,11 +203,13 @@ def sk_sketch_destroy(handle: int) -> None:
     _check(load().sk_sketch_destroy(handle), "sk_sketch_destroy")
 
 
-ESTIMATORS = {"fft64": 0, "ntt": 1}
+ESTIMATORS = {"fft64": 0, "ntt": 1, "fused": 2}
 
 
 def sk_sketch_set_estimator(handle: int, estimator: str) -> None:
-    """estimator: "fft64" (FP64 FFT, certified rounding) or "ntt" (GF(2^64 - 2^32 + 1) transform)."""
+    """estimator: "fft64" (FP64 FFT, certified rounding), "ntt" (GF(2^64 - 2^32 + 1) transform) or
+    "fused" (one product of spectra modulo CRT primes, for queries whose components all join two
+    attributes; others as "ntt")."""
     _check(load().sk_sketch_set_estimator(handle, ESTIMATORS[estimator]), "sk_sketch_set_estimator")
 
 

@@ -380,6 +380,7 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
   build_plan(s);
   const char* ev = std::getenv("SK_ESTIMATOR");
   if (ev && std::strcmp(ev, "ntt") == 0) s->estimator = SK_ESTIMATOR_NTT;
+  if (ev && std::strcmp(ev, "fused") == 0) s->estimator = SK_ESTIMATOR_FUSED;
   *out = s;
   return SK_OK;
 }
@@ -420,7 +421,7 @@ sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_str
 }
 
 sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator) {
-  if (!set || (estimator != SK_ESTIMATOR_FFT64 && estimator != SK_ESTIMATOR_NTT)) return SK_ERR_INVALID_ARG;
+  if (!set || estimator < SK_ESTIMATOR_FFT64 || estimator > SK_ESTIMATOR_FUSED) return SK_ERR_INVALID_ARG;
   set->estimator = estimator;
   return SK_OK;
 }

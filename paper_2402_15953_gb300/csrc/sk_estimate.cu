@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sk_internal.h"
 
@@ -941,6 +942,12 @@ struct HostI256 {
 }  // namespace
 
 void free_estimator(sk_set* s) {
+  if (s->d_fu_tw) cudaFree(s->d_fu_tw);
+  if (s->d_fu_rel) cudaFree(s->d_fu_rel);
+  s->d_fu_tw = nullptr;
+  s->d_fu_rel = nullptr;
+  s->fu_m = 0;
+  s->fu_np = 0;
   if (s->scratch.ptr) cudaFree(s->scratch.ptr);
   if (s->fft_scratch.ptr) cudaFree(s->fft_scratch.ptr);
   if (s->d_twiddle) cudaFree(s->d_twiddle);
@@ -1048,6 +1055,412 @@ void fill_estimate(sk_estimate* out, const I256* rows, const I256* sorted, int d
                               : 0.5 * (to_double(sorted[d / 2 - 1]) + to_double(sorted[d / 2]));
 }
 
+// ===========================================================================
+// Fused estimator for queries whose components all have exactly two attributes
+// (chains, stars).  Writing each sketch through its DFT over an m-th root of unity w,
+// the sum over all components' bins in Eq. 5 leaves one free frequency: with the
+// relations two-coloured along the tree of components (s_k = +1 / -1),
+//     X = (1/m) sum_nu prod_k C_k(s_k nu),     C_k(nu) = sum_t c_k[t] w^(nu t).
+// That identity is evaluated exactly modulo several primes p = c 2^22 + 1 in
+// (2^30, 2^31) and the row values are recombined by the Chinese remainder theorem.
+// |X| <= prod_k ||c_k||_1 (each choice of one counter per relation meets at most one
+// bin assignment, by peeling leaf relations), so primes whose product exceeds eight
+// times that bound give X exactly.  Arithmetic mod p is Montgomery with R = 2^32.
+// ===========================================================================
+constexpr int kFuMaxPrimes = 9;            // 9 x 30+ bits covers any signed 256-bit result
+__constant__ uint32_t c_fu_p[kFuMaxPrimes];
+__constant__ uint32_t c_fu_pinv[kFuMaxPrimes];   // -p^-1 mod 2^32
+
+struct FuPrime {
+  uint32_t p, pinv, r2, r3;   // r2 = 2^64 mod p, r3 = 2^96 mod p
+  uint64_t g;                 // a quadratic non-residue mod p
+  double log2p;
+};
+
+uint64_t fu_powmod(uint64_t b, uint64_t e, uint64_t p) {
+  uint64_t r = 1 % p;
+  b %= p;
+  for (; e; e >>= 1) {
+    if (e & 1) r = (uint64_t)((unsigned __int128)r * b % p);
+    b = (uint64_t)((unsigned __int128)b * b % p);
+  }
+  return r;
+}
+
+// the primes c 2^22 + 1 in (2^30, 2^31), largest first (trial division suffices below 2^31)
+const std::vector<FuPrime>& fu_primes() {
+  static const std::vector<FuPrime> v = [] {
+    std::vector<FuPrime> out;
+    for (uint64_t c = ((1ull << 31) - 1) >> 22; c >= (1ull << 8) && (int)out.size() < kFuMaxPrimes; c--) {
+      const uint64_t p = (c << 22) + 1;
+      if (p >= (1ull << 31) || p <= (1ull << 30)) continue;
+      bool prime = true;
+      for (uint64_t f = 3; f * f <= p; f += 2)
+        if (p % f == 0) {
+          prime = false;
+          break;
+        }
+      if (!prime) continue;
+      FuPrime fp;
+      fp.p = (uint32_t)p;
+      uint32_t inv = 1;   // p^-1 mod 2^32 by Newton's iteration (correct bits double each step)
+      for (int k = 0; k < 5; k++) inv *= 2u - (uint32_t)p * inv;
+      fp.pinv = 0u - inv;
+      const uint64_t R = (1ull << 32) % p;
+      fp.r2 = (uint32_t)((unsigned __int128)R * R % p);
+      fp.r3 = (uint32_t)((unsigned __int128)fp.r2 * R % p);
+      fp.g = 0;
+      for (uint64_t g = 3; g < p; g++)
+        if (fu_powmod(g, (p - 1) / 2, p) == p - 1) {
+          fp.g = g;
+          break;
+        }
+      fp.log2p = std::log2((double)p);
+      out.push_back(fp);
+    }
+    return out;
+  }();
+  return v;
+}
+
+// a * b / 2^32 mod p for a, b < p < 2^31 (Montgomery reduction; the sum below stays < 2^64)
+__device__ __forceinline__ uint32_t mont32(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t q = (uint32_t)t * pinv;
+  const uint64_t u = (t + (uint64_t)q * p) >> 32;
+  return (uint32_t)(u >= p ? u - p : u);
+}
+
+template <int PI>
+struct MontOps {
+  using T = uint32_t;
+  static __device__ __forceinline__ T mul(T a, T b) { return mont32(a, b, c_fu_p[PI], c_fu_pinv[PI]); }
+  static __device__ __forceinline__ T add(T a, T b) {
+    const uint32_t p = c_fu_p[PI], s = a + b;
+    return s >= p ? s - p : s;
+  }
+  static __device__ __forceinline__ T sub(T a, T b) { return a >= b ? a - b : a + c_fu_p[PI] - b; }
+  static __device__ __forceinline__ T neg(T a) { return a ? c_fu_p[PI] - a : 0; }
+  static __device__ __forceinline__ T tw(const T* tab, int64_t i, bool) { return tab[i]; }
+  static __device__ __forceinline__ T rot4(T w, bool, T r4) { return mul(w, r4); }
+};
+
+// tw[t] = w^t, itw[t] = w^-t for t < n/2 (Montgomery form; one is R mod p)
+template <int PI>
+__global__ void k_fu_twiddle(uint32_t* tw, uint32_t* itw, int64_t n, uint32_t w, uint32_t winv, uint32_t one) {
+  const int64_t half = n >> 1;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += step) {
+    uint32_t r = one, ri = one, b = w, bi = winv;
+    for (int64_t e = t; e; e >>= 1) {
+      if (e & 1) {
+        r = MontOps<PI>::mul(r, b);
+        ri = MontOps<PI>::mul(ri, bi);
+      }
+      b = MontOps<PI>::mul(b, b);
+      bi = MontOps<PI>::mul(bi, bi);
+    }
+    tw[t] = r;
+    itw[t] = ri;
+  }
+}
+
+// l1[k * d + row] = sum_j |c_k[row][j]| (double; the host adds a safety margin)
+__global__ void __launch_bounds__(256) k_fu_l1(const int64_t* const* rel, int d, int64_t m, double* l1) {
+  __shared__ double red[256];
+  const int k = blockIdx.x / d, row = blockIdx.x % d;
+  const int64_t* c = rel[k] + (int64_t)row * m;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) s += fabs((double)c[j]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) l1[blockIdx.x] = red[0];
+}
+
+// out[(k d + row) m + j] = c_k[row][j] mod p, Montgomery form (|c| = h 2^32 + l)
+template <int PI>
+__global__ void k_fu_load(const int64_t* const* rel, int r, int d, int64_t m, uint32_t r2, uint32_t r3, uint32_t* out) {
+  using O = MontOps<PI>;
+  const int64_t dm = (int64_t)d * m, total = (int64_t)r * dm;
+  const uint32_t p = c_fu_p[PI];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t c = rel[g / dm][g % dm];
+    const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
+    uint32_t h = (uint32_t)(mag >> 32);
+    if (h >= p) h -= p;
+    const uint32_t v = O::add(O::mul(h, r3), O::mul((uint32_t)mag, r2));
+    out[g] = c < 0 ? O::neg(v) : v;
+  }
+}
+
+// part[row * nchunk + chunk] = sum over the chunk's nu of prod_k C_k(s_k nu)
+template <int PI>
+__global__ void __launch_bounds__(256) k_fu_reduce(const uint32_t* W, int r, int d, int64_t M, unsigned long long negmask,
+                                                   int nchunk, uint32_t* part) {
+  using O = MontOps<PI>;
+  __shared__ uint32_t red[256];
+  const int row = blockIdx.x / nchunk, c = blockIdx.x % nchunk;
+  const int64_t clen = M / nchunk;
+  uint32_t s = 0;
+  for (int64_t nu = (int64_t)c * clen + threadIdx.x; nu < (int64_t)(c + 1) * clen; nu += blockDim.x) {
+    const int64_t neg_nu = (M - nu) & (M - 1);
+    uint32_t prod = W[(int64_t)row * M + ((negmask & 1ull) ? neg_nu : nu)];
+    for (int k = 1; k < r; k++)
+      prod = O::mul(prod, W[((int64_t)k * d + row) * M + (((negmask >> k) & 1ull) ? neg_nu : nu)]);
+    s = O::add(s, prod);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = O::add(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// res[row * np + PI] = (sum of the row's chunks) / m, back from Montgomery form
+template <int PI>
+__global__ void k_fu_final(const uint32_t* part, int d, int nchunk, uint32_t minv_mont, uint32_t* res, int np) {
+  using O = MontOps<PI>;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= d) return;
+  uint32_t s = 0;
+  for (int c = 0; c < nchunk; c++) s = O::add(s, part[row * nchunk + c]);
+  res[row * np + PI] = O::mul(O::mul(s, minv_mont), 1u);
+}
+
+// host: Montgomery form of v (< p)
+uint32_t fu_to_mont(uint64_t v, uint32_t p) { return (uint32_t)(((unsigned __int128)v << 32) % p); }
+
+// One prime's pass: twiddles (when missing), load, forward transform, product-sum.
+template <int PI>
+sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, uint32_t* W, uint32_t* part,
+                        int nchunk, uint32_t* res, int np, unsigned long long negmask, cudaStream_t st) {
+  const int r = s->r, d = s->d;
+  uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
+  const uint64_t p = fp.p;
+  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
+  const uint64_t winv = fu_powmod(w, p - 2, p);
+  if (s->fu_np <= PI) {
+    k_fu_twiddle<PI><<<grid_for(M / 2), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p), fu_to_mont(winv, fp.p),
+                                                        fu_to_mont(1, fp.p));
+    count_launch();
+    SK_CK(cudaGetLastError());
+  }
+  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
+  k_fu_load<PI><<<grid_for((int64_t)r * d * M), 256, 0, st>>>(s->d_fu_rel, r, d, M, fp.r2, fp.r3, V);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  sk_status fs = xform<MontOps<PI>>(V, W, (int64_t)r * d, M, tw, false, r4, st);
+  if (fs != SK_OK) return fs;
+  k_fu_reduce<PI><<<d * nchunk, 256, 0, st>>>(W, r, d, M, negmask, nchunk, part);
+  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
+  k_fu_final<PI><<<(d + 63) / 64, 64, 0, st>>>(part, d, nchunk, minv, res, np);
+  count_launch(2);
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+// Garner's mixed-radix reconstruction of the integer with the given residues, taken in
+// [-P/2, P/2) with P the product of the primes; false when it needs more than 255 bits.
+bool fu_crt(const uint32_t* res, int np, const std::vector<FuPrime>& pr, I256* out) {
+  constexpr int W = 6;   // 384-bit accumulators
+  uint64_t X[W] = {0}, Q[W] = {1, 0, 0, 0, 0, 0};
+  auto mod_small = [](const uint64_t* a, uint64_t p) {
+    unsigned __int128 r = 0;
+    for (int i = W - 1; i >= 0; i--) r = ((r << 64) | a[i]) % p;
+    return (uint64_t)r;
+  };
+  auto mul_add = [](uint64_t* acc, const uint64_t* a, uint64_t t) {   // acc += a * t
+    unsigned __int128 carry = 0;
+    for (int i = 0; i < W; i++) {
+      const unsigned __int128 v = (unsigned __int128)a[i] * t + acc[i] + carry;
+      acc[i] = (uint64_t)v;
+      carry = v >> 64;
+    }
+  };
+  for (int i = 0; i < np; i++) {
+    const uint64_t p = pr[i].p;
+    const uint64_t xm = mod_small(X, p), qm = mod_small(Q, p);
+    const uint64_t t = (uint64_t)((unsigned __int128)((res[i] + p - xm) % p) * fu_powmod(qm, p - 2, p) % p);
+    mul_add(X, Q, t);
+    uint64_t Qn[W] = {0};
+    mul_add(Qn, Q, p);
+    std::memcpy(Q, Qn, sizeof(Q));
+  }
+  // negative when 2X >= Q
+  uint64_t X2[W];
+  uint64_t carry = 0;
+  for (int i = 0; i < W; i++) {
+    X2[i] = (X[i] << 1) | carry;
+    carry = X[i] >> 63;
+  }
+  bool neg = false;
+  for (int i = W - 1; i >= 0; i--)
+    if (X2[i] != Q[i]) {
+      neg = X2[i] > Q[i];
+      break;
+    } else if (i == 0) {
+      neg = true;
+    }
+  uint64_t mag[W];
+  if (neg) {   // mag = Q - X
+    uint64_t borrow = 0;
+    for (int i = 0; i < W; i++) {
+      const unsigned __int128 v = (unsigned __int128)Q[i] - X[i] - borrow;
+      mag[i] = (uint64_t)v;
+      borrow = (uint64_t)(v >> 64) ? 1 : 0;
+    }
+  } else {
+    std::memcpy(mag, X, sizeof(mag));
+  }
+  if (mag[4] || mag[5] || (mag[3] >> 63)) return false;
+  I256 v;
+  for (int i = 0; i < 4; i++) v.w[i] = mag[i];
+  *out = neg ? i256_neg(v) : v;
+  return true;
+}
+
+// true when every component has exactly two attributes (then the components, as edges,
+// make the relations a tree); signs: bit k of *negmask set when s_k = -1
+bool fu_eligible(const sk_set* s, unsigned long long* negmask) {
+  if (s->r > 64) return false;
+  std::vector<std::vector<int>> members(s->n_comp);
+  for (int u = 0; u < (int)s->comp_of.size(); u++) members[s->comp_of[u]].push_back(u);
+  for (const auto& mb : members)
+    if (mb.size() != 2) return false;
+  std::vector<int> sign(s->r, 0);
+  sign[0] = 1;
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (const auto& mb : members) {
+      const int ka = s->rel_of[mb[0]], kb = s->rel_of[mb[1]];
+      if (sign[ka] && !sign[kb]) sign[kb] = -sign[ka], changed = true;
+      if (sign[kb] && !sign[ka]) sign[ka] = -sign[kb], changed = true;
+    }
+  }
+  unsigned long long nm = 0;
+  for (int k = 0; k < s->r; k++) {
+    if (!sign[k]) return false;
+    if (sign[k] < 0) nm |= 1ull << k;
+  }
+  *negmask = nm;
+  return true;
+}
+
+std::mutex g_fu_const_mutex;
+bool g_fu_const_ready[64] = {false};
+
+// The fused estimate; *done false when it does not apply (the caller then estimates
+// step by step).
+sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
+  *done = false;
+  const int64_t m = s->m;
+  const int r = s->r, d = s->d;
+  unsigned long long negmask = 0;
+  if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
+  const std::vector<FuPrime>& pr = fu_primes();
+  if ((int)pr.size() < kFuMaxPrimes) return SK_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_fu_const_mutex);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return SK_OK;
+    if (!g_fu_const_ready[dev]) {
+      uint32_t ps[kFuMaxPrimes], pis[kFuMaxPrimes];
+      for (int i = 0; i < kFuMaxPrimes; i++) {
+        ps[i] = pr[i].p;
+        pis[i] = pr[i].pinv;
+      }
+      SK_CK(cudaMemcpyToSymbol(c_fu_p, ps, sizeof(ps)));
+      SK_CK(cudaMemcpyToSymbol(c_fu_pinv, pis, sizeof(pis)));
+      g_fu_const_ready[dev] = true;
+    }
+  }
+  if (!s->d_fu_rel) {
+    SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
+    SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
+  }
+  // scratch: l1 [r][d] doubles | residues [d][9] | partials [d][nchunk] | V, W [r][d][m] words
+  int nchunk = 1;
+  while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
+  const size_t l1_bytes = ((size_t)r * d * 8 + 255) & ~(size_t)255;
+  const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
+  const size_t part_bytes = ((size_t)d * nchunk * 4 + 255) & ~(size_t)255;
+  SK_CK(ensure(s->scratch, l1_bytes + res_bytes + part_bytes, st));
+  double* d_l1 = (double*)s->scratch.ptr;
+  uint32_t* d_res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
+  uint32_t* d_part = (uint32_t*)((char*)d_res + res_bytes);
+  k_fu_l1<<<r * d, 256, 0, st>>>(s->d_fu_rel, d, m, d_l1);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  std::vector<double> l1((size_t)r * d);
+  SK_CK(cudaMemcpyAsync(l1.data(), d_l1, l1.size() * 8, cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  double bits = 0.0;   // log2 of the largest row bound prod_k ||c_k||_1
+  for (int row = 0; row < d; row++) {
+    double b = 0.0;
+    bool zero = false;
+    for (int k = 0; k < r; k++) {
+      const double v = l1[(size_t)k * d + row];
+      if (v <= 0.0) zero = true;
+      else b += std::log2(v * (1.0 + 1e-9));
+    }
+    if (!zero) bits = std::max(bits, b);
+  }
+  int np = 0;
+  double cover = 0.0;
+  while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
+  if (cover < bits + 3.0) return SK_OK;   // beyond 9 primes: the stepwise estimate handles it
+  const size_t words = (size_t)r * d * m;
+  SK_CK(ensure(s->fft_scratch, 2 * words * sizeof(uint32_t), st));
+  uint32_t* V = (uint32_t*)s->fft_scratch.ptr;
+  uint32_t* Wb = V + words;
+  if (s->fu_m != m || !s->d_fu_tw) {
+    if (s->d_fu_tw) cudaFree(s->d_fu_tw);
+    s->d_fu_tw = nullptr;
+    s->fu_np = 0;
+    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * m * sizeof(uint32_t)));
+    s->fu_m = m;
+  }
+  for (int i = 0; i < np; i++) {
+    sk_status ps;
+    switch (i) {
+      case 0: ps = fu_prime_pass<0>(s, pr[0], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 1: ps = fu_prime_pass<1>(s, pr[1], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 2: ps = fu_prime_pass<2>(s, pr[2], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 3: ps = fu_prime_pass<3>(s, pr[3], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 4: ps = fu_prime_pass<4>(s, pr[4], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 5: ps = fu_prime_pass<5>(s, pr[5], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 6: ps = fu_prime_pass<6>(s, pr[6], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      case 7: ps = fu_prime_pass<7>(s, pr[7], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+      default: ps = fu_prime_pass<8>(s, pr[8], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
+    }
+    if (ps != SK_OK) return ps;
+  }
+  s->fu_np = std::max(s->fu_np, np);
+  std::vector<uint32_t> res((size_t)d * kFuMaxPrimes);
+  SK_CK(cudaMemcpyAsync(res.data(), d_res, res.size() * 4, cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
+  for (int row = 0; row < d; row++)
+    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, np, pr, &rows[row])) return SK_ERR_OVERFLOW;
+  std::memcpy(sorted, rows, sizeof(I256) * d);
+  std::sort(sorted, sorted + d, [](const I256& a, const I256& b) { return i256_lt(a, b); });
+  fill_estimate(out, rows, sorted, d);
+  out->max_residual = 0.0;
+  out->max_limbs = np;      // CRT primes
+  out->limb_bits = 0;
+  out->corr_steps = s->corr_steps;
+  out->retries = 0;
+  *done = true;
+  return SK_OK;
+}
+
 // Algorithm 3 over the schedule.  One host round trip per correlation step: before a
 // step the host reads the bit lengths of its two operands (written by the kernels that
 // produced them) together with the previous step's certificate (largest rounding
@@ -1056,6 +1469,11 @@ void fill_estimate(sk_estimate* out, const I256* rows, const I256* sorted, int d
 // Z(w) modulo q for power-of-two m).  A failed certificate restarts the
 // schedule with narrower limbs for that step.
 sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
+  if (s->estimator == SK_ESTIMATOR_FUSED) {
+    bool done = false;
+    const sk_status fs = run_estimate_fused(s, out, st, &done);
+    if (fs != SK_OK || done) return fs;
+  }
   const int64_t m = s->m;
   const int d = s->d;
   const int64_t dm = (int64_t)d * m;
@@ -1181,7 +1599,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
           continue;
         }
         if (bits_a + bits_x + logm + 1 > 255) return SK_ERR_OVERFLOW;
-        if (s->estimator == SK_ESTIMATOR_NTT) {
+        if (s->estimator != SK_ESTIMATOR_FFT64) {   // GF(q) transforms (also the fused fallback)
           sk_status ns = corr_ntt(s, a, x, slot(spare), d_bits + phys[spare], cert_t, bits_a, bits_x, m, M, st,
                                   &max_limbs, &last_B);
           if (ns != SK_OK) return ns;

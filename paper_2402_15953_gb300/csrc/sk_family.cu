@@ -484,6 +484,7 @@ sk_status sk_family_create(const sk_query* query, int32_t n_sub, const int32_t* 
     }
     const char* ev = std::getenv("SK_ESTIMATOR");
     if (ev && std::strcmp(ev, "ntt") == 0) fs.est->estimator = SK_ESTIMATOR_NTT;
+    if (ev && std::strcmp(ev, "fused") == 0) fs.est->estimator = SK_ESTIMATOR_FUSED;
   }
   const int nw = std::min(env_workers(), n_sub);
   for (int w = 0; w < nw; w++) {
@@ -575,7 +576,7 @@ sk_status sk_family_estimate(sk_family* fam, sk_estimate* out, void* cuda_stream
 }
 
 sk_status sk_family_set_estimator(sk_family* fam, int32_t estimator) {
-  if (!fam || (estimator != SK_ESTIMATOR_FFT64 && estimator != SK_ESTIMATOR_NTT)) return SK_ERR_INVALID_ARG;
+  if (!fam || estimator < SK_ESTIMATOR_FFT64 || estimator > SK_ESTIMATOR_FUSED) return SK_ERR_INVALID_ARG;
   for (auto& s : fam->sub) s.est->estimator = estimator;
   return SK_OK;
 }

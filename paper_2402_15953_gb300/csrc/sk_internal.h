@@ -83,6 +83,10 @@ struct sk_set {
   int64_t gl_m = 0;
   uint64_t gl_r4 = 1, gl_r4inv = 1, gl_minv = 1;
   uint64_t eval_draws = 0;                     // evaluation points drawn for certificates
+  uint32_t* d_fu_tw = nullptr;                 // fused estimator: per prime [w^t | w^-t], t < m/2
+  int64_t fu_m = 0;                            // width the fused twiddles are for
+  int fu_np = 0;                               // primes they cover
+  const int64_t** d_fu_rel = nullptr;          // fused estimator: device copy of rel_ctr
 };
 
 namespace sk {

@@ -1,0 +1,125 @@
+"""The fused estimator (SK_ESTIMATOR_FUSED): for queries whose components all join two
+attributes, X = (1/m) sum_nu prod_k C_k(+-nu) modulo CRT primes.  Rows must equal the
+oracle's exact Algorithm 3 rows; other queries and widths fall back to the stepwise
+GF(q) estimate, also exact."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2402_15953_gb300 as pkg
+import synth
+from tests._helpers import random_relations, random_tree_query
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+
+
+def _estimate(attrs, edges, m, d, seed, rels, estimator):
+    s = pkg.SketchSet(attrs, edges, m, d, seed)
+    s.set_estimator(estimator)
+    for k, (cols, w) in enumerate(rels):
+        s.update(k, torch.as_tensor(np.ascontiguousarray(cols)).cuda(),
+                 None if w is None else torch.as_tensor(np.ascontiguousarray(w)).cuda())
+    e = s.estimate()
+    s.close()
+    return e
+
+
+def _oracle_rows(attrs, edges, m, d, seed, rels):
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(seed, d, q.n_comp, len(q.edges))
+    return O.estimate(q, O.sketch_all(q, co, rels, m)).rows
+
+
+@pytest.mark.parametrize("m", [2, 4, 64, 1024, 1 << 14, 1 << 17])
+def test_pairwise_queries_exact(m):
+    """Random tree queries where every attribute is joined once (components of two), keys
+    over small and wide domains, signed weights."""
+    rng = random.Random(500 + m)
+    for trial in range(4 if m <= 1024 else 2):
+        attrs, edges = random_tree_query(rng, rng.randint(2, 6), share_prob=0.0)
+        rels = random_relations(rng, attrs, 2000 if m <= 1024 else 800, 1 << rng.choice([4, 12, 40]))
+        d = rng.choice([1, 3, 7])
+        seed = rng.randrange(1 << 60)
+        e = _estimate(attrs, edges, m, d, seed, rels, "fused")
+        assert e["limb_bits"] == 0 and 1 <= e["max_limbs"] <= 9       # the fused path ran
+        assert e["rows"] == _oracle_rows(attrs, edges, m, d, seed, rels), (m, trial)
+
+
+def test_many_primes_for_large_weights():
+    """A five-relation chain with weights up to 2^30 in magnitude: the bound needs most of
+    the nine primes."""
+    rng = random.Random(9)
+    attrs, edges = [1, 2, 2, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0), (2, 1, 3, 0), (3, 1, 4, 0)]
+    rels = []
+    for a in attrs:
+        n = 300
+        cols = np.array([[rng.randrange(50) for _ in range(n)] for _ in range(a)], dtype=np.int64)
+        w = np.array([rng.choice([-1, 1]) * rng.randrange(1, 1 << 30) for _ in range(n)], dtype=np.int64)
+        rels.append((cols, w))
+    e = _estimate(attrs, edges, 256, 5, 77, rels, "fused")
+    assert e["max_limbs"] >= 6
+    assert e["rows"] == _oracle_rows(attrs, edges, 256, 5, 77, rels)
+    assert max(abs(v) for v in e["rows"]) > (1 << 64)
+
+
+def test_fallbacks_are_exact():
+    """Components of three attributes (Figure 3's {0, 1, 3}) and widths that are not powers
+    of two take the stepwise GF(q) estimate."""
+    rng = random.Random(4)
+    attrs, edges = synth.fig3_query()
+    rels = random_relations(rng, attrs, 1500, 64)
+    e = _estimate(attrs, edges, 128, 5, 3, rels, "fused")
+    assert e["limb_bits"] > 0
+    assert e["rows"] == _oracle_rows(attrs, edges, 128, 5, 3, rels)
+    w = synth.chain3()
+    rels = [(r.cols.numpy(), None) for r in w.relations]
+    e = _estimate(w.num_join_attrs, w.edges, 1000, 5, 42, rels, "fused")
+    assert e["limb_bits"] > 0
+    assert e["rows"] == _oracle_rows(w.num_join_attrs, w.edges, 1000, 5, 42, rels)
+
+
+def test_star_and_chain8_full_size_match_fft64():
+    """The headline star (F 1e8 x 5, m = 2^16, d = 9) at 2e7 fact rows and the 8-relation
+    chain (8 x 1e7 rows, m = 2^20, d = 16): fused rows equal the certified FP64 rows."""
+    for wl in (synth.star(n_fact=20_000_000, device="cuda"), synth.chain(device="cuda")):
+        s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+        for k, rel in enumerate(wl.relations):
+            s.update(k, rel.cols)
+        a = s.estimate()
+        s.set_estimator("fused")
+        b = s.estimate()
+        c = s.estimate()
+        assert b["limb_bits"] == 0
+        assert a["rows"] == b["rows"] == c["rows"] and a["median"] == b["median"]
+        s.close()
+        del wl
+        torch.cuda.empty_cache()
+
+
+def test_family_with_fused_estimator():
+    """Sub-query families estimate each sub-query with the fused arithmetic where it
+    applies (every two-way or chain sub-query of a chain)."""
+    from tests.test_oracle_subquery import connected_subsets
+    rng = random.Random(12)
+    attrs, edges = [1, 2, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0), (2, 1, 3, 0)]
+    rels = random_relations(rng, attrs, 2000, 200)
+    subs = connected_subsets(attrs, edges)
+    fam = pkg.SketchFamily(attrs, edges, subs, 512, 5, 99)
+    for k, (cols, w) in enumerate(rels):
+        fam.update(k, torch.as_tensor(cols).cuda(), torch.as_tensor(w).cuda())
+    ref = fam.estimate()
+    fam.set_estimator("fused")
+    got = fam.estimate()
+    assert [e["rows"] for e in got] == [e["rows"] for e in ref]
+    assert all(e["limb_bits"] == 0 for e in got)
+    fam.close()
