@@ -438,8 +438,58 @@ __global__ void k_xf_small(const typename Ops::T* __restrict__ in, typename Ops:
   for (int idx = threadIdx.x; idx < cnt * L; idx += blockDim.x) out[(v0 * L) + idx] = sm[idx];
 }
 
+// In-place radix-2 decimation-in-frequency transforms (natural-order input, output in
+// bit-reversed order) of `cnt` vectors of length 2^logL held interleaved in shared
+// memory: element i of vector v at s[i * S + v] with S = cnt + 1 (odd, so that the
+// transposing loads of the row pass and the bit-reversed reads stay conflict-free).
+// Consecutive threads take consecutive vectors of the same butterfly: every access of a
+// warp is a contiguous run and the butterfly's twiddle is the same across it.  Pairs of
+// stages (half sizes 2q and q) are fused on the four elements i0 + {0, q, 2q, 3q}.
+// tw is the half table of the length-N transform, twstride = N / L; r4 as in smem_xform.
+template <class Ops>
+__device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const typename Ops::T* __restrict__ tw,
+                            int64_t twstride, bool inv, typename Ops::T r4) {
+  using T = typename Ops::T;
+  const int L = 1 << logL;
+  int lh = logL - 1;   // log2 of the larger half size of the pair
+  for (; lh >= 1; lh -= 2) {
+    const int q = 1 << (lh - 1);
+    const int64_t s4 = (int64_t)(L >> (lh + 1)) * twstride;   // w_4q^pos = tw[pos * s4]
+    const int64_t s2 = (int64_t)(L >> lh) * twstride;         // w_2q^pos = tw[pos * s2]
+    const int total4 = cnt * (L >> 2);
+    const int qS = q * S;
+    for (int b = threadIdx.x; b < total4; b += blockDim.x) {
+      const int v = b % cnt, jj = b / cnt;
+      const int grp = jj >> (lh - 1), pos = jj & (q - 1);
+      T* e = s + (grp * 4 * q + pos) * S + v;
+      const T w4 = Ops::tw(tw, (int64_t)pos * s4, inv);
+      const T w4b = Ops::rot4(w4, inv, r4);                    // w_4q^(pos + q)
+      const T w2 = Ops::tw(tw, (int64_t)pos * s2, inv);
+      const T e0 = e[0], e1 = e[qS], e2 = e[2 * qS], e3 = e[3 * qS];
+      const T u0 = Ops::add(e0, e2), u2 = Ops::mul(Ops::sub(e0, e2), w4);
+      const T u1 = Ops::add(e1, e3), u3 = Ops::mul(Ops::sub(e1, e3), w4b);
+      e[0] = Ops::add(u0, u1);
+      e[qS] = Ops::mul(Ops::sub(u0, u1), w2);
+      e[2 * qS] = Ops::add(u2, u3);
+      e[3 * qS] = Ops::mul(Ops::sub(u2, u3), w2);
+    }
+    __syncthreads();
+  }
+  if (lh == 0) {   // odd logL: the last stage, half size 1 (twiddle 1)
+    const int total = cnt * (L >> 1);
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      const int v = b % cnt, g = b / cnt;
+      T* e = s + (2 * g) * S + v;
+      const T a0 = e[0], a1 = e[S];
+      e[0] = Ops::add(a0, a1);
+      e[S] = Ops::sub(a0, a1);
+    }
+    __syncthreads();
+  }
+}
+
 // four-step, pass 1: length-R transforms down the columns of the R x C view
-// (element n1 * C + n2), then the twiddle w_N^(n2 k1); in place.
+// (element n1 * C + n2), then the twiddle w_N^(n2 k1); in place.  Tile: cb columns.
 template <class Ops>
 __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC, int cb,
                           const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
@@ -447,6 +497,7 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
   extern __shared__ __align__(16) unsigned char xf_smem[];
   T* sm = (T*)xf_smem;
   const int R = 1 << logR, C = 1 << logC;
+  const int S = cb + 1;
   const int64_t N = (int64_t)R * C;
   const int blocks_per_vec = C / cb;
   const int64_t vec = blockIdx.x / blocks_per_vec;
@@ -454,21 +505,21 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
   T* v = buf + vec * N;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
     const int c = idx % cb, n1 = idx / cb;
-    sm[c * R + bitrev(n1, logR)] = v[(int64_t)n1 * C + c0 + c];
+    sm[n1 * S + c] = v[(int64_t)n1 * C + c0 + c];
   }
   __syncthreads();
-  smem_xform<Ops>(sm, cb, logR, tw, C, inv, r4);
+  smem_dif_il<Ops>(sm, cb, S, logR, tw, C, inv, r4);
   const int64_t half = N >> 1;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
     const int c = idx % cb, k1 = idx / cb;
     const int64_t n2 = c0 + c;
     const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
-    v[(int64_t)k1 * C + n2] = Ops::mul(sm[c * R + k1], w);
+    v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
   }
 }
 
 // four-step, pass 2: length-C transforms along the rows k1, written to the
-// natural-order output X[k1 + R k2]; out of place.
+// natural-order output X[k1 + R k2]; out of place.  Tile: rb rows.
 template <class Ops>
 __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::T* __restrict__ out, int logR,
                           int logC, int rb, const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
@@ -476,6 +527,7 @@ __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::
   extern __shared__ __align__(16) unsigned char xf_smem[];
   T* sm = (T*)xf_smem;
   const int R = 1 << logR, C = 1 << logC;
+  const int S = rb + 1;
   const int64_t N = (int64_t)R * C;
   const int blocks_per_vec = R / rb;
   const int64_t vec = blockIdx.x / blocks_per_vec;
@@ -484,13 +536,13 @@ __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::
   T* vo = out + vec * N;
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
     const int rr = idx / C, n2 = idx % C;
-    sm[rr * C + bitrev(n2, logC)] = vi[(int64_t)(r0 + rr) * C + n2];
+    sm[n2 * S + rr] = vi[(int64_t)(r0 + rr) * C + n2];
   }
   __syncthreads();
-  smem_xform<Ops>(sm, rb, logC, tw, R, inv, r4);
+  smem_dif_il<Ops>(sm, rb, S, logC, tw, R, inv, r4);
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
     const int rr = idx % rb, k2 = idx / rb;
-    vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[rr * C + k2];
+    vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[bitrev(k2, logC) * S + rr];
   }
 }
 
@@ -920,7 +972,7 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   const int64_t want = 2 * (int64_t)num_sms();
   while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
   while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
-  const size_t smc = (size_t)cb * R * esz, smr = (size_t)rb * C * esz;
+  const size_t smc = (size_t)(cb + 1) * R * esz, smr = (size_t)(rb + 1) * C * esz;   // padded tiles
   SK_CK(allow_dynamic_smem((const void*)k_xf_cols<Ops>));
   SK_CK(allow_dynamic_smem((const void*)k_xf_rows<Ops>));
   k_xf_cols<Ops><<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv, r4);
