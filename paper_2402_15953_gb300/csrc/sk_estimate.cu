@@ -964,7 +964,9 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   }
   const int logR = logm / 2, logC = logm - logR;
   const int R = 1 << logR, C = 1 << logC;
-  const int budget = R >= 1024 ? (128 << 10) : (64 << 10);
+  // 64 KB tiles: two or three CTAs per SM (measured against 128 KB at m = 2^20, one CTA per SM:
+  // chain8 estimate 36 -> 24 ms fused, 57 -> 45 ms GF(q), 214 -> 196 ms FP64; 32 KB: no gain)
+  const int budget = 64 << 10;
   int cb = std::max(1, std::min(C, budget / (R * esz)));
   int rb = std::max(1, std::min(R, budget / (C * esz)));
   // narrower tiles until the grid gives every SM two CTAs (a small batch of vectors would
