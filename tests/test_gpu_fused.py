@@ -123,3 +123,30 @@ def test_family_with_fused_estimator():
     assert [e["rows"] for e in got] == [e["rows"] for e in ref]
     assert all(e["limb_bits"] == 0 for e in got)
     fam.close()
+
+
+def test_widest_width_two_relations():
+    """m = 2^22 (the largest estimator width), two relations: each row is the Count-sketch
+    inner product of the two oracle sketches (Section 2.4)."""
+    rng = np.random.default_rng(22)
+    n = 100_000
+    a = rng.integers(0, 5000, size=(1, n)).astype(np.int64)
+    b = rng.integers(0, 5000, size=(1, n)).astype(np.int64)
+    wa = rng.choice(np.array([-2, 1, 3], dtype=np.int64), size=n)
+    attrs, edges, m, d = [1, 1], [(0, 0, 1, 0)], 1 << 22, 2
+    e = _estimate(attrs, edges, m, d, 5, [(a, wa), (b, None)], "fused")
+    assert e["limb_bits"] == 0
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(5, d, q.n_comp, len(q.edges))
+    sa = O.sketch_relation(q, co, 0, a, wa, m, threads=16)
+    sb = O.sketch_relation(q, co, 1, b, None, m, threads=16)
+    assert e["rows"] == [int(np.dot(sa[r], sb[r])) for r in range(d)]
+
+
+def test_eight_relation_chain_d64():
+    """An 8-relation chain with d = 64 rows (the largest d) at m = 64."""
+    wl = synth.chain(r=8, n=3000, domain=300, m=64, d=64, seed=3)
+    rels = [(r.cols.numpy(), None) for r in wl.relations]
+    e = _estimate(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, rels, "fused")
+    assert e["limb_bits"] == 0 and len(e["rows"]) == 64
+    assert e["rows"] == _oracle_rows(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, rels)
