@@ -604,6 +604,36 @@ def run_batched(args, world, rank):
     step_b()
     torch.cuda.synchronize()
     same = all(torch.equal(x.counters, y.counters) for x, y in zip(sa, sb))
+
+    # estimating all 256 sets: one sk_estimate_join per set (FP64, then fused) against one
+    # sk_estimate_many call (fused sets grouped by width)
+    def est_seq():
+        return [x.estimate() for x in sb]
+
+    def est_many():
+        return pkg.estimate_many(sb)
+
+    def host_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps, out
+
+    reps = max(1, args.steps // 5)
+    seq_fft_ms, rows_fft = host_time(est_seq, reps)
+    for x in sb:
+        x.set_estimator("fused")
+    seq_fu_ms, rows_fu = host_time(est_seq, reps)
+    many_ms, rows_many = host_time(est_many, reps)
+    for x in sb:
+        x.set_estimator("fft64")
+    est_same = [e["rows"] for e in rows_fft] == [e["rows"] for e in rows_many] == [e["rows"] for e in rows_fu]
+    estimates = {"sets": len(sb), "one_call_per_set_fft64_ms": seq_fft_ms, "one_call_per_set_fused_ms": seq_fu_ms,
+                 "estimate_many_fused_ms": many_ms, "estimates_per_s_many": len(sb) / (many_ms / 1e3),
+                 "identical_rows": est_same}
     line = {"metric": "batched build: tuples/s for 256 relations", "value": world * total / (ms_c / 1e3),
             "unit": "tuples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -612,7 +642,8 @@ def run_batched(args, world, rank):
                                    "columns (s in [0.8, 1.4], domains 1e4..1e7), m = 2^10..2^18, d = 7, +-1 weights "
                                    "with 10% deletions", "tuples_per_step": total},
             "per_relation_launches_ms": ms_a, "persistent_plan_ms": ms_b, "persistent_plan_graph_ms": ms_c,
-            "speedup_vs_per_relation": ms_a / ms_c, "identical_sketches": same, "autotuned": best}
+            "speedup_vs_per_relation": ms_a / ms_c, "identical_sketches": same, "autotuned": best,
+            "estimates": estimates}
     plan.close()
     for s in sa + sb:
         s.close()

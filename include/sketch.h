@@ -222,6 +222,20 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
 sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * sk_estimate_many: sk_estimate_join for n distinct sets in one call; out[i] is
+ * set i's estimate, identical to what sk_estimate_join would give.  Sets using
+ * SK_ESTIMATOR_FUSED whose queries qualify are grouped by width and estimated
+ * together (per CRT prime: one load, one batch of transforms and one product-sum
+ * over all their relations' rows); the others are estimated concurrently on
+ * internal worker streams (SK_MANY_WORKERS, default 4), which first wait for the
+ * work already queued on cuda_stream, and cuda_stream continues after them.  The
+ * call returns when every estimate is on the host; grouped work takes one
+ * stream-ordered device block for the call.  Returns the first error of any set.
+ * Errors: SK_ERR_INVALID_ARG (null, or a set twice), SK_ERR_UNSUPPORTED_WIDTH,
+ * and those of sk_estimate_join. */
+sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * sk_sketch_set_estimator: selects how sk_estimate_join computes each circular
  * cross-correlation (Definition 3.1); all give the identical exact result.
  *   SK_ESTIMATOR_FFT64 (default): FP64 FFTs on signed limbs, outputs rounded to

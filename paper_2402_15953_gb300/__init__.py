@@ -85,7 +85,7 @@ EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_
            "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy",
            "sk_family_create", "sk_family_update_batch", "sk_family_estimate", "sk_family_set_estimator",
            "sk_family_info", "sk_family_view", "sk_family_copy_sketch", "sk_family_reset", "sk_family_sync",
-           "sk_family_destroy"]
+           "sk_family_destroy", "sk_estimate_many"]
 
 _lib = None
 
@@ -135,6 +135,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_family_reset.argtypes = [vp, vp]
     L.sk_family_sync.argtypes = [vp, vp]
     L.sk_family_destroy.argtypes = [vp]
+    L.sk_estimate_many.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(sk_estimate), vp]
     L.sk_launch_count.argtypes = []
     L.sk_launch_count.restype = i64
     for name in EXPORTS:
@@ -550,3 +551,20 @@ class SketchFamily:
             self.close()
         except Exception:
             pass
+
+
+# ---- many sets in one call ---------------------------------------------------------------
+
+def sk_estimate_many(handles: Sequence[int], stream: int):
+    n = len(handles)
+    hs = (ctypes.c_void_p * max(1, n))(*handles)
+    out = (sk_estimate * max(1, n))()
+    _check(load().sk_estimate_many(hs, n, out, stream), "sk_estimate_many")
+    return [out[i] for i in range(n)]
+
+
+def estimate_many(sets: Sequence["SketchSet"]) -> List[dict]:
+    """The estimates of several SketchSets in one call (sk_estimate_many), on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    return [_estimate_dict(e) for e in sk_estimate_many([s.handle for s in sets], stream)]

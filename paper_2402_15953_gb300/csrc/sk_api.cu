@@ -413,6 +413,23 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream) {
   return run_estimate(set, out, (cudaStream_t)cuda_stream);
 }
 
+sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!sets || !out))) return SK_ERR_INVALID_ARG;
+  std::vector<sk_set*> v(n);
+  for (int i = 0; i < n; i++) {
+    sk_set* s = sets[i];
+    if (!s) return SK_ERR_INVALID_ARG;
+    const bool pow2 = (s->m & (s->m - 1)) == 0;
+    if (s->m < 2 || s->m > (pow2 ? (1ll << 22) : (1ll << 21))) return SK_ERR_UNSUPPORTED_WIDTH;
+    for (int j = 0; j < i; j++)
+      if (v[j] == s) return SK_ERR_INVALID_ARG;   // a set once per call (it owns one scratch)
+    v[i] = s;
+  }
+  if (n == 0) return SK_OK;
+  std::memset(out, 0, sizeof(sk_estimate) * n);
+  return run_estimate_many(v.data(), n, out, (cudaStream_t)cuda_stream);
+}
+
 sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_stream) {
   if (!set || !out) return SK_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));

@@ -28,7 +28,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <thread>
 
 #include "sk_internal.h"
 
@@ -1409,6 +1411,31 @@ bool fu_eligible(const sk_set* s, unsigned long long* negmask) {
 std::mutex g_fu_const_mutex;
 bool g_fu_const_ready[64] = {false};
 
+// Uploads the primes' constants to the current device once; *ready false when the fused
+// form cannot run here (fewer primes than needed, device index beyond the table).
+cudaError_t fu_constants(bool* ready) {
+  *ready = false;
+  const std::vector<FuPrime>& pr = fu_primes();
+  if ((int)pr.size() < kFuMaxPrimes) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_fu_const_mutex);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaSuccess;
+  if (!g_fu_const_ready[dev]) {
+    uint32_t ps[kFuMaxPrimes], pis[kFuMaxPrimes];
+    for (int i = 0; i < kFuMaxPrimes; i++) {
+      ps[i] = pr[i].p;
+      pis[i] = pr[i].pinv;
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_fu_p, ps, sizeof(ps));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_fu_pinv, pis, sizeof(pis));
+    if (e != cudaSuccess) return e;
+    g_fu_const_ready[dev] = true;
+  }
+  *ready = true;
+  return cudaSuccess;
+}
+
 // The fused estimate; *done false when it does not apply (the caller then estimates
 // step by step).
 sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
@@ -1418,23 +1445,9 @@ sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool*
   unsigned long long negmask = 0;
   if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
   const std::vector<FuPrime>& pr = fu_primes();
-  if ((int)pr.size() < kFuMaxPrimes) return SK_OK;
-  {
-    std::lock_guard<std::mutex> lk(g_fu_const_mutex);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return SK_OK;
-    if (!g_fu_const_ready[dev]) {
-      uint32_t ps[kFuMaxPrimes], pis[kFuMaxPrimes];
-      for (int i = 0; i < kFuMaxPrimes; i++) {
-        ps[i] = pr[i].p;
-        pis[i] = pr[i].pinv;
-      }
-      SK_CK(cudaMemcpyToSymbol(c_fu_p, ps, sizeof(ps)));
-      SK_CK(cudaMemcpyToSymbol(c_fu_pinv, pis, sizeof(pis)));
-      g_fu_const_ready[dev] = true;
-    }
-  }
+  bool ready = false;
+  SK_CK(fu_constants(&ready));
+  if (!ready) return SK_OK;
   if (!s->d_fu_rel) {
     SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
     SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
@@ -1763,6 +1776,277 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
     bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(M, 1)) - 3);
   }
   return SK_ERR_INEXACT;
+}
+
+// ===========================================================================
+// Many sets at once (sk_estimate_many).  Sets that use the fused form and qualify are
+// grouped by width; each group is estimated with one load, one transform pass and one
+// product-sum per prime over all of its (set, relation, row) vectors, with a descriptor
+// per output row.  The other sets run their own estimates concurrently on worker streams.
+// ===========================================================================
+struct FuOut {
+  int64_t base;                 // first vector of the set; vector (base + k d + row)
+  int r, d, row;
+  unsigned long long negmask;   // relations with s_k = -1
+};
+
+// l1[v] = sum_j |rows[v][j]|
+__global__ void __launch_bounds__(256) k_fu_l1_rows(const int64_t* const* rows, int64_t m, double* l1) {
+  __shared__ double red[256];
+  const int64_t* c = rows[blockIdx.x];
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) s += fabs((double)c[j]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) l1[blockIdx.x] = red[0];
+}
+
+// out[v * m + j] = rows[v][j] mod p, Montgomery form
+template <int PI>
+__global__ void k_fu_load_rows(const int64_t* const* rows, int64_t nvec, int logm, uint32_t r2, uint32_t r3,
+                               uint32_t* out) {
+  using O = MontOps<PI>;
+  const int64_t m = (int64_t)1 << logm, total = nvec * m;
+  const uint32_t p = c_fu_p[PI];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t c = rows[g >> logm][g & (m - 1)];
+    const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
+    uint32_t h = (uint32_t)(mag >> 32);
+    if (h >= p) h -= p;
+    const uint32_t v = O::add(O::mul(h, r3), O::mul((uint32_t)mag, r2));
+    out[g] = c < 0 ? O::neg(v) : v;
+  }
+}
+
+template <int PI>
+__global__ void __launch_bounds__(256) k_fu_reduce_many(const uint32_t* W, const FuOut* outs, int64_t M, int nchunk,
+                                                        uint32_t* part) {
+  using O = MontOps<PI>;
+  __shared__ uint32_t red[256];
+  const FuOut f = outs[blockIdx.x / nchunk];
+  const int c = blockIdx.x % nchunk;
+  const int64_t clen = M / nchunk;
+  uint32_t s = 0;
+  for (int64_t nu = (int64_t)c * clen + threadIdx.x; nu < (int64_t)(c + 1) * clen; nu += blockDim.x) {
+    const int64_t neg_nu = (M - nu) & (M - 1);
+    uint32_t prod = W[(f.base + f.row) * M + ((f.negmask & 1ull) ? neg_nu : nu)];
+    for (int k = 1; k < f.r; k++)
+      prod = O::mul(prod, W[(f.base + (int64_t)k * f.d + f.row) * M + (((f.negmask >> k) & 1ull) ? neg_nu : nu)]);
+    s = O::add(s, prod);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = O::add(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// One prime over a group: twiddles, load, forward transforms, product-sums, row values.
+template <int PI>
+sk_status fu_group_pass(const FuPrime& fp, int64_t M, const int64_t* const* d_rows, int64_t nvec, const FuOut* d_outs,
+                        int nout, uint32_t* tw, uint32_t* V, uint32_t* W, uint32_t* part, int nchunk, uint32_t* res,
+                        cudaStream_t st) {
+  const uint64_t p = fp.p;
+  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);
+  const uint64_t winv = fu_powmod(w, p - 2, p);
+  k_fu_twiddle<PI><<<grid_for(std::max<int64_t>(1, M / 2)), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p),
+                                                                           fu_to_mont(winv, fp.p), fu_to_mont(1, fp.p));
+  k_fu_load_rows<PI><<<grid_for(nvec * M), 256, 0, st>>>(d_rows, nvec, ilog2(M), fp.r2, fp.r3, V);
+  count_launch(2);
+  SK_CK(cudaGetLastError());
+  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
+  sk_status fs = xform<MontOps<PI>>(V, W, nvec, M, tw, false, r4, st);
+  if (fs != SK_OK) return fs;
+  k_fu_reduce_many<PI><<<nout * nchunk, 256, 0, st>>>(W, d_outs, M, nchunk, part);
+  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
+  k_fu_final<PI><<<(nout + 63) / 64, 64, 0, st>>>(part, nout, nchunk, minv, res, kFuMaxPrimes);
+  count_launch(2);
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+// The fused estimates of one group of sets of width M (all eligible); done[i] is set for
+// every set estimated here (a group whose bound needs more than 9 primes is left to the
+// caller).
+sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_estimate* out, std::vector<char>& done,
+                   cudaStream_t st) {
+  const std::vector<FuPrime>& pr = fu_primes();
+  std::vector<const int64_t*> rows;
+  std::vector<FuOut> outs;
+  for (int i : idx) {
+    sk_set* s = sets[i];
+    unsigned long long negmask = 0;
+    fu_eligible(s, &negmask);
+    const int64_t base = (int64_t)rows.size();
+    for (int k = 0; k < s->r; k++)
+      for (int row = 0; row < s->d; row++) rows.push_back(s->rel_ctr[k] + (int64_t)row * M);
+    for (int row = 0; row < s->d; row++) outs.push_back({base, s->r, s->d, row, negmask});
+  }
+  const int64_t nvec = (int64_t)rows.size();
+  const int nout = (int)outs.size();
+  int nchunk = 1;
+  while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)nout * nchunk * 2 <= 4096) nchunk *= 2;
+  // one stream-ordered block: row pointers | descriptors | l1 | residues | partials |
+  // twiddles | V | W (freed at the end of the call)
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_rows = al(nvec * sizeof(void*)), b_outs = al(nout * sizeof(FuOut)), b_l1 = al(nvec * 8),
+               b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
+               b_tw = al((size_t)M * 4), b_v = al((size_t)nvec * M * 4);
+  char* blk = nullptr;
+  SK_CK(cudaMallocAsync((void**)&blk, b_rows + b_outs + b_l1 + b_res + b_part + b_tw + 2 * b_v, st));
+  const int64_t** d_rows = (const int64_t**)blk;
+  FuOut* d_outs = (FuOut*)(blk + b_rows);
+  double* d_l1 = (double*)(blk + b_rows + b_outs);
+  uint32_t* d_res = (uint32_t*)(blk + b_rows + b_outs + b_l1);
+  uint32_t* d_part = (uint32_t*)((char*)d_res + b_res);
+  uint32_t* d_tw = (uint32_t*)((char*)d_part + b_part);
+  uint32_t* V = (uint32_t*)((char*)d_tw + b_tw);
+  uint32_t* W = (uint32_t*)((char*)V + b_v);
+  sk_status status = SK_OK;
+  auto fail = [&](sk_status x) {
+    if (status == SK_OK) status = x;
+  };
+  std::vector<double> l1(nvec);
+  std::vector<uint32_t> res((size_t)nout * kFuMaxPrimes);
+  int np = 0;
+  do {
+    cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), nvec * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_outs, outs.data(), nout * sizeof(FuOut), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
+    k_fu_l1_rows<<<(unsigned)nvec, 256, 0, st>>>(d_rows, M, d_l1);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(l1.data(), d_l1, nvec * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
+    double bits = 0.0;
+    for (const FuOut& f : outs) {
+      double b = 0.0;
+      bool zero = false;
+      for (int k = 0; k < f.r; k++) {
+        const double v = l1[f.base + (int64_t)k * f.d + f.row];
+        if (v <= 0.0) zero = true;
+        else b += std::log2(v * (1.0 + 1e-9));
+      }
+      if (!zero) bits = std::max(bits, b);
+    }
+    double cover = 0.0;
+    while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
+    if (cover < bits + 3.0) { np = 0; break; }   // left to the per-set estimates
+    for (int i = 0; i < np && status == SK_OK; i++) {
+      sk_status ps;
+      switch (i) {
+        case 0: ps = fu_group_pass<0>(pr[0], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 1: ps = fu_group_pass<1>(pr[1], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 2: ps = fu_group_pass<2>(pr[2], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 3: ps = fu_group_pass<3>(pr[3], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 4: ps = fu_group_pass<4>(pr[4], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 5: ps = fu_group_pass<5>(pr[5], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 6: ps = fu_group_pass<6>(pr[6], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        case 7: ps = fu_group_pass<7>(pr[7], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+        default: ps = fu_group_pass<8>(pr[8], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+      }
+      fail(ps);
+    }
+    if (status != SK_OK) break;
+    e = cudaMemcpyAsync(res.data(), d_res, res.size() * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) fail(set_status_from_cuda(e));
+  } while (false);
+  const cudaError_t ef = cudaFreeAsync(blk, st);
+  if (status != SK_OK) return status;
+  if (ef != cudaSuccess) return set_status_from_cuda(ef);
+  if (np == 0) return SK_OK;
+  int o = 0;
+  for (int i : idx) {
+    sk_set* s = sets[i];
+    I256 r_rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
+    for (int row = 0; row < s->d; row++, o++)
+      if (!fu_crt(res.data() + (size_t)o * kFuMaxPrimes, np, pr, &r_rows[row])) return SK_ERR_OVERFLOW;
+    std::memcpy(sorted, r_rows, sizeof(I256) * s->d);
+    std::sort(sorted, sorted + s->d, [](const I256& a, const I256& b) { return i256_lt(a, b); });
+    fill_estimate(&out[i], r_rows, sorted, s->d);
+    out[i].max_residual = 0.0;
+    out[i].max_limbs = np;
+    out[i].limb_bits = 0;
+    out[i].corr_steps = s->corr_steps;
+    out[i].retries = 0;
+    done[i] = 1;
+  }
+  return SK_OK;
+}
+
+int many_workers() {
+  const char* v = std::getenv("SK_MANY_WORKERS");
+  const int x = v ? std::atoi(v) : 4;
+  return x < 1 ? 1 : (x > 16 ? 16 : x);
+}
+
+sk_status run_estimate_many(sk_set** sets, int n, sk_estimate* out, cudaStream_t st) {
+  std::vector<char> done(n, 0);
+  std::vector<sk_status> status(n, SK_OK);
+  // fused groups by width, on the caller's stream
+  std::map<int64_t, std::vector<int>> groups;
+  bool ready = false;
+  SK_CK(fu_constants(&ready));
+  for (int i = 0; i < n; i++) {
+    sk_set* s = sets[i];
+    unsigned long long nm = 0;
+    const int64_t m = s->m;
+    if (ready && s->estimator == SK_ESTIMATOR_FUSED && (m & (m - 1)) == 0 && m >= 2 && m <= (1ll << 22) &&
+        fu_eligible(s, &nm))
+      groups[m].push_back(i);
+  }
+  for (auto& g : groups) {
+    const sk_status gs = fu_group(sets, g.second, g.first, out, done, st);
+    if (gs != SK_OK) return gs;
+  }
+  // everything else: per-set estimates on worker streams, after the caller's queued work
+  std::vector<int> rest;
+  for (int i = 0; i < n; i++)
+    if (!done[i]) rest.push_back(i);
+  if (rest.empty()) return SK_OK;
+  const int nw = std::min<int>(many_workers(), (int)rest.size());
+  std::vector<cudaStream_t> ws(nw, nullptr);
+  cudaEvent_t ev = nullptr;
+  cudaError_t ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev, st);
+  for (int w = 0; w < nw && ce == cudaSuccess; w++) {
+    ce = cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ws[w], ev, 0);
+  }
+  if (ce == cudaSuccess) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto work = [&](int w) {
+      cudaSetDevice(dev);
+      for (size_t j = w; j < rest.size(); j += nw) {
+        const int i = rest[j];
+        status[i] = run_estimate(sets[i], &out[i], ws[w]);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int w = 1; w < nw; w++) th.emplace_back(work, w);
+    work(0);
+    for (auto& t : th) t.join();
+    for (int w = 0; w < nw && ce == cudaSuccess; w++) {   // the caller's stream continues after them
+      ce = cudaEventRecord(ev, ws[w]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, ev, 0);
+    }
+  }
+  for (cudaStream_t w : ws)
+    if (w) cudaStreamDestroy(w);
+  if (ev) cudaEventDestroy(ev);
+  if (ce != cudaSuccess) return set_status_from_cuda(ce);
+  for (int i : rest)
+    if (status[i] != SK_OK) return status[i];
+  return SK_OK;
 }
 
 // ===========================================================================

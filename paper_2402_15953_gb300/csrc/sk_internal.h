@@ -99,6 +99,7 @@ sk_status launch_merge(int64_t* dst, const int64_t* src, int64_t count, cudaStre
 // sk_estimate.cu
 sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st);
 sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st);
+sk_status run_estimate_many(sk_set** sets, int n, sk_estimate* out, cudaStream_t st);
 void free_estimator(sk_set* s);
 
 // sk_api.cu
