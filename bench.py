@@ -56,6 +56,8 @@ def parse_args():
                     help="do not declare the key domains (every tuple is hashed; no key tables)")
     ap.add_argument("--estimate-priority", default="high", choices=["high", "normal"],
                     help="stream priority of the estimates that overlap the next step's update")
+    ap.add_argument("--estimator", default="fused", choices=["fft64", "ntt", "fused"],
+                    help="exact estimator arithmetic of the star step (identical rows from each)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not overlap step i's estimate with step i+1's update")
     return ap.parse_args()
@@ -271,6 +273,7 @@ def run_ours(args, world, rank, local):
     rels = [r.cols for r in wl.relations]
     total = sum(int(c.shape[1]) for c in rels)
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, device=dev)
+    s.set_estimator(args.estimator)
     stream = torch.cuda.current_stream()
     doms = declared_domains(args, wl)
 
@@ -322,29 +325,22 @@ def run_ours(args, world, rank, local):
     ms_per_step = max_over_ranks(world, total_ms / args.steps)
     value = world * total / (ms_per_step / 1e3)
 
-    # The same estimate with the GF(q) number-theoretic-transform backend (identical rows).
-    s.set_estimator("ntt")
-    ntt_est = s.estimate()
-    torch.cuda.synchronize()
+    # The same estimate in each exact arithmetic (identical rows): the FP64 FFT with its
+    # certificate, the GF(q) number-theoretic transform, the fused product of spectra modulo
+    # CRT primes (this query qualifies).
+    by_arith = {}
     e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_a.record(stream)
-    for _ in range(args.steps):
-        ntt_est = s.estimate()
-    e_b.record(stream)
-    torch.cuda.synchronize()
-    ntt_ms = e_a.elapsed_time(e_b) / args.steps
-    ntt_same = ntt_est["rows"] == est["rows"]
-    # ... and with the fused product of spectra modulo CRT primes (this query qualifies)
-    s.set_estimator("fused")
-    fu_est = s.estimate()
-    torch.cuda.synchronize()
-    e_a.record(stream)
-    for _ in range(args.steps):
-        fu_est = s.estimate()
-    e_b.record(stream)
-    torch.cuda.synchronize()
-    fused_ms = e_a.elapsed_time(e_b) / args.steps
-    s.set_estimator("fft64")
+    for name in ("fft64", "ntt", "fused"):
+        s.set_estimator(name)
+        alt = s.estimate()
+        torch.cuda.synchronize()
+        e_a.record(stream)
+        for _ in range(args.steps):
+            alt = s.estimate()
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        by_arith[name] = (e_a.elapsed_time(e_b) / args.steps, alt)
+    s.set_estimator(args.estimator)
 
     # Pipelined steps: two counter buffers; step i's update runs on the update stream while
     # step i-1's estimate runs on the estimate stream (the update is integer-bound, the FFTs
@@ -353,6 +349,7 @@ def run_ours(args, world, rank, local):
     pipe = None
     if not args.no_pipeline:
         s2 = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, device=dev)
+        s2.set_estimator(args.estimator)
         sets = [s, s2]
         upd = torch.cuda.Stream()
         est_stream = torch.cuda.Stream(priority=-1 if args.estimate_priority == "high" else 0)
@@ -447,7 +444,7 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic", "estimator": args.estimator,
         "config": {**star_config(args, total),
                    "parallelism": f"replicas x{world}",
                    "pipelined": pipe is not None and value == pipe["value"]},
@@ -456,12 +453,10 @@ def run_ours(args, world, rank, local):
         "p50_ms": statistics.median(step_ms), "p99_ms": percentile(step_ms, 99.0),
         "update_ms": statistics.mean(upd_all_ms), "estimate_ms": statistics.mean(step_ms) - statistics.mean(upd_all_ms),
         "fact_update_ms": fact_ms,
-        "estimate_ntt": {"estimate_ms": ntt_ms, "identical_rows": ntt_same,
-                         "step_ms_with_ntt": statistics.mean(upd_all_ms) + ntt_ms,
-                         "note": "sk_sketch_set_estimator(SK_ESTIMATOR_NTT); the headline uses the FP64 FFT"},
-        "estimate_fused": {"estimate_ms": fused_ms, "identical_rows": fu_est["rows"] == est["rows"],
-                           "primes": fu_est["max_limbs"], "step_ms_with_fused": statistics.mean(upd_all_ms) + fused_ms,
-                           "note": "sk_sketch_set_estimator(SK_ESTIMATOR_FUSED)"},
+        **{f"estimate_{name}": {"estimate_ms": ms_e, "identical_rows": alt["rows"] == est["rows"],
+                                "limbs_or_primes": alt["max_limbs"], "limb_bits": alt["limb_bits"],
+                                "step_ms_serial_with_it": statistics.mean(upd_all_ms) + ms_e}
+           for name, (ms_e, alt) in by_arith.items()},
         "roofline": roofline, **extra,
         "estimate_check": {"median": str(est["median"]), "max_residual": est["max_residual"],
                            "max_limbs": est["max_limbs"], "limb_bits": est["limb_bits"]},
@@ -606,7 +601,11 @@ def run_batched(args, world, rank):
     same = all(torch.equal(x.counters, y.counters) for x, y in zip(sa, sb))
 
     # estimating all 256 sets: one sk_estimate_join per set (FP64, then fused) against one
-    # sk_estimate_many call (fused sets grouped by width)
+    # sk_estimate_many call (fused sets grouped by width).  Each dimension relation first gets
+    # 2e4 keys from the fact column it joins, so every estimate is of a non-empty join.
+    for s, b in zip(sb, wl):
+        for k in range(1, len(b.num_join_attrs)):
+            s.update(k, b.relation.cols[k - 1:k, :20_000].contiguous())
     def est_seq():
         return [x.estimate() for x in sb]
 
@@ -821,6 +820,8 @@ def run_e2e_direct_pipelined(args, wl, world):
     h2d = sum(h.numel() * 8 for h in host)
     doms = declared_domains(args, wl)
     sets = [pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed) for _ in range(2)]
+    for x in sets:
+        x.set_estimator(args.estimator)
     upd, est = torch.cuda.Stream(), torch.cuda.Stream(priority=-1 if args.estimate_priority == "high" else 0)
     done = [torch.cuda.Event() for _ in range(2)]
 
