@@ -400,12 +400,12 @@ def run_ours(args, world, rank, local):
         # (5 key loads, 5 gathers of 32-byte records, 9 counter atomics each).
         # HBM roofline (algorithmic bytes = the 40 key bytes per tuple; tables and sketch are
         # meant to stay in L2).  traffic = DRAM bytes of one ncu capture of k_update_tab at
-        # 2e7 rows (1.450 GB, record misses included) scaled to this row count, plus the
+        # 2e7 rows (1.448 GB, record misses included) scaled to this row count, plus the
         # table write (5e6 records x 32 B).
         # L2 roofline, the bound that binds: L2 tag lookups per tuple from the same capture
         # (16.35 = 9 atomics + key and record reads + lookups forwarded between the two dies'
         # L2 halves) against 188 slices x 1 lookup per cycle x 2.016 GHz.
-        traffic = 1.450e9 * args.fact_rows / 2e7 / 1e9 + 5 * 1_000_000 * 32 / 1e9
+        traffic = 1.448e9 * args.fact_rows / 2e7 / 1e9 + 5 * 1_000_000 * 32 / 1e9
         kernel = "k_key_table + k_update_tab<5,pow2,global,narrow,v8> (fact table F)"
         l2_req_per_tuple = 16.35
         l2_peak = 188 * 2.016e9
@@ -418,7 +418,7 @@ def run_ours(args, world, rank, local):
         extra = {"roofline_l2": {"bound": "l2_tag_lookups", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
                                  "unit": "G lookups/s", "frac": l2_rate / l2_peak,
                                  "per_tuple": l2_req_per_tuple, "kernel": kernel,
-                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 82 % of peak"}}
+                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 84 % of peak"}}
     else:
         # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
         # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the

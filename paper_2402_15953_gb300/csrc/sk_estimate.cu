@@ -1221,20 +1221,45 @@ __global__ void k_fu_twiddle(uint32_t* tw, uint32_t* itw, int64_t n, uint32_t w,
   }
 }
 
-// l1[k * d + row] = sum_j |c_k[row][j]| (double; the host adds a safety margin)
-__global__ void __launch_bounds__(256) k_fu_l1(const int64_t* const* rel, int d, int64_t m, double* l1) {
+// Partial l1 norms: vector v (= blockIdx.x / nch) is base[v / per] + (v % per) m; block
+// (v, ch) writes part[v * nch + ch] = sum |c[j]| over the ch-th of nch equal chunks (nch
+// divides m). The host adds a vector's partials in order (double; it adds a safety margin).
+__global__ void __launch_bounds__(256) k_fu_l1(const int64_t* const* base, int per, int64_t m, int nch,
+                                               double* part) {
   __shared__ double red[256];
-  const int k = blockIdx.x / d, row = blockIdx.x % d;
-  const int64_t* c = rel[k] + (int64_t)row * m;
+  const int64_t v = blockIdx.x / nch, ch = blockIdx.x % nch, len = m / nch;
+  const int64_t* c = base[v / per] + (v % per) * m + ch * len;
   double s = 0.0;
-  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) s += fabs((double)c[j]);
+  for (int64_t j = threadIdx.x; j < len; j += blockDim.x) s += fabs((double)__ldg(c + j));
   red[threadIdx.x] = s;
   __syncthreads();
   for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) l1[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// chunks per vector for k_fu_l1: at least 2048 elements each, about four waves of blocks
+int fu_l1_chunks(int64_t nvec, int64_t m) {
+  int nch = 1;
+  while (m / (nch * 2) >= 2048 && nvec * nch < 4 * (int64_t)num_sms()) nch *= 2;
+  return nch;
+}
+
+// Launches k_fu_l1 and reads the nvec norms back (synchronises st).
+sk_status fu_l1_norms(const int64_t* const* base, int per, int64_t nvec, int64_t m, double* d_part, int nch,
+                      std::vector<double>& l1, cudaStream_t st) {
+  k_fu_l1<<<(unsigned)(nvec * nch), 256, 0, st>>>(base, per, m, nch, d_part);
+  count_launch();
+  SK_CK(cudaGetLastError());
+  std::vector<double> part((size_t)nvec * nch);
+  SK_CK(cudaMemcpyAsync(part.data(), d_part, part.size() * 8, cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  l1.assign((size_t)nvec, 0.0);
+  for (int64_t v = 0; v < nvec; v++)
+    for (int c = 0; c < nch; c++) l1[v] += part[(size_t)v * nch + c];
+  return SK_OK;
 }
 
 // out[(k d + row) m + j] = c_k[row][j] mod p, Montgomery form (|c| = h 2^32 + l)
@@ -1455,19 +1480,17 @@ sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool*
   // scratch: l1 [r][d] doubles | residues [d][9] | partials [d][nchunk] | V, W [r][d][m] words
   int nchunk = 1;
   while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
-  const size_t l1_bytes = ((size_t)r * d * 8 + 255) & ~(size_t)255;
+  const int l1ch = fu_l1_chunks((int64_t)r * d, m);
+  const size_t l1_bytes = ((size_t)r * d * l1ch * 8 + 255) & ~(size_t)255;
   const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
   const size_t part_bytes = ((size_t)d * nchunk * 4 + 255) & ~(size_t)255;
   SK_CK(ensure(s->scratch, l1_bytes + res_bytes + part_bytes, st));
   double* d_l1 = (double*)s->scratch.ptr;
   uint32_t* d_res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
   uint32_t* d_part = (uint32_t*)((char*)d_res + res_bytes);
-  k_fu_l1<<<r * d, 256, 0, st>>>(s->d_fu_rel, d, m, d_l1);
-  count_launch();
-  SK_CK(cudaGetLastError());
-  std::vector<double> l1((size_t)r * d);
-  SK_CK(cudaMemcpyAsync(l1.data(), d_l1, l1.size() * 8, cudaMemcpyDeviceToHost, st));
-  SK_CK(cudaStreamSynchronize(st));
+  std::vector<double> l1;
+  const sk_status ls = fu_l1_norms(s->d_fu_rel, d, (int64_t)r * d, m, d_l1, l1ch, l1, st);
+  if (ls != SK_OK) return ls;
   double bits = 0.0;   // log2 of the largest row bound prod_k ||c_k||_1
   for (int row = 0; row < d; row++) {
     double b = 0.0;
@@ -1790,21 +1813,6 @@ struct FuOut {
   unsigned long long negmask;   // relations with s_k = -1
 };
 
-// l1[v] = sum_j |rows[v][j]|
-__global__ void __launch_bounds__(256) k_fu_l1_rows(const int64_t* const* rows, int64_t m, double* l1) {
-  __shared__ double red[256];
-  const int64_t* c = rows[blockIdx.x];
-  double s = 0.0;
-  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) s += fabs((double)c[j]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) l1[blockIdx.x] = red[0];
-}
-
 // out[v * m + j] = rows[v][j] mod p, Montgomery form
 template <int PI>
 __global__ void k_fu_load_rows(const int64_t* const* rows, int64_t nvec, int logm, uint32_t r2, uint32_t r3,
@@ -1895,8 +1903,9 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   // one stream-ordered block: row pointers | descriptors | l1 | residues | partials |
   // twiddles | V | W (freed at the end of the call)
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t b_rows = al(nvec * sizeof(void*)), b_outs = al(nout * sizeof(FuOut)), b_l1 = al(nvec * 8),
-               b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
+  const int l1ch = fu_l1_chunks(nvec, M);
+  const size_t b_rows = al(nvec * sizeof(void*)), b_outs = al(nout * sizeof(FuOut)),
+               b_l1 = al((size_t)nvec * l1ch * 8), b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
                b_tw = al((size_t)M * 4), b_v = al((size_t)nvec * M * 4);
   char* blk = nullptr;
   SK_CK(cudaMallocAsync((void**)&blk, b_rows + b_outs + b_l1 + b_res + b_part + b_tw + 2 * b_v, st));
@@ -1912,19 +1921,15 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   auto fail = [&](sk_status x) {
     if (status == SK_OK) status = x;
   };
-  std::vector<double> l1(nvec);
+  std::vector<double> l1;
   std::vector<uint32_t> res((size_t)nout * kFuMaxPrimes);
   int np = 0;
   do {
     cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), nvec * sizeof(void*), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_outs, outs.data(), nout * sizeof(FuOut), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
-    k_fu_l1_rows<<<(unsigned)nvec, 256, 0, st>>>(d_rows, M, d_l1);
-    count_launch();
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(l1.data(), d_l1, nvec * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
+    const sk_status ls = fu_l1_norms(d_rows, 1, nvec, M, d_l1, l1ch, l1, st);
+    if (ls != SK_OK) { fail(ls); break; }
     double bits = 0.0;
     for (const FuOut& f : outs) {
       double b = 0.0;

@@ -297,6 +297,13 @@ __device__ __forceinline__ int64_t ld_key_stream(const int64_t* ptr) {
   return v;
 }
 
+// Lane-wise sum of two pairs of 16-bit values (each half mod 2^16, no carry across halves):
+// the low 15 bits of each half add normally, bit 15 is the XOR of both inputs' bit 15 with
+// the carry into it.
+__device__ __forceinline__ uint32_t add16x2(uint32_t a, uint32_t b) {
+  return ((a & 0x7fff7fffu) + (b & 0x7fff7fffu)) ^ ((a ^ b) & 0x80008000u);
+}
+
 // One 32-byte record with a single 256-bit load.  Only for records of exactly two
 // 16-byte vectors: the table base is 256-byte aligned, so every record is 32-byte aligned.
 __device__ __forceinline__ void ld_record32(const uint4* ptr, uint32_t (&w)[8]) {
@@ -329,24 +336,44 @@ __device__ __forceinline__ void update_tuple_tab(const UpdArgs& p, const TabArgs
   const uint32_t m32 = (uint32_t)p.m;
   if (V8 && NARROW) {
     // d <= 14: bins in words 0..6, sign mask in word 7
-    uint32_t b[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, sg = 0;
+    if (POW2) {
+      // m divides 2^16, so each bin sum is needed mod 2^16 only: two rows per 32-bit word,
+      // added lane-wise without a carry between the 16-bit halves
+      uint32_t b2[7] = {0, 0, 0, 0, 0, 0, 0}, sg = 0;
 #pragma unroll
-    for (int u = 0; u < AM; u++) {
-      if (A == 0 && u >= na) break;
-      uint32_t w[8];
-      ld_record32(rec[u], w);
-      sg ^= w[7];
+      for (int u = 0; u < AM; u++) {
+        if (A == 0 && u >= na) break;
+        uint32_t w[8];
+        ld_record32(rec[u], w);
+        sg ^= w[7];
+#pragma unroll
+        for (int j = 0; j < 7; j++) b2[j] = add16x2(b2[j], w[j]);
+      }
 #pragma unroll
       for (int j = 0; j < 14; j++) {
-        b[j] += (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-        if (!POW2 && b[j] >= m32) b[j] -= m32;
+        if (j >= p.d) break;
+        const uint32_t bin = (b2[j >> 1] >> (16 * (j & 1))) & (m32 - 1);
+        scatter_row<SMEM>(p, s_sub, small, j, bin, ((sg >> j) & 1u) ? -delta : delta);
       }
-    }
+    } else {
+      uint32_t b[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, sg = 0;
 #pragma unroll
-    for (int j = 0; j < 14; j++) {
-      if (j >= p.d) break;
-      const uint32_t bin = POW2 ? (b[j] & (m32 - 1)) : b[j];
-      scatter_row<SMEM>(p, s_sub, small, j, bin, ((sg >> j) & 1u) ? -delta : delta);
+      for (int u = 0; u < AM; u++) {
+        if (A == 0 && u >= na) break;
+        uint32_t w[8];
+        ld_record32(rec[u], w);
+        sg ^= w[7];
+#pragma unroll
+        for (int j = 0; j < 14; j++) {
+          b[j] += (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+          if (b[j] >= m32) b[j] -= m32;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 14; j++) {
+        if (j >= p.d) break;
+        scatter_row<SMEM>(p, s_sub, small, j, b[j], ((sg >> j) & 1u) ? -delta : delta);
+      }
     }
   } else if (V8) {
     // d <= 8: one word per row

@@ -76,9 +76,11 @@ __global__ void __launch_bounds__(256) k_key_table(UpdArgs p, TabArgs t) {
   }
 }
 
-// Algorithm 2 through the key tables; scatter targets as in k_update.
+// Algorithm 2 through the key tables; scatter targets as in k_update.  The instances with
+// 32-byte narrow records and a power-of-two width fit 48 registers without spills, which
+// gives five CTAs per SM and more gathers in flight (star F update 5.63 -> 5.50 ms).
 template <int A, bool POW2, bool SMEM, bool NARROW, bool V8>
-__global__ void __launch_bounds__(256) k_update_tab(UpdArgs p, TabArgs t) {
+__global__ void __launch_bounds__(256, (A > 0 && V8 && NARROW && POW2) ? 5 : 1) k_update_tab(UpdArgs p, TabArgs t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* s_sub = (int*)smem_raw;
   const int64_t dm = (int64_t)p.d * (int64_t)p.m;

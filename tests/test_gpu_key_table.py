@@ -52,7 +52,7 @@ MODES = {"direct": ("0", "1"), "table": ("1", "1"), "table-16B-loads": ("1", "0"
 @pytest.mark.parametrize("a,d,m", [(1, 1, 64), (2, 3, 1000), (3, 9, 1 << 16), (5, 9, 1 << 16), (5, 7, 77777),
                                     (4, 64, 1 << 12), (7, 5, 1 << 14), (2, 13, 256), (3, 14, 1 << 16),
                                     (2, 15, 4096), (3, 32, 2048), (6, 9, 65535), (2, 5, 1 << 18),
-                                    (2, 9, 50000)])
+                                    (2, 9, 50000), (5, 11, 1 << 15), (3, 1, 2)])
 def test_key_table_bit_exact(mode, a, d, m, monkeypatch):
     """mode: per-tuple hashing; key tables with 32-byte records read by one 256-bit load
     where they apply; key tables read in 16-byte loads only (SK_TAB_V8=0)."""
