@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-tuples", type=int, default=1_000_000)
     ap.add_argument("--workload", default="star",
-                    choices=["star", "batched", "serving", "chain3", "chain8", "subqueries"],
+                    choices=["star", "batched", "serving", "chain3", "chain8", "subqueries", "shapes"],
                     help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
                          "launches; serving: request loop latency")
     ap.add_argument("--requests", type=int, default=4000)
@@ -1006,6 +1006,63 @@ def run_subqueries(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_shapes(args, world, rank):
+    """Estimator arithmetics beyond the pairwise power-of-two case: (a) Figure 3's query
+    (a component of three attributes) with 10^6 Zipf(1.1) rows per relation over [0, 1e6),
+    m = 2^16, d = 9; (b) a three-relation chain with 10^6 Zipf(1.2) rows per relation at
+    the paper's width m = 10^6, d = 5.  Times one estimate in each exact arithmetic (FP64
+    FFT with certificate, GF(q) transform with limbs, Algorithm 3's schedule modulo CRT
+    primes) with CUDA events and checks the rows are identical."""
+    import torch
+
+    import paper_2402_15953_gb300 as pkg
+    import synth
+    from paper_2402_15953_gb300 import build as pkg_build
+    pkg_build.build()
+    stream = torch.cuda.current_stream()
+    attrs, edges = synth.fig3_query()
+    fig3_rels = [synth.random_relation(1_000_000, [1_000_000] * a, 60 + k, device="cuda", zipf_s=1.1).cols
+                 for k, a in enumerate(attrs)]
+    ch = synth.chain(r=3, n=1_000_000, m=1_000_000, d=5, device="cuda")
+    cases = [("figure3 m=2^16 d=9", attrs, edges, 1 << 16, 9, 42, fig3_rels),
+             ("chain3 m=10^6 d=5", ch.num_join_attrs, ch.edges, ch.m, ch.d, ch.hash_seed,
+              [r.cols for r in ch.relations])]
+    reps = max(3, args.steps // 5)
+    out = {}
+    for name, at, ed, m, d, seed, rels in cases:
+        st = pkg.SketchSet(at, ed, m, d, seed)
+        for k, c in enumerate(rels):
+            st.update(k, c)
+        res = {}
+        rows = None
+        for arith in ("fft64", "ntt", "fused"):
+            st.set_estimator(arith)
+            for _ in range(args.warmup):
+                est = st.estimate()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                est = st.estimate()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[arith] = {"estimate_ms": e0.elapsed_time(e1) / reps, "limbs_or_primes": est["max_limbs"],
+                          "limb_bits": est["limb_bits"]}
+            rows = est["rows"] if rows is None else rows
+            res[arith]["identical_rows"] = est["rows"] == rows
+        res["median"] = str(est["median"])
+        out[name] = res
+        st.close()
+    fu = [v["fused"]["estimate_ms"] for v in out.values()]
+    line = {"metric": "estimates/s beyond the pairwise power-of-two case (schedule modulo CRT primes)",
+            "value": len(fu) * 1e3 / sum(fu), "unit": "estimates/s", "n_gpus": world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": sum(fu), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "shapes: figure3 m=2^16 d=9; chain3 m=10^6 d=5"}, "cases": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
@@ -1019,6 +1076,8 @@ def main():
         run_small_config(args, world, rank, args.workload)
     elif args.workload == "subqueries":
         run_subqueries(args, world, rank)
+    elif args.workload == "shapes":
+        run_shapes(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -251,9 +251,14 @@ sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, voi
  *     relations two-coloured along the components, X = (1/m) sum_nu prod_k C_k(+-nu)
  *     (C_k the DFT of relation k's row), evaluated modulo 31-bit primes c 2^22 + 1
  *     and recombined by the Chinese remainder theorem, with enough primes that their
- *     product exceeds 8 prod_k ||c_k||_1 >= 8 |X| (exact).  Other queries and widths,
- *     and bounds beyond 9 primes, are estimated as with SK_ESTIMATOR_NTT.  In the
- *     result, max_limbs is the number of primes and limb_bits 0.
+ *     product exceeds 8 prod_k ||c_k||_1 >= 8 |X| (exact: correlation, Hadamard
+ *     product and sum are all submultiplicative in the l1 norm).  Other queries (a
+ *     component of three or more attributes, Figure 3) and widths run Algorithm 3's
+ *     correlation steps modulo the same primes (one transform per operand, no limbs;
+ *     widths that are not powers of two zero-padded to a power of two >= 2m - 1 and
+ *     folded back) and recombine the row sums by CRT; only bounds beyond 9 primes
+ *     are estimated as with SK_ESTIMATOR_NTT.  In the result, max_limbs is the
+ *     number of primes and limb_bits 0.
  * The environment variable SK_ESTIMATOR=ntt (or =fused) selects that arithmetic for
  * sets created after it is set.  Errors: SK_ERR_INVALID_ARG. */
 enum { SK_ESTIMATOR_FFT64 = 0, SK_ESTIMATOR_NTT = 1, SK_ESTIMATOR_FUSED = 2 };

@@ -945,6 +945,12 @@ cudaError_t ensure(Scratch& s, size_t bytes, cudaStream_t st) {
     if (_e != cudaSuccess) return set_status_from_cuda(_e); \
   } while (0)
 
+#define SK_CK_ST(x)                \
+  do {                             \
+    const sk_status _s = (x);      \
+    if (_s != SK_OK) return _s;    \
+  } while (0)
+
 // Forward (inv = false) or inverse (unnormalised) transform of `batch` vectors of
 // length m held in src; the result is written to dst, src is clobbered.  Complex FP64
 // with the W table (conjugated for the inverse), or GF(q) with the w^t / w^-t table.
@@ -1222,15 +1228,17 @@ __global__ void k_fu_twiddle(uint32_t* tw, uint32_t* itw, int64_t n, uint32_t w,
 }
 
 // Partial l1 norms: vector v (= blockIdx.x / nch) is base[v / per] + (v % per) m; block
-// (v, ch) writes part[v * nch + ch] = sum |c[j]| over the ch-th of nch equal chunks (nch
-// divides m). The host adds a vector's partials in order (double; it adds a safety margin).
+// (v, ch) writes part[v * nch + ch] = sum |c[j]| over the ch-th of nch chunks of
+// ceil(m / nch) elements (the last one shorter).  The host adds a vector's partials in
+// order (double; it adds a safety margin).
 __global__ void __launch_bounds__(256) k_fu_l1(const int64_t* const* base, int per, int64_t m, int nch,
                                                double* part) {
   __shared__ double red[256];
-  const int64_t v = blockIdx.x / nch, ch = blockIdx.x % nch, len = m / nch;
-  const int64_t* c = base[v / per] + (v % per) * m + ch * len;
+  const int64_t v = blockIdx.x / nch, ch = blockIdx.x % nch, len = (m + nch - 1) / nch;
+  const int64_t j0 = ch * len, j1 = j0 + len < m ? j0 + len : m;
+  const int64_t* c = base[v / per] + (v % per) * m;
   double s = 0.0;
-  for (int64_t j = threadIdx.x; j < len; j += blockDim.x) s += fabs((double)__ldg(c + j));
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) s += fabs((double)__ldg(c + j));
   red[threadIdx.x] = s;
   __syncthreads();
   for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
@@ -1318,7 +1326,7 @@ __global__ void k_fu_final(const uint32_t* part, int d, int nchunk, uint32_t min
 // host: Montgomery form of v (< p)
 uint32_t fu_to_mont(uint64_t v, uint32_t p) { return (uint32_t)(((unsigned __int128)v << 32) % p); }
 
-// One prime's pass: twiddles (when missing), load, forward transform, product-sum.
+// One prime's pass (twiddles already in place): load, forward transform, product-sum.
 template <int PI>
 sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, uint32_t* W, uint32_t* part,
                         int nchunk, uint32_t* res, int np, unsigned long long negmask, cudaStream_t st) {
@@ -1326,13 +1334,6 @@ sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, ui
   uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
   const uint64_t p = fp.p;
   const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
-  const uint64_t winv = fu_powmod(w, p - 2, p);
-  if (s->fu_np <= PI) {
-    k_fu_twiddle<PI><<<grid_for(M / 2), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p), fu_to_mont(winv, fp.p),
-                                                        fu_to_mont(1, fp.p));
-    count_launch();
-    SK_CK(cudaGetLastError());
-  }
   const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
   k_fu_load<PI><<<grid_for((int64_t)r * d * M), 256, 0, st>>>(s->d_fu_rel, r, d, M, fp.r2, fp.r3, V);
   count_launch();
@@ -1461,33 +1462,38 @@ cudaError_t fu_constants(bool* ready) {
   return cudaSuccess;
 }
 
-// The fused estimate; *done false when it does not apply (the caller then estimates
-// step by step).
-sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
-  *done = false;
+// Scratch, bound and primes shared by both fused forms.  The row estimate of Algorithm 3 is
+// built from the counters by correlations, Hadamard products and one sum, each of which
+// satisfies ||f(a, x)||_1 <= ||a||_1 ||x||_1, so |X_row| <= prod_k ||c_k[row]||_1.  np is
+// the number of CRT primes whose product exceeds 8 times the largest such bound (0 when
+// nine primes do not reach it); the twiddle tables are kept for transform length M.
+struct FuSetup {
+  uint32_t* d_res = nullptr;    // [d][kFuMaxPrimes] residues of the row estimates
+  uint32_t* d_part = nullptr;   // [d][nchunk] partial sums
+  int nchunk = 1;
+  int np = 0;
+};
+
+sk_status fu_setup(sk_set* s, int64_t M, cudaStream_t st, FuSetup* f) {
   const int64_t m = s->m;
   const int r = s->r, d = s->d;
-  unsigned long long negmask = 0;
-  if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
   const std::vector<FuPrime>& pr = fu_primes();
-  bool ready = false;
-  SK_CK(fu_constants(&ready));
-  if (!ready) return SK_OK;
   if (!s->d_fu_rel) {
     SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
     SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
   }
-  // scratch: l1 [r][d] doubles | residues [d][9] | partials [d][nchunk] | V, W [r][d][m] words
+  // scratch: l1 partials [r][d][l1ch] doubles | residues [d][9] | partials [d][nchunk]
   int nchunk = 1;
-  while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
+  while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
   const int l1ch = fu_l1_chunks((int64_t)r * d, m);
   const size_t l1_bytes = ((size_t)r * d * l1ch * 8 + 255) & ~(size_t)255;
   const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
   const size_t part_bytes = ((size_t)d * nchunk * 4 + 255) & ~(size_t)255;
   SK_CK(ensure(s->scratch, l1_bytes + res_bytes + part_bytes, st));
   double* d_l1 = (double*)s->scratch.ptr;
-  uint32_t* d_res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
-  uint32_t* d_part = (uint32_t*)((char*)d_res + res_bytes);
+  f->d_res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
+  f->d_part = (uint32_t*)((char*)f->d_res + res_bytes);
+  f->nchunk = nchunk;
   std::vector<double> l1;
   const sk_status ls = fu_l1_norms(s->d_fu_rel, d, (int64_t)r * d, m, d_l1, l1ch, l1, st);
   if (ls != SK_OK) return ls;
@@ -1505,50 +1511,264 @@ sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool*
   int np = 0;
   double cover = 0.0;
   while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
-  if (cover < bits + 3.0) return SK_OK;   // beyond 9 primes: the stepwise estimate handles it
-  const size_t words = (size_t)r * d * m;
-  SK_CK(ensure(s->fft_scratch, 2 * words * sizeof(uint32_t), st));
-  uint32_t* V = (uint32_t*)s->fft_scratch.ptr;
-  uint32_t* Wb = V + words;
-  if (s->fu_m != m || !s->d_fu_tw) {
+  f->np = cover < bits + 3.0 ? 0 : np;
+  if (f->np && (s->fu_m != M || !s->d_fu_tw)) {
     if (s->d_fu_tw) cudaFree(s->d_fu_tw);
     s->d_fu_tw = nullptr;
     s->fu_np = 0;
-    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * m * sizeof(uint32_t)));
-    s->fu_m = m;
+    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * M * sizeof(uint32_t)));
+    s->fu_m = M;
   }
-  for (int i = 0; i < np; i++) {
-    sk_status ps;
-    switch (i) {
-      case 0: ps = fu_prime_pass<0>(s, pr[0], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 1: ps = fu_prime_pass<1>(s, pr[1], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 2: ps = fu_prime_pass<2>(s, pr[2], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 3: ps = fu_prime_pass<3>(s, pr[3], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 4: ps = fu_prime_pass<4>(s, pr[4], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 5: ps = fu_prime_pass<5>(s, pr[5], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 6: ps = fu_prime_pass<6>(s, pr[6], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      case 7: ps = fu_prime_pass<7>(s, pr[7], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-      default: ps = fu_prime_pass<8>(s, pr[8], m, V, Wb, d_part, nchunk, d_res, kFuMaxPrimes, negmask, st); break;
-    }
-    if (ps != SK_OK) return ps;
-  }
-  s->fu_np = std::max(s->fu_np, np);
+  return SK_OK;
+}
+
+// Reads the residues back, reconstructs each row by CRT and fills *out.
+sk_status fu_finish(sk_set* s, const FuSetup& f, sk_estimate* out, cudaStream_t st) {
+  const int d = s->d;
+  const std::vector<FuPrime>& pr = fu_primes();
+  s->fu_np = std::max(s->fu_np, f.np);
   std::vector<uint32_t> res((size_t)d * kFuMaxPrimes);
-  SK_CK(cudaMemcpyAsync(res.data(), d_res, res.size() * 4, cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(res.data(), f.d_res, res.size() * 4, cudaMemcpyDeviceToHost, st));
   SK_CK(cudaStreamSynchronize(st));
   I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
   for (int row = 0; row < d; row++)
-    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, np, pr, &rows[row])) return SK_ERR_OVERFLOW;
+    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, f.np, pr, &rows[row])) return SK_ERR_OVERFLOW;
   std::memcpy(sorted, rows, sizeof(I256) * d);
   std::sort(sorted, sorted + d, [](const I256& a, const I256& b) { return i256_lt(a, b); });
   fill_estimate(out, rows, sorted, d);
   out->max_residual = 0.0;
-  out->max_limbs = np;      // CRT primes
+  out->max_limbs = f.np;      // CRT primes
   out->limb_bits = 0;
   out->corr_steps = s->corr_steps;
   out->retries = 0;
+  return SK_OK;
+}
+
+// Twiddles of prime PI for length M (once per set and length).
+template <int PI>
+sk_status fu_twiddles(sk_set* s, const FuPrime& fp, int64_t M, cudaStream_t st) {
+  if (s->fu_np > PI) return SK_OK;
+  const uint64_t p = fp.p;
+  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
+  const uint64_t winv = fu_powmod(w, p - 2, p);
+  uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
+  k_fu_twiddle<PI><<<grid_for(M / 2), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p), fu_to_mont(winv, fp.p),
+                                                      fu_to_mont(1, fp.p));
+  count_launch();
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+// The fused estimate for queries whose components all join two attributes and a
+// power-of-two width: one product of spectra per prime.  *done false when it does not
+// apply.
+sk_status run_estimate_pairwise(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
+  *done = false;
+  const int64_t m = s->m;
+  unsigned long long negmask = 0;
+  if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
+  FuSetup f;
+  SK_CK_ST(fu_setup(s, m, st, &f));
+  if (!f.np) return SK_OK;   // beyond nine primes: the GF(q) steps handle it
+  const std::vector<FuPrime>& pr = fu_primes();
+  const size_t words = (size_t)s->r * s->d * m;
+  SK_CK(ensure(s->fft_scratch, 2 * words * sizeof(uint32_t), st));
+  uint32_t* V = (uint32_t*)s->fft_scratch.ptr;
+  uint32_t* Wb = V + words;
+  for (int i = 0; i < f.np; i++) {
+    sk_status ps;
+    switch (i) {
+#define SK_FU_CASE(I)                                                                                      \
+  case I:                                                                                                  \
+    ps = fu_twiddles<I>(s, pr[I], m, st);                                                                  \
+    if (ps == SK_OK)                                                                                       \
+      ps = fu_prime_pass<I>(s, pr[I], m, V, Wb, f.d_part, f.nchunk, f.d_res, kFuMaxPrimes, negmask, st);   \
+    break;
+      SK_FU_CASE(0) SK_FU_CASE(1) SK_FU_CASE(2) SK_FU_CASE(3) SK_FU_CASE(4) SK_FU_CASE(5) SK_FU_CASE(6)
+      SK_FU_CASE(7) default: SK_FU_CASE(8)
+#undef SK_FU_CASE
+    }
+    if (ps != SK_OK) return ps;
+  }
+  SK_CK_ST(fu_finish(s, f, out, st));
   *done = true;
   return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 step by step modulo each CRT prime, for every query shape (components of
+// three or more attributes, Figure 3) and every width.  The schedule is the one the
+// stepwise estimate runs; the row estimate is a polynomial in the counters, so running it
+// in Z/p for each prime and reconstructing by CRT (np from the l1 bound above) gives it
+// exactly, with one transform per operand of a correlation and no limbs.  Slots hold d
+// rows of M residues (Montgomery form), zero beyond m.
+// ---------------------------------------------------------------------------
+template <int PI>
+__global__ void k_crt_leaf(const int64_t* __restrict__ c, int d, int64_t m, int64_t M, uint32_t r2, uint32_t r3,
+                           uint32_t* __restrict__ out) {
+  using O = MontOps<PI>;
+  const uint32_t p = c_fu_p[PI];
+  const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / M, j = g - row * M;
+    uint32_t v = 0;
+    if (j < m) {
+      const int64_t x = c[row * m + j];
+      const uint64_t mag = x < 0 ? 0ull - (uint64_t)x : (uint64_t)x;
+      uint32_t h = (uint32_t)(mag >> 32);
+      if (h >= p) h -= p;
+      v = O::add(O::mul(h, r3), O::mul((uint32_t)mag, r2));
+      if (x < 0) v = O::neg(v);
+    }
+    out[g] = v;
+  }
+}
+
+template <int PI>
+__global__ void k_crt_had(uint32_t* __restrict__ x, const uint32_t* __restrict__ y, int64_t n) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += step)
+    x[g] = MontOps<PI>::mul(x[g], y[g]);
+}
+
+// X[row][k] <- A[row][-k mod M] X[row][k] / M: the spectrum of z = a (star) x, since
+// sum_j z_j w^jk = sum_i a_i w^-ik sum_t x_t w^tk (Definition 3.1, t = i + j mod M)
+template <int PI>
+__global__ void k_crt_product(const uint32_t* __restrict__ A, uint32_t* __restrict__ X, int d, int64_t M,
+                              uint32_t minv) {
+  using O = MontOps<PI>;
+  const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / M, k = g - row * M;
+    X[g] = O::mul(O::mul(A[row * M + ((M - k) & (M - 1))], X[g]), minv);
+  }
+}
+
+// x[row][j] = L[row][j] + L[row][j - m mod M] for j < m, 0 beyond: the circular correlation
+// mod m from the length-M one of the zero-padded rows (M >= 2m - 1)
+template <int PI>
+__global__ void k_crt_fold(const uint32_t* __restrict__ L, uint32_t* __restrict__ x, int d, int64_t m, int64_t M) {
+  const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int64_t row = g / M, j = g - row * M;
+    x[g] = j < m ? MontOps<PI>::add(L[g], L[row * M + M - m + j]) : 0u;
+  }
+}
+
+// part[row * nchunk + c] = sum of the c-th chunk of row `row` (mod p)
+template <int PI>
+__global__ void __launch_bounds__(256) k_crt_rowsum(const uint32_t* __restrict__ x, int64_t M, int nchunk,
+                                                    uint32_t* part) {
+  using O = MontOps<PI>;
+  __shared__ uint32_t red[256];
+  const int row = blockIdx.x / nchunk, c = blockIdx.x % nchunk;
+  const int64_t clen = M / nchunk;
+  const uint32_t* v = x + (int64_t)row * M + (int64_t)c * clen;
+  uint32_t s = 0;
+  for (int64_t j = threadIdx.x; j < clen; j += blockDim.x) s = O::add(s, v[j]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = O::add(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// One prime's run of the schedule; the row sums' residues go to f.d_res[row][PI].
+template <int PI>
+sk_status crt_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* slots, uint32_t* T1, uint32_t* T2,
+                         const FuSetup& f, cudaStream_t st) {
+  using O = MontOps<PI>;
+  const int d = s->d;
+  const int64_t m = s->m, dM = (int64_t)d * M;
+  const uint64_t p = fp.p;
+  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);
+  const uint64_t winv = fu_powmod(w, p - 2, p);
+  const uint32_t one = fu_to_mont(1, fp.p);
+  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : one;
+  const uint32_t r4i = M >= 4 ? fu_to_mont(fu_powmod(winv, (uint64_t)M / 4, p), fp.p) : one;
+  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
+  const uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
+  auto slot = [&](int i) { return slots + (size_t)i * dM; };
+  const int eg = grid_for(dM);
+  for (const EstOp& op : s->plan) {
+    if (op.kind == OP_LEAF) {
+      k_crt_leaf<PI><<<eg, 256, 0, st>>>(s->rel_ctr[op.rel], d, m, M, fp.r2, fp.r3, slot(op.dst));
+      count_launch();
+    } else if (op.kind == OP_HAD) {
+      k_crt_had<PI><<<eg, 256, 0, st>>>(slot(op.dst), slot(op.src), dM);
+      count_launch();
+    } else if (op.kind == OP_CORR) {
+      // src (a) is not read after its correlation, so its slot may be clobbered
+      sk_status e = xform<O>(slot(op.src), T1, d, M, tw, false, r4, st);
+      if (e == SK_OK) e = xform<O>(slot(op.dst), T2, d, M, tw, false, r4, st);
+      if (e != SK_OK) return e;
+      k_crt_product<PI><<<eg, 256, 0, st>>>(T1, T2, d, M, minv);
+      count_launch();
+      SK_CK(cudaGetLastError());
+      if (M == m) {
+        e = xform<O>(T2, slot(op.dst), d, M, tw + M / 2, true, r4i, st);
+        if (e != SK_OK) return e;
+      } else {
+        e = xform<O>(T2, T1, d, M, tw + M / 2, true, r4i, st);
+        if (e != SK_OK) return e;
+        k_crt_fold<PI><<<eg, 256, 0, st>>>(T1, slot(op.dst), d, m, M);
+        count_launch();
+      }
+    } else {   // OP_SUM
+      k_crt_rowsum<PI><<<d * f.nchunk, 256, 0, st>>>(slot(op.dst), M, f.nchunk, f.d_part);
+      k_fu_final<PI><<<(d + 63) / 64, 64, 0, st>>>(f.d_part, d, f.nchunk, one, f.d_res, kFuMaxPrimes);
+      count_launch(2);
+    }
+    SK_CK(cudaGetLastError());
+  }
+  return SK_OK;
+}
+
+// The stepwise CRT estimate; *done false when nine primes do not cover the bound.
+sk_status run_estimate_crt(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
+  *done = false;
+  const int64_t m = s->m;
+  const int64_t M = (m & (m - 1)) == 0 ? m : (int64_t)1 << ilog2(2 * m - 1);
+  if (M < 2 || M > (1ll << 22) || s->n_slots + 1 > 64) return SK_OK;
+  FuSetup f;
+  SK_CK_ST(fu_setup(s, M, st, &f));
+  if (!f.np) return SK_OK;
+  const std::vector<FuPrime>& pr = fu_primes();
+  const size_t dM = (size_t)s->d * M;
+  SK_CK(ensure(s->fft_scratch, (size_t)(s->n_slots + 2) * dM * sizeof(uint32_t), st));
+  uint32_t* slots = (uint32_t*)s->fft_scratch.ptr;
+  uint32_t* T1 = slots + (size_t)s->n_slots * dM;
+  uint32_t* T2 = T1 + dM;
+  for (int i = 0; i < f.np; i++) {
+    sk_status ps;
+    switch (i) {
+#define SK_CRT_CASE(I)                                                   \
+  case I:                                                                \
+    ps = fu_twiddles<I>(s, pr[I], M, st);                                \
+    if (ps == SK_OK) ps = crt_prime_pass<I>(s, pr[I], M, slots, T1, T2, f, st); \
+    break;
+      SK_CRT_CASE(0) SK_CRT_CASE(1) SK_CRT_CASE(2) SK_CRT_CASE(3) SK_CRT_CASE(4) SK_CRT_CASE(5) SK_CRT_CASE(6)
+      SK_CRT_CASE(7) default: SK_CRT_CASE(8)
+#undef SK_CRT_CASE
+    }
+    if (ps != SK_OK) return ps;
+  }
+  SK_CK_ST(fu_finish(s, f, out, st));
+  *done = true;
+  return SK_OK;
+}
+
+// The fused estimate: the product of spectra where it applies, else the schedule modulo
+// the CRT primes; *done false when neither applies (the caller then runs the GF(q) steps).
+sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
+  *done = false;
+  bool ready = false;
+  SK_CK(fu_constants(&ready));
+  if (!ready) return SK_OK;
+  SK_CK_ST(run_estimate_pairwise(s, out, st, done));
+  if (*done) return SK_OK;
+  return run_estimate_crt(s, out, st, done);
 }
 
 // Algorithm 3 over the schedule.  One host round trip per correlation step: before a

@@ -1,7 +1,7 @@
 """The fused estimator (SK_ESTIMATOR_FUSED): for queries whose components all join two
-attributes, X = (1/m) sum_nu prod_k C_k(+-nu) modulo CRT primes.  Rows must equal the
-oracle's exact Algorithm 3 rows; other queries and widths fall back to the stepwise
-GF(q) estimate, also exact."""
+attributes and power-of-two widths, X = (1/m) sum_nu prod_k C_k(+-nu) modulo CRT primes;
+for other query shapes and widths, Algorithm 3's schedule modulo the same primes.  Rows
+must equal the oracle's exact Algorithm 3 rows."""
 import random
 
 import numpy as np
@@ -72,20 +72,80 @@ def test_many_primes_for_large_weights():
     assert max(abs(v) for v in e["rows"]) > (1 << 64)
 
 
-def test_fallbacks_are_exact():
+def test_schedule_modulo_primes_for_other_shapes_and_widths():
     """Components of three attributes (Figure 3's {0, 1, 3}) and widths that are not powers
-    of two take the stepwise GF(q) estimate."""
+    of two run Algorithm 3's schedule modulo the CRT primes (no limbs)."""
     rng = random.Random(4)
     attrs, edges = synth.fig3_query()
     rels = random_relations(rng, attrs, 1500, 64)
     e = _estimate(attrs, edges, 128, 5, 3, rels, "fused")
-    assert e["limb_bits"] > 0
+    assert e["limb_bits"] == 0 and e["max_limbs"] >= 1
     assert e["rows"] == _oracle_rows(attrs, edges, 128, 5, 3, rels)
     w = synth.chain3()
     rels = [(r.cols.numpy(), None) for r in w.relations]
     e = _estimate(w.num_join_attrs, w.edges, 1000, 5, 42, rels, "fused")
-    assert e["limb_bits"] > 0
+    assert e["limb_bits"] == 0
     assert e["rows"] == _oracle_rows(w.num_join_attrs, w.edges, 1000, 5, 42, rels)
+
+
+@pytest.mark.parametrize("m", [2, 3, 12, 64, 777, 1000, 1024, 3000, 1 << 13, 1 << 14])
+def test_shared_attribute_queries_exact(m):
+    """Random tree queries where a relation's attribute often joins several others (so
+    components span three or more relations), signed weights, over small and wide key
+    domains: the schedule modulo the primes gives the oracle's rows."""
+    rng = random.Random(700 + m)
+    for trial in range(4 if m <= 1024 else 2):
+        attrs, edges = random_tree_query(rng, rng.randint(3, 6), share_prob=0.7)
+        rels = random_relations(rng, attrs, 600 if m <= 1024 else 1500, 1 << rng.choice([3, 10, 40]))
+        d = rng.choice([1, 2, 5])
+        seed = rng.randrange(1 << 60)
+        e = _estimate(attrs, edges, m, d, seed, rels, "fused")
+        assert e["limb_bits"] == 0, (m, trial)
+        assert e["rows"] == _oracle_rows(attrs, edges, m, d, seed, rels), (m, trial, attrs, edges)
+
+
+def test_shared_attribute_query_large_weights():
+    """Figure 3's query with weights up to 2^30 in magnitude: most of the nine primes."""
+    rng = random.Random(19)
+    attrs, edges = synth.fig3_query()
+    rels = []
+    for a in attrs:
+        n = 200
+        cols = np.array([[rng.randrange(30) for _ in range(n)] for _ in range(a)], dtype=np.int64)
+        w = np.array([rng.choice([-1, 1]) * rng.randrange(1, 1 << 30) for _ in range(n)], dtype=np.int64)
+        rels.append((cols, w))
+    for m in (256, 300):
+        e = _estimate(attrs, edges, m, 3, 8, rels, "fused")
+        assert e["limb_bits"] == 0 and e["max_limbs"] >= 5
+        assert e["rows"] == _oracle_rows(attrs, edges, m, 3, 8, rels)
+
+
+def test_width_one_million_fused():
+    """m = 10^6 (Section 4.4's width): R1 with one tuple makes each row one output of the
+    circular correlation of R3's and R2's sketches, which the oracle computes directly."""
+    attrs, edges = [1, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0)]
+    n = 300_000
+    r2 = torch.stack([synth.zipf_keys(n, 1.2, 1 << 20, 3), synth.zipf_keys(n, 1.2, 1 << 20, 4)])
+    r3 = synth.zipf_keys(n, 1.2, 1 << 20, 5)[None, :].contiguous()
+    m, d = 1_000_000, 3
+    s = pkg.SketchSet(attrs, edges, m, d, 91)
+    s.set_estimator("fused")
+    s.update(0, torch.tensor([[777]], dtype=torch.int64, device="cuda"))
+    s.update(1, r2.cuda())
+    s.update(2, r3.cuda())
+    est = s.estimate()
+    assert est["limb_bits"] == 0
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(91, d, q.n_comp, len(q.edges))
+    c2 = O.sketch_relation(q, co, 1, r2.numpy(), None, m, threads=16)
+    c3 = O.sketch_relation(q, co, 2, r3.numpy(), None, m, threads=16)
+    bins, signs = O.tuple_hash(q, co, 0, [777], m)
+    for row in range(d):
+        z = O.correlate(c3[row].tolist(), c2[row].tolist(), threads=16, bins=[int(bins[row])])[0]
+        assert est["rows"][row] == int(signs[row]) * z
+    s.set_estimator("ntt")
+    assert s.estimate()["rows"] == est["rows"]
+    s.close()
 
 
 def test_star_and_chain8_full_size_match_fft64():
