@@ -1227,47 +1227,91 @@ __global__ void k_fu_twiddle(uint32_t* tw, uint32_t* itw, int64_t n, uint32_t w,
   }
 }
 
-// Partial l1 norms: vector v (= blockIdx.x / nch) is base[v / per] + (v % per) m; block
-// (v, ch) writes part[v * nch + ch] = sum |c[j]| over the ch-th of nch chunks of
-// ceil(m / nch) elements (the last one shorter).  The host adds a vector's partials in
-// order (double; it adds a safety margin).
-__global__ void __launch_bounds__(256) k_fu_l1(const int64_t* const* base, int per, int64_t m, int nch,
-                                               double* part) {
-  __shared__ double red[256];
+// Partial norms: vector v (= blockIdx.x / nch) is base[v / per] + (v % per) m; block
+// (v, ch) writes part[2 (v nch + ch)] = sum |c[j]| and part[2 (v nch + ch) + 1] = sum c[j]^2
+// over the ch-th of nch chunks of ceil(m / nch) elements (the last one shorter).  The
+// host adds a vector's partials in order (double; the bounds carry a safety margin).
+__global__ void __launch_bounds__(256) k_fu_norms(const int64_t* const* base, int per, int64_t m, int nch,
+                                                  double* part) {
+  __shared__ double red1[256], red2[256];
   const int64_t v = blockIdx.x / nch, ch = blockIdx.x % nch, len = (m + nch - 1) / nch;
   const int64_t j0 = ch * len, j1 = j0 + len < m ? j0 + len : m;
   const int64_t* c = base[v / per] + (v % per) * m;
-  double s = 0.0;
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) s += fabs((double)__ldg(c + j));
-  red[threadIdx.x] = s;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const double x = (double)__ldg(c + j);
+    s1 += fabs(x);
+    s2 += x * x;
+  }
+  red1[threadIdx.x] = s1;
+  red2[threadIdx.x] = s2;
   __syncthreads();
   for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    if ((int)threadIdx.x < h) {
+      red1[threadIdx.x] += red1[threadIdx.x + h];
+      red2[threadIdx.x] += red2[threadIdx.x + h];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) {
+    part[2 * (int64_t)blockIdx.x] = red1[0];
+    part[2 * (int64_t)blockIdx.x + 1] = red2[0];
+  }
 }
 
-// chunks per vector for k_fu_l1: at least 2048 elements each, about four waves of blocks
+// chunks per vector for k_fu_norms: at least 2048 elements each, about four waves of blocks
 int fu_l1_chunks(int64_t nvec, int64_t m) {
   int nch = 1;
   while (m / (nch * 2) >= 2048 && nvec * nch < 4 * (int64_t)num_sms()) nch *= 2;
   return nch;
 }
 
-// Launches k_fu_l1 and reads the nvec norms back (synchronises st).
-sk_status fu_l1_norms(const int64_t* const* base, int per, int64_t nvec, int64_t m, double* d_part, int nch,
-                      std::vector<double>& l1, cudaStream_t st) {
-  k_fu_l1<<<(unsigned)(nvec * nch), 256, 0, st>>>(base, per, m, nch, d_part);
+// Launches k_fu_norms and reads the nvec l1 and l2 norms back (synchronises st).  d_part
+// holds 2 nvec nch doubles.
+sk_status fu_norms(const int64_t* const* base, int per, int64_t nvec, int64_t m, double* d_part, int nch,
+                   std::vector<double>& l1, std::vector<double>& l2, cudaStream_t st) {
+  k_fu_norms<<<(unsigned)(nvec * nch), 256, 0, st>>>(base, per, m, nch, d_part);
   count_launch();
   SK_CK(cudaGetLastError());
-  std::vector<double> part((size_t)nvec * nch);
+  std::vector<double> part((size_t)2 * nvec * nch);
   SK_CK(cudaMemcpyAsync(part.data(), d_part, part.size() * 8, cudaMemcpyDeviceToHost, st));
   SK_CK(cudaStreamSynchronize(st));
   l1.assign((size_t)nvec, 0.0);
-  for (int64_t v = 0; v < nvec; v++)
-    for (int c = 0; c < nch; c++) l1[v] += part[(size_t)v * nch + c];
+  l2.assign((size_t)nvec, 0.0);
+  for (int64_t v = 0; v < nvec; v++) {
+    double sq = 0.0;
+    for (int c = 0; c < nch; c++) {
+      l1[v] += part[2 * ((size_t)v * nch + c)];
+      sq += part[2 * ((size_t)v * nch + c) + 1];
+    }
+    l2[v] = std::sqrt(sq);
+  }
   return SK_OK;
+}
+
+// log2 of an upper bound on |X_row| from the norms of the row's r relation vectors
+// (l1[k * stride], l2[k * stride]); -1 when one of them is zero (then X_row = 0).  Any
+// schedule: prod_k ||c_k||_1 (correlation, Hadamard product and sum are submultiplicative
+// in the l1 norm).  Pairwise product of spectra, X = (1/m) sum_nu prod_k C_k(+-nu): with
+// |C_k| <= ||c_k||_1 for all but two relations a, b, Cauchy-Schwarz and Parseval
+// (sum_nu |C|^2 = m ||c||_2^2) give ||c_a||_2 ||c_b||_2 prod_{k != a, b} ||c_k||_1; a and b
+// are the two relations with the largest l1 / l2 ratio.  Each factor carries a relative
+// margin of 1e-9 for the rounding of the double sums.
+double fu_row_bits(const double* l1, const double* l2, int r, int64_t stride, bool pairwise) {
+  double b = 0.0, best1 = 0.0, best2 = 0.0;
+  for (int k = 0; k < r; k++) {
+    const double v1 = l1[k * stride], v2 = l2[k * stride];
+    if (v1 <= 0.0) return -1.0;
+    b += std::log2(v1 * (1.0 + 1e-9));
+    const double save = std::log2(v1 * (1.0 + 1e-9)) - std::log2(v2 * (1.0 + 1e-9));
+    if (save > best1) {
+      best2 = best1;
+      best1 = save;
+    } else if (save > best2) {
+      best2 = save;
+    }
+  }
+  return pairwise && r >= 2 ? b - best1 - best2 : b;
 }
 
 // out[(k d + row) m + j] = c_k[row][j] mod p, Montgomery form (|c| = h 2^32 + l)
@@ -1474,7 +1518,7 @@ struct FuSetup {
   int np = 0;
 };
 
-sk_status fu_setup(sk_set* s, int64_t M, cudaStream_t st, FuSetup* f) {
+sk_status fu_setup(sk_set* s, int64_t M, bool pairwise, cudaStream_t st, FuSetup* f) {
   const int64_t m = s->m;
   const int r = s->r, d = s->d;
   const std::vector<FuPrime>& pr = fu_primes();
@@ -1482,11 +1526,11 @@ sk_status fu_setup(sk_set* s, int64_t M, cudaStream_t st, FuSetup* f) {
     SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
     SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
   }
-  // scratch: l1 partials [r][d][l1ch] doubles | residues [d][9] | partials [d][nchunk]
+  // scratch: norm partials [r][d][l1ch][2] doubles | residues [d][9] | partials [d][nchunk]
   int nchunk = 1;
   while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
   const int l1ch = fu_l1_chunks((int64_t)r * d, m);
-  const size_t l1_bytes = ((size_t)r * d * l1ch * 8 + 255) & ~(size_t)255;
+  const size_t l1_bytes = ((size_t)r * d * l1ch * 16 + 255) & ~(size_t)255;
   const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
   const size_t part_bytes = ((size_t)d * nchunk * 4 + 255) & ~(size_t)255;
   SK_CK(ensure(s->scratch, l1_bytes + res_bytes + part_bytes, st));
@@ -1494,20 +1538,11 @@ sk_status fu_setup(sk_set* s, int64_t M, cudaStream_t st, FuSetup* f) {
   f->d_res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
   f->d_part = (uint32_t*)((char*)f->d_res + res_bytes);
   f->nchunk = nchunk;
-  std::vector<double> l1;
-  const sk_status ls = fu_l1_norms(s->d_fu_rel, d, (int64_t)r * d, m, d_l1, l1ch, l1, st);
+  std::vector<double> l1, l2;
+  const sk_status ls = fu_norms(s->d_fu_rel, d, (int64_t)r * d, m, d_l1, l1ch, l1, l2, st);
   if (ls != SK_OK) return ls;
-  double bits = 0.0;   // log2 of the largest row bound prod_k ||c_k||_1
-  for (int row = 0; row < d; row++) {
-    double b = 0.0;
-    bool zero = false;
-    for (int k = 0; k < r; k++) {
-      const double v = l1[(size_t)k * d + row];
-      if (v <= 0.0) zero = true;
-      else b += std::log2(v * (1.0 + 1e-9));
-    }
-    if (!zero) bits = std::max(bits, b);
-  }
+  double bits = 0.0;   // log2 of the largest row bound
+  for (int row = 0; row < d; row++) bits = std::max(bits, fu_row_bits(&l1[row], &l2[row], r, d, pairwise));
   int np = 0;
   double cover = 0.0;
   while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
@@ -1567,7 +1602,7 @@ sk_status run_estimate_pairwise(sk_set* s, sk_estimate* out, cudaStream_t st, bo
   unsigned long long negmask = 0;
   if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
   FuSetup f;
-  SK_CK_ST(fu_setup(s, m, st, &f));
+  SK_CK_ST(fu_setup(s, m, true, st, &f));
   if (!f.np) return SK_OK;   // beyond nine primes: the GF(q) steps handle it
   const std::vector<FuPrime>& pr = fu_primes();
   const size_t words = (size_t)s->r * s->d * m;
@@ -1732,7 +1767,7 @@ sk_status run_estimate_crt(sk_set* s, sk_estimate* out, cudaStream_t st, bool* d
   const int64_t M = (m & (m - 1)) == 0 ? m : (int64_t)1 << ilog2(2 * m - 1);
   if (M < 2 || M > (1ll << 22) || s->n_slots + 1 > 64) return SK_OK;
   FuSetup f;
-  SK_CK_ST(fu_setup(s, M, st, &f));
+  SK_CK_ST(fu_setup(s, M, false, st, &f));
   if (!f.np) return SK_OK;
   const std::vector<FuPrime>& pr = fu_primes();
   const size_t dM = (size_t)s->d * M;
@@ -2125,7 +2160,7 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const int l1ch = fu_l1_chunks(nvec, M);
   const size_t b_rows = al(nvec * sizeof(void*)), b_outs = al(nout * sizeof(FuOut)),
-               b_l1 = al((size_t)nvec * l1ch * 8), b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
+               b_l1 = al((size_t)nvec * l1ch * 16), b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
                b_tw = al((size_t)M * 4), b_v = al((size_t)nvec * M * 4);
   char* blk = nullptr;
   SK_CK(cudaMallocAsync((void**)&blk, b_rows + b_outs + b_l1 + b_res + b_part + b_tw + 2 * b_v, st));
@@ -2141,26 +2176,18 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   auto fail = [&](sk_status x) {
     if (status == SK_OK) status = x;
   };
-  std::vector<double> l1;
+  std::vector<double> l1, l2;
   std::vector<uint32_t> res((size_t)nout * kFuMaxPrimes);
   int np = 0;
   do {
     cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), nvec * sizeof(void*), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_outs, outs.data(), nout * sizeof(FuOut), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
-    const sk_status ls = fu_l1_norms(d_rows, 1, nvec, M, d_l1, l1ch, l1, st);
+    const sk_status ls = fu_norms(d_rows, 1, nvec, M, d_l1, l1ch, l1, l2, st);
     if (ls != SK_OK) { fail(ls); break; }
     double bits = 0.0;
-    for (const FuOut& f : outs) {
-      double b = 0.0;
-      bool zero = false;
-      for (int k = 0; k < f.r; k++) {
-        const double v = l1[f.base + (int64_t)k * f.d + f.row];
-        if (v <= 0.0) zero = true;
-        else b += std::log2(v * (1.0 + 1e-9));
-      }
-      if (!zero) bits = std::max(bits, b);
-    }
+    for (const FuOut& f : outs)
+      bits = std::max(bits, fu_row_bits(&l1[f.base + f.row], &l2[f.base + f.row], f.r, f.d, true));
     double cover = 0.0;
     while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
     if (cover < bits + 3.0) { np = 0; break; }   // left to the per-set estimates

@@ -210,3 +210,33 @@ def test_eight_relation_chain_d64():
     e = _estimate(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, rels, "fused")
     assert e["limb_bits"] == 0 and len(e["rows"]) == 64
     assert e["rows"] == _oracle_rows(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed, rels)
+
+
+@pytest.mark.parametrize("m", [64, 4096])
+def test_bound_is_tight_for_identical_relations(m):
+    """Two identical relations joined on one attribute: both sketches are the same vector c,
+    so each row is ||c||_2^2, exactly the l2 bound that sets the number of primes (weights
+    near 2^57, counters far from int64 wrap-around, several primes).  Through one estimate
+    and through sk_estimate_many."""
+    rng = np.random.default_rng(m)
+    n = 1000
+    cols = rng.integers(0, 300, size=(1, n)).astype(np.int64)
+    w = (rng.integers(1 << 55, 1 << 57, size=n) * rng.choice(np.array([-1, 1]), size=n)).astype(np.int64)
+    attrs, edges, d = [1, 1], [(0, 0, 1, 0)], 4
+    sets = []
+    for seed in (5, 6):
+        s = pkg.SketchSet(attrs, edges, m, d, seed)
+        s.set_estimator("fused")
+        for k in range(2):
+            s.update(k, torch.as_tensor(cols).cuda(), torch.as_tensor(w).cuda())
+        sets.append(s)
+    many = pkg.estimate_many(sets)
+    q = O.canonical_query(attrs, edges)
+    for s, seed, e in zip(sets, (5, 6), many):
+        one = s.estimate()
+        co = O.draw_coefficients(seed, d, q.n_comp, len(q.edges))
+        c = O.sketch_relation(q, co, 0, cols, w, m)
+        want = [sum(int(v) * int(v) for v in c[r]) for r in range(d)]
+        assert one["limb_bits"] == 0 and one["max_limbs"] >= 4
+        assert one["rows"] == want and e["rows"] == want
+        s.close()
