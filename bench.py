@@ -545,9 +545,10 @@ def run_e2e(args, s, wl, stream, world):
 def run_batched(args, world, rank):
     """256 relations (lognormal row counts 1e3..1e7, 1-4 Zipf columns, m = 2^10..2^18, d = 7,
     +-1 weights with 10% deletions): one step resets the 256 sketches and applies every
-    relation's batch, (a) one sk_sketch_update_batch launch per relation, (b) one persistent
-    sk_update_plan_run (autotuned), (c) the same captured in a CUDA graph.  The sketches of
-    (a) and (b) are compared after timing."""
+    relation's batch, (a) one sk_sketch_reset and one sk_sketch_update_batch launch per
+    relation, (b) one sk_update_plan_zero and one persistent sk_update_plan_run (autotuned),
+    (c) the same captured in a CUDA graph.  The sketches of (a) and (b) are compared after
+    timing."""
     import torch
 
     import paper_2402_15953_gb300 as pkg
@@ -568,8 +569,7 @@ def run_batched(args, world, rank):
             s.update(0, b.relation.cols, b.relation.weights)
 
     def step_b():
-        for s in sb:
-            s.reset()
+        plan.zero()     # the 256 relations' counters, one launch
         plan.run()
 
     def timeit(fn, steps):

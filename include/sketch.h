@@ -196,6 +196,11 @@ typedef struct sk_update_plan sk_update_plan;
 
 sk_status sk_update_plan_create(const sk_update_item* items, int32_t n_items, sk_update_plan** out);
 sk_status sk_update_plan_run(sk_update_plan* plan, void* cuda_stream);
+/* sk_update_plan_zero: sets to zero, in one launch on cuda_stream, the int64[d][m]
+ * counters of every (set, relation) that the plan's items write (the other relations
+ * of those sets are left as they are): the batched form of sk_sketch_reset for a plan
+ * that re-sketches its relations.  Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
+sk_status sk_update_plan_zero(sk_update_plan* plan, void* cuda_stream);
 sk_status sk_update_plan_get_config(const sk_update_plan* plan, sk_update_plan_config* out);
 sk_status sk_update_plan_set_config(sk_update_plan* plan, const sk_update_plan_config* config);
 sk_status sk_update_plan_autotune(sk_update_plan* plan, void* cuda_stream, sk_update_plan_config* best,

@@ -81,7 +81,7 @@ class sk_update_plan_config(ctypes.Structure):
 EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_sketch_merge",
            "sk_estimate_join", "sk_sync", "sk_sketch_destroy", "sk_status_string", "sk_sketch_info",
            "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
-           "sk_estimate_join_noalloc", "sk_sketch_set_estimator", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_get_config",
+           "sk_estimate_join_noalloc", "sk_sketch_set_estimator", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_zero", "sk_update_plan_get_config",
            "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy",
            "sk_family_create", "sk_family_update_batch", "sk_family_estimate", "sk_family_set_estimator",
            "sk_family_info", "sk_family_view", "sk_family_copy_sketch", "sk_family_reset", "sk_family_sync",
@@ -120,6 +120,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_sketch_reset.argtypes = [vp, vp]
     L.sk_update_plan_create.argtypes = [ctypes.POINTER(sk_update_item), i32, ctypes.POINTER(vp)]
     L.sk_update_plan_run.argtypes = [vp, vp]
+    L.sk_update_plan_zero.argtypes = [vp, vp]
     L.sk_update_plan_get_config.argtypes = [vp, ctypes.POINTER(sk_update_plan_config)]
     L.sk_update_plan_set_config.argtypes = [vp, ctypes.POINTER(sk_update_plan_config)]
     L.sk_update_plan_autotune.argtypes = [vp, vp, ctypes.POINTER(sk_update_plan_config), ctypes.POINTER(ctypes.c_double)]
@@ -260,6 +261,10 @@ def sk_update_plan_run(plan: int, stream: int) -> None:
     _check(load().sk_update_plan_run(plan, stream), "sk_update_plan_run")
 
 
+def sk_update_plan_zero(plan: int, stream: int) -> None:
+    _check(load().sk_update_plan_zero(plan, stream), "sk_update_plan_zero")
+
+
 def sk_update_plan_get_config(plan: int) -> sk_update_plan_config:
     c = sk_update_plan_config()
     _check(load().sk_update_plan_get_config(plan, ctypes.byref(c)), "sk_update_plan_get_config")
@@ -388,6 +393,10 @@ class UpdatePlan:
 
     def run(self) -> None:
         sk_update_plan_run(self.handle, self._stream())
+
+    def zero(self) -> None:
+        """Zeroes the counters of every (set, relation) the plan writes, in one launch."""
+        sk_update_plan_zero(self.handle, self._stream())
 
     def config(self) -> dict:
         return sk_update_plan_get_config(self.handle).as_dict()

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_update_views(UpdArgs p, ViewArgs v) {
         }
         const uint32_t bin = POW2 ? (b & (m32 - 1)) : b;
         const int64_t val = (__popcll(bits & v.jmask[vi]) & 1) ? -delta : delta;
-        atomicAdd(v.ctr[vi] + (int64_t)row * p.m + bin, (unsigned long long)val);
+        red_add_global(v.ctr[vi] + (int64_t)row * p.m + bin, (unsigned long long)val);
       }
     }
   }

@@ -87,6 +87,13 @@ __device__ __forceinline__ uint64_t reduce_lazy(uint64_t v) {
 
 __device__ __forceinline__ void record(int* status, int code) { atomicCAS(status, 0, code); }
 
+// counter += v as a global-memory reduction (no return value).  The pointer may come from
+// memory the compiler cannot trace to a kernel argument (the batched plan's items), where
+// atomicAdd would be issued as a generic atomic with a return value.
+__device__ __forceinline__ void red_add_global(unsigned long long* ptr, unsigned long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(ptr)), "l"(v));
+}
+
 template <bool POW2>
 __device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
   return POW2 ? (v & (m - 1)) : (v % m);
@@ -184,11 +191,11 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
       const unsigned same = __match_any_sync(0xffffffffu, key);
       const int sum = __reduce_add_sync(same, small ? (int)v : 0);
       if (small && lane == (unsigned)(__ffs(same) - 1) && sum != 0) atomicAdd(s_sub + key, sum);
-      if (!small && v != 0) atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
+      if (!small && v != 0) red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
     } else if (SMEM && small) {
       atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
     } else {
-      atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
+      red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
     }
   }
 }
@@ -284,7 +291,7 @@ template <bool SMEM>
 __device__ __forceinline__ void scatter_row(const UpdArgs& p, int* s_sub, bool small, int row, uint32_t bin,
                                             int64_t v) {
   if (SMEM && small) atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
-  else atomicAdd(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
+  else red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
 }
 
 // Key-column load for the key-table kernel: the columns are streamed once, so they are

@@ -1,10 +1,11 @@
 // Batched update: one persistent launch applies many update batches (items), each
 // an Algorithm 2 pass over one relation of one sketch set.  CTAs pull chunks of
 // tuples from a device work counter in item order; a CTA reloads an item's hash
-// coefficients into shared memory only when it moves to another item.  Items with
+// coefficients and arguments into shared memory only when it moves to another item.  Items with
 // a small d x m accumulate each chunk in an int32 shared-memory sub-sketch that is
 // flushed into the int64 counters at the end of the chunk.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -37,7 +38,7 @@ __device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, con
     __syncthreads();
     for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) {
       const int v = s_sub[j];
-      if (v != 0) atomicAdd(p.ctr + j, (unsigned long long)(int64_t)v);
+      if (v != 0) red_add_global(p.ctr + j, (unsigned long long)(int64_t)v);
     }
   } else {
     for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) update_tuple<A, POW2, false>(p, s_coef, s_sub, i);
@@ -61,6 +62,10 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_c;
   __shared__ int s_item;
+  // the current item's arguments: read in the tuple loop from shared memory rather than
+  // from the item array (global memory the counter updates could alias)
+  __shared__ UpdArgs s_args;
+  __shared__ int s_pow2, s_smem;
   uint64_t* s_coef = (uint64_t*)smem_raw;
   int* s_sub = (int*)(s_coef + coef_words);
   int cur = -1;
@@ -81,19 +86,45 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
     const int64_t c = s_c;
     if (c >= total_chunks) break;
     const int it = s_item;
-    const MultiItem& mi = items[it];
-    const UpdArgs& p = mi.args;
     if (it != cur) {
-      const int nc = p.d * p.row_len;
-      for (int j = threadIdx.x; j < nc; j += blockDim.x) s_coef[j] = p.coef[j];
+      const MultiItem& mi = items[it];
+      if (threadIdx.x == 0) {
+        s_args = mi.args;
+        s_pow2 = mi.pow2;
+        s_smem = mi.use_smem;
+      }
+      const int nc = mi.args.d * mi.args.row_len;
+      for (int j = threadIdx.x; j < nc; j += blockDim.x) s_coef[j] = mi.args.coef[j];
       cur = it;
       __syncthreads();
     }
-    const int64_t t0 = (c - mi.chunk0) * chunk;
+    const UpdArgs& p = s_args;
+    const int64_t t0 = (c - items[it].chunk0) * chunk;
     const int64_t t1 = min(p.n, t0 + chunk);
-    if (mi.pow2) multi_dispatch<true>(p, mi.use_smem != 0, s_coef, s_sub, t0, t1);
-    else multi_dispatch<false>(p, mi.use_smem != 0, s_coef, s_sub, t0, t1);
+    if (s_pow2) multi_dispatch<true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+    else multi_dispatch<false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
     __syncthreads();
+  }
+}
+
+// Zeroes the counter block of every item (d x m int64 words each; an item repeated for
+// several batches of one relation is zeroed more than once, harmlessly).  Grid row y takes
+// items y, y + gridDim.y, ...; its blocks stride over the item's words with 16-byte stores
+// (a block starting at an odd word, as a later relation's block with d m odd does, first
+// clears that word on its own).
+__global__ void k_zero_multi(const MultiItem* __restrict__ items, int n_items) {
+  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+    unsigned long long* c = items[it].args.ctr;
+    const int64_t words = (int64_t)items[it].args.d * (int64_t)items[it].args.m;
+    const int head = ((uintptr_t)c & 15u) ? 1 : 0;   // counters are 8-byte aligned
+    if (head && words > 0 && blockIdx.x == 0 && threadIdx.x == 0) c[0] = 0ull;
+    const int64_t rest = words - head;
+    ulonglong2* v = (ulonglong2*)(c + head);
+    const int64_t pairs = rest > 0 ? rest >> 1 : 0;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < pairs; j += step)
+      v[j] = make_ulonglong2(0ull, 0ull);
+    if (rest > 0 && (rest & 1) && blockIdx.x == 0 && threadIdx.x == 0) c[head + rest - 1] = 0ull;
   }
 }
 
@@ -227,6 +258,15 @@ sk_status sk_update_plan_run(sk_update_plan* pl, void* cuda_stream) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * pl->cfg.ctas_per_sm));
   k_update_multi<<<grid, pl->cfg.threads, pl->smem_bytes, st>>>(pl->d_items, pl->n_active, pl->total_chunks,
                                                                 pl->cfg.chunk_tuples, pl->coef_words, pl->d_queue);
+  count_launch();
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+sk_status sk_update_plan_zero(sk_update_plan* pl, void* cuda_stream) {
+  if (!pl) return SK_ERR_INVALID_ARG;
+  if (pl->n_active == 0) return SK_OK;
+  const dim3 grid(8, (unsigned)std::min(pl->n_active, 65535));
+  k_zero_multi<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(pl->d_items, pl->n_active);
   count_launch();
   return set_status_from_cuda(cudaGetLastError());
 }

@@ -96,3 +96,40 @@ def test_plan_argument_checks(workload):
         empty.set_config(100, 256, 4, 0)
     empty.close()
     s.close()
+
+
+def test_plan_zero_clears_only_the_planned_relations(workload):
+    """sk_update_plan_zero: the counters of every (set, relation) the plan writes become
+    zero, the set's other relations keep theirs; d m odd puts relation 1's block on an
+    8-byte (not 16-byte) boundary; a relation listed twice; a run after the zeroing equals
+    the items applied one by one to fresh sets."""
+    rng = np.random.default_rng(3)
+    attrs, edges = [1, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0)]
+    shapes = [(777, 3), (64, 5), (1000, 1), (4096, 7), (2, 1)]
+    sets, items = [], []
+    for i, (m, d) in enumerate(shapes):
+        s = pkg.SketchSet(attrs, edges, m, d, 10 + i)
+        for k, a in enumerate(attrs):
+            s.update(k, torch.as_tensor(rng.integers(0, 500, size=(a, 3000))).cuda())
+        sets.append(s)
+        c0 = torch.as_tensor(rng.integers(0, 500, size=(1, 100))).cuda()
+        c1 = torch.as_tensor(rng.integers(0, 500, size=(2, 100))).cuda()
+        items += [(s, 0, c0, None), (s, 1, c1, None), (s, 1, c1, None)]
+    torch.cuda.synchronize()
+    keep = [s.counters[2].clone() for s in sets]
+    plan = pkg.UpdatePlan(items)
+    plan.zero()
+    torch.cuda.synchronize()
+    for s, k in zip(sets, keep):
+        assert not bool(s.counters[0].any()) and not bool(s.counters[1].any())
+        assert bool(k.any()) and torch.equal(s.counters[2], k)
+    plan.run()
+    fresh = [pkg.SketchSet(attrs, edges, m, d, 10 + i) for i, (m, d) in enumerate(shapes)]
+    for j, (s, rel, cols, w) in enumerate(items):
+        fresh[j // 3].update(rel, cols, w)
+    torch.cuda.synchronize()
+    for s, f in zip(sets, fresh):
+        assert torch.equal(s.counters[:2], f.counters[:2])
+    plan.close()
+    for s in sets + fresh:
+        s.close()
