@@ -94,6 +94,16 @@ __device__ __forceinline__ void red_add_global(unsigned long long* ptr, unsigned
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(ptr)), "l"(v));
 }
 
+// Key-column load for the update kernels: the columns are streamed once, so they are
+// kept out of L1 and marked first to leave L2 (the tables and the sketch stay cached).
+__device__ __forceinline__ int64_t ld_key_stream(const int64_t* ptr) {
+  int64_t v;
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
 template <bool POW2>
 __device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
   return POW2 ? (v & (m - 1)) : (v % m);
@@ -118,7 +128,7 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
 #pragma unroll
   for (int u = 0; u < (A > 0 ? A : kMaxAttrs); u++) {
     if (A == 0 && u >= na) break;
-    const int64_t key = (!AGG || live) ? __ldg(p.cols + (int64_t)u * p.stride + i) : 0;
+    const int64_t key = (!AGG || live) ? ld_key_stream(p.cols + (int64_t)u * p.stride + i) : 0;
     if (p.has_dom && (!AGG || live) && (key < 0 || key >= p.dom[u])) ok = false;
     x[u] = field_of(key);
   }
@@ -292,16 +302,6 @@ __device__ __forceinline__ void scatter_row(const UpdArgs& p, int* s_sub, bool s
                                             int64_t v) {
   if (SMEM && small) atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
   else red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
-}
-
-// Key-column load for the key-table kernel: the columns are streamed once, so they are
-// kept out of L1 and marked first to leave L2 (the tables and the sketch stay cached).
-__device__ __forceinline__ int64_t ld_key_stream(const int64_t* ptr) {
-  int64_t v;
-  uint64_t pol;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
-  return v;
 }
 
 // Lane-wise sum of two pairs of 16-bit values (each half mod 2^16, no carry across halves):

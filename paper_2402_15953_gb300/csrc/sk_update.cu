@@ -409,6 +409,16 @@ int key_table_mode() {
   return v[0] == '0' ? 0 : (v[0] == '1' ? 1 : 2);
 }
 
+// Share of L2 for the counters one per-tuple update pass writes (SK_ROW_PASS_MB, default
+// 64 MiB, half of GB300's L2; 0 = never split the rows).  8 x 1e7 rows into 16 x 2^20
+// counters (128 MiB per relation): one pass 22.9 ms, two passes of 64 MiB 19.3 ms, three
+// of 43 MiB 23.6 ms, four of 32 MiB 27.5 ms (each pass reads the keys again).
+size_t row_pass_bytes() {
+  const char* v = std::getenv("SK_ROW_PASS_MB");
+  const long long x = v ? std::atoll(v) : 64;
+  return (size_t)(x < 0 ? 0 : x) << 20;
+}
+
 size_t key_table_max_bytes() {
   const char* v = std::getenv("SK_KEY_TABLE_MAX_MB");
   const long long x = v ? std::atoll(v) : 1024;
@@ -543,8 +553,26 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
     a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(tpc, 1);
     e = pow2 ? dispatch_a<true, true>(a, grid, smem, st) : dispatch_a<false, true>(a, grid, smem, st);
   } else {
+    // Counters in global memory.  When the relation's d x m int64 counters exceed the share
+    // of L2 given by row_pass_bytes(), the rows are split into passes over the whole batch
+    // (each pass hashes only its rows; the keys are read once per pass), so that the
+    // counter updates of a pass stay in L2.
     a.smem_wmax = 0;
-    e = pow2 ? dispatch_a<true, false>(a, 0, coef_bytes, st) : dispatch_a<false, false>(a, 0, coef_bytes, st);
+    const size_t row_bytes = (size_t)s->m * sizeof(int64_t);
+    const size_t budget = row_pass_bytes();
+    int rows = s->d;
+    if (budget > 0 && (size_t)s->d * row_bytes > budget) rows = (int)std::max<size_t>(1, budget / row_bytes);
+    const int passes = (s->d + rows - 1) / rows;
+    rows = (s->d + passes - 1) / passes;   // even split
+    e = cudaSuccess;
+    for (int r0 = 0; r0 < s->d && e == cudaSuccess; r0 += rows) {
+      UpdArgs b = a;
+      b.d = std::min(rows, s->d - r0);
+      b.coef = a.coef + (size_t)r0 * rp.coef_row_len;
+      b.ctr = a.ctr + (size_t)r0 * s->m;
+      const size_t cb = (size_t)b.d * rp.coef_row_len * sizeof(uint64_t);
+      e = pow2 ? dispatch_a<true, false>(b, 0, cb, st) : dispatch_a<false, false>(b, 0, cb, st);
+    }
   }
   return set_status_from_cuda(e);
 }
