@@ -698,6 +698,7 @@ def run_serving(args, world, rank):
         srv = SketchServer(hbm_budget_bytes=32 << 30, update_slots=16, estimate_workers=4)
         for i, (a, e, m, d, sd) in enumerate(sets):
             srv.register_set(i, a, e, m, d, sd)
+            srv.sets[i].sset.set_estimator(args.estimator)
         reqs = []
         t0 = time.perf_counter()
 
@@ -737,6 +738,8 @@ def run_serving(args, world, rank):
         each estimate after the previous request completed (no overlap, no admission)."""
         from paper_2402_15953_gb300 import SketchSet
         live = [SketchSet(a, e, m, d, sd) for (a, e, m, d, sd) in sets]
+        for x in live:
+            x.set_estimator(args.estimator)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tuples = 0
@@ -763,6 +766,7 @@ def run_serving(args, world, rank):
             "unit": "tuples/s", "n_gpus": world, "steps": args.requests, "warmup": 200,
             "ms_per_step": 1e3 / sat["requests_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "estimator": args.estimator,
             "config": {"workload": "64 live sets (chains of 2-6 relations, m = 2^14..2^18, d = 9); update batches "
                                    "log-uniform 1e3..1e6 tuples, Zipf 1.1 keys over 1e6, 5% deletions; 10 updates : "
                                    "1 estimate; Poisson arrivals; HBM budget 32 GB"},
@@ -872,6 +876,7 @@ def run_small_config(args, world, rank, which):
     pkg_build.build()
     wl = synth.chain3(device="cuda") if which == "chain3" else synth.chain(device="cuda")
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+    s.set_estimator(args.estimator)
     stream = torch.cuda.current_stream()
     reps = args.steps if which == "chain3" else max(3, args.steps // 10)
     doms = declared_domains(args, wl)
@@ -900,6 +905,7 @@ def run_small_config(args, world, rank, which):
     line = {"metric": f"{which}: update and estimate time", "value": tot / (ms / 1e3), "unit": "tuples/s",
             "n_gpus": world, "steps": reps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "estimator": args.estimator,
             "config": {"workload": which, "tuples_per_step": tot, "m": wl.m, "d": wl.d},
             "update_us": 1e3 * statistics.mean(up), "estimate_us": 1e3 * statistics.mean(es),
             "estimate_p99_us": 1e3 * percentile(es, 99.0), "estimates_per_s": 1e3 / statistics.mean(es),
@@ -933,6 +939,7 @@ def run_subqueries(args, world, rank):
     total = sum(r.n for r in wl.relations)
 
     fam = pkg.SketchFamily(wl.num_join_attrs, wl.edges, subs, wl.m, wl.d, wl.hash_seed)
+    fam.set_estimator(args.estimator)
 
     def fam_step():
         fam.reset()
@@ -949,6 +956,7 @@ def run_subqueries(args, world, rank):
         fcols = wl.relations[0].cols[sub].contiguous() if len(sub) < k else wl.relations[0].cols
         naive.append((pkg.SketchSet(attrs, edges, wl.m, wl.d, wl.hash_seed),
                       [fcols] + [wl.relations[dd].cols for dd in dims]))
+        naive[-1][0].set_estimator(args.estimator)
 
     def naive_step():
         outs = []
@@ -990,6 +998,7 @@ def run_subqueries(args, world, rank):
             "value": world * len(subs) / (fam_ms / 1e3), "unit": "sub-query estimates/s", "n_gpus": world,
             "steps": reps, "warmup": args.warmup, "ms_per_step": fam_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "estimator": args.estimator,
             "config": {"workload": f"star F(K1..K{k}) {n_fact:.0e} rows Zipf 1.1 over [0,1e6), D_i {n_dim:.0e} "
                                    f"uniform; m=65536, d=9; all {len(subs)} connected sub-queries",
                        "tuples_per_step": total},

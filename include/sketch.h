@@ -54,7 +54,8 @@ enum {
   SK_ERR_OVERFLOW = -11,          /* an exact intermediate would leave the signed 256-bit range */
   SK_ERR_INEXACT = -12,           /* an FFT correlation could not be certified exact */
   SK_ERR_NO_MEMORY = -13,         /* device allocation failed */
-  SK_ERR_SCRATCH_TOO_SMALL = -14  /* the allocation-free estimator's fixed scratch cannot hold this set */
+  SK_ERR_SCRATCH_TOO_SMALL = -14, /* the allocation-free estimator's fixed scratch cannot hold this set */
+  SK_ERR_OVER_BUDGET = -15        /* a serving request or set does not fit the server's HBM budget */
 };
 
 /* Largest number of median rows d a set may have. */
@@ -331,6 +332,59 @@ sk_status sk_sketch_info(const sk_set* set, int32_t* r, int64_t* m, int32_t* d, 
                          int32_t* n_joins);
 sk_status sk_get_coefficients(const sk_set* set, uint64_t* host_out, size_t count);
 sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t count, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving (sk_server_*): a continuous-batching request loop over live sets resident on
+ * the current device, run by native threads (a scheduler, a retire thread and one
+ * worker per estimate stream).  Every set keeps its requests in arrival order: an
+ * estimate sees exactly the updates of that set submitted before it, and later
+ * updates of the set wait until it has read the counters, so each result equals
+ * running the set's requests one by one.  Across sets the scheduler admits the
+ * oldest head request as soon as an update slot or an estimate worker is free and its
+ * memory fits the budget; updates are staged from host memory on a copy stream and
+ * run on an update stream, estimates on their worker's stream, overlapping on the
+ * device.  Charged against hbm_budget_bytes: the counters of every registered set
+ * (r * d * m * 8 bytes), the staged columns and weights of every in-flight update and
+ * an allowance per running estimate of (max(2, r) + 1) * d * m * 32 + 128 * d * m +
+ * 8 * m bytes.
+ *
+ * sk_server_create: update_slots in-flight update batches (>= 1), estimate_workers
+ *   concurrent estimates (1..64), estimate streams at the device's highest priority
+ *   when estimate_priority != 0.
+ * sk_server_register_set: makes `set` (created and owned by the caller, alive until
+ *   sk_server_destroy) a live set named set_id; SK_ERR_OVER_BUDGET when its counters
+ *   do not fit.  Sets must not be updated or estimated outside the server meanwhile.
+ * sk_server_submit_update: queues Algorithm 2 for n_rows tuples of `relation` from
+ *   host memory (int64 attribute-major columns with col_stride >= n_rows, optional
+ *   int64 weights; page-locked memory lets the copy overlap).  The host buffers must
+ *   stay valid until the request has finished.  *request_id names the request.
+ *   A request that could never fit (more memory than the budget leaves beside the
+ *   registered sets' counters) finishes at once with status SK_ERR_OVER_BUDGET, and an
+ *   update of zero rows finishes at once with SK_OK.
+ * sk_server_submit_estimate: queues Algorithm 3 and the median for set set_id.
+ * sk_server_result: the state of a request (wait != 0 blocks until it finishes).
+ *   When *finished is 1 it also returns its status, the estimate (zeroed for an
+ *   update), its submission and completion times in seconds since sk_server_create,
+ *   and forgets the request (a later call with the same id is SK_ERR_INVALID_ARG).
+ * sk_server_pending: the number of submitted requests not yet finished.
+ * sk_server_drain: blocks until every submitted request has finished.
+ * sk_server_destroy: drains, stops the threads and releases the server (not the sets).
+ * Errors: SK_ERR_INVALID_ARG (null, unknown set or request, bad relation or sizes),
+ * SK_ERR_OVER_BUDGET, SK_ERR_CUDA, SK_ERR_NO_MEMORY; a request's own status carries
+ * the errors of its update or estimate. */
+typedef struct sk_server sk_server;
+sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32_t estimate_workers,
+                           int32_t estimate_priority, sk_server** out);
+sk_status sk_server_register_set(sk_server* server, int32_t set_id, sk_set* set);
+sk_status sk_server_submit_update(sk_server* server, int32_t set_id, int32_t relation, int64_t n_rows,
+                                  const int64_t* host_cols, int64_t col_stride, const int64_t* host_weights,
+                                  int64_t* request_id);
+sk_status sk_server_submit_estimate(sk_server* server, int32_t set_id, int64_t* request_id);
+sk_status sk_server_result(sk_server* server, int64_t request_id, int32_t wait, int32_t* finished,
+                           sk_status* status, sk_estimate* est, double* arrival_s, double* done_s);
+sk_status sk_server_pending(sk_server* server, int64_t* n);
+sk_status sk_server_drain(sk_server* server);
+sk_status sk_server_destroy(sk_server* server);
 
 /* sk_launch_count: number of CUDA kernels this library has launched in this process
  * (all sets, all devices), for accounting of GPU work. */

@@ -313,6 +313,7 @@ const char* sk_status_string(sk_status status) {
     case SK_ERR_INEXACT: return "SK_ERR_INEXACT";
     case SK_ERR_NO_MEMORY: return "SK_ERR_NO_MEMORY";
     case SK_ERR_SCRATCH_TOO_SMALL: return "SK_ERR_SCRATCH_TOO_SMALL";
+    case SK_ERR_OVER_BUDGET: return "SK_ERR_OVER_BUDGET";
     default: return "SK_ERR_UNKNOWN";
   }
 }

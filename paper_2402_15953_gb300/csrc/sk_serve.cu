@@ -1,0 +1,422 @@
+// Continuous-batching request loop over live sketch sets resident on one GPU
+// (sk_server_*): the serving form of the update (Algorithm 2) and the estimate
+// (Algorithm 3 and the median over rows).
+//
+// Scheduling
+//  - Every set keeps its requests in arrival order.  An estimate of a set sees exactly
+//    the updates of that set that arrived before it; updates that arrive after it wait
+//    until it has read the counters.  Results are therefore identical to running the
+//    requests one by one (counter updates are exact integer additions).
+//  - Across sets nothing is serialised: the scheduler thread admits the head request of
+//    each set, oldest first, as soon as an update slot (a bounded number of in-flight
+//    update batches) or an estimate worker is free and its device memory fits the HBM
+//    budget, so newly arrived work joins the work already running on the device.
+//  - Updates: the host columns are copied into a stream-ordered staging buffer on the
+//    copy stream; the update runs on the update stream after that copy; an event marks
+//    its end and the set's last admitted update.  Estimates: one worker thread per
+//    estimate stream; the stream first waits for the set's last update.
+//  - A retire thread waits on the oldest in-flight update's event (updates complete in
+//    launch order on the single update stream) and releases its slot and memory; the
+//    scheduler sleeps on a condition variable until a submission, a retired update or a
+//    finished estimate changes what can be admitted.  No thread polls.
+//  - Memory: the counters of every registered set, the staging buffers of in-flight
+//    updates and a per-estimate scratch allowance are charged against the budget; a
+//    request that does not fit waits.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "sk_internal.h"
+
+using sk::set_status_from_cuda;
+
+namespace {
+
+struct SvRequest {
+  int64_t id = 0;
+  bool is_estimate = false;
+  int32_t set_id = 0;
+  int32_t relation = 0;
+  int64_t n = 0;
+  const int64_t* cols = nullptr;   // host, attribute-major, stride `stride`
+  int64_t stride = 0;
+  const int64_t* w = nullptr;      // host or null
+  size_t bytes = 0;                // memory charged while admitted
+  double arrival = 0.0, done = 0.0;
+  bool finished = false;
+  sk_status status = SK_OK;
+  sk_estimate est;
+  cudaEvent_t ev = nullptr;        // update: end of the update on the update stream
+};
+
+struct SvSet {
+  sk_set* set = nullptr;
+  size_t counter_bytes = 0;
+  size_t est_bytes = 0;
+  std::deque<SvRequest*> queue;
+  bool estimating = false;
+  bool has_update = false;
+  cudaEvent_t last_update = nullptr;
+};
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct sk_server {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  size_t resident = 0;               // counters of the registered sets (charged for good)
+  int slots = 1;
+  int est_free = 1;
+  std::chrono::steady_clock::time_point t0;
+  cudaStream_t copy_stream = nullptr, update_stream = nullptr;
+  std::vector<cudaStream_t> est_streams;
+  std::mutex mu;
+  std::condition_variable cv;        // scheduler, retire thread, waiters
+  std::condition_variable est_cv;    // estimate workers
+  std::map<int32_t, SvSet> sets;
+  std::map<int64_t, std::unique_ptr<SvRequest>> reqs;
+  std::deque<SvRequest*> inflight;   // launched updates, launch order
+  std::deque<SvRequest*> est_queue;  // admitted estimates
+  int64_t next_id = 1;
+  int64_t unfinished = 0;
+  bool changed = false;
+  bool stop = false;
+  std::vector<std::thread> threads;
+};
+
+namespace {
+
+// Device bytes an admitted update holds: its staged columns and weights.
+size_t update_bytes(const sk_set* s, int relation, int64_t n, bool weights) {
+  return (size_t)n * 8 * ((size_t)s->num_join_attrs[relation] + (weights ? 1 : 0));
+}
+
+// Launches one admitted update (called with the lock held).
+sk_status launch_update(sk_server* sv, SvSet& ss, SvRequest* q) {
+  sk_set* s = ss.set;
+  const int a = s->num_join_attrs[q->relation];
+  const size_t col_bytes = (size_t)q->n * 8 * a;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, q->bytes, sv->copy_stream);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  int64_t* dc = (int64_t*)buf;
+  int64_t* dw = q->w ? (int64_t*)((char*)buf + col_bytes) : nullptr;
+  e = cudaMemcpy2DAsync(dc, (size_t)q->n * 8, q->cols, (size_t)q->stride * 8, (size_t)q->n * 8, (size_t)a,
+                        cudaMemcpyHostToDevice, sv->copy_stream);
+  if (e == cudaSuccess && dw) e = cudaMemcpyAsync(dw, q->w, (size_t)q->n * 8, cudaMemcpyHostToDevice, sv->copy_stream);
+  cudaEvent_t copied = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(copied, sv->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->update_stream, copied, 0);
+  if (copied) cudaEventDestroy(copied);
+  sk_status st = set_status_from_cuda(e);
+  if (st == SK_OK) st = sk_sketch_update_batch(s, q->relation, q->n, dc, q->n, dw, nullptr, sv->update_stream);
+  e = cudaFreeAsync(buf, sv->update_stream);
+  if (st == SK_OK) st = set_status_from_cuda(e);
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(q->ev, sv->update_stream));
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(ss.last_update, sv->update_stream));
+  if (st == SK_OK) ss.has_update = true;
+  return st;
+}
+
+void finish(sk_server* sv, SvRequest* q, sk_status st) {
+  q->status = st;
+  q->done = now_s(sv->t0);
+  q->finished = true;
+  sv->unfinished--;
+  sv->changed = true;
+}
+
+// One scheduling pass (lock held): heads of the sets' queues in global arrival order.
+void admit(sk_server* sv) {
+  std::vector<std::pair<int64_t, int32_t>> heads;
+  for (auto& kv : sv->sets)
+    if (!kv.second.queue.empty() && !kv.second.estimating) heads.push_back({kv.second.queue.front()->id, kv.first});
+  std::sort(heads.begin(), heads.end());
+  for (const auto& h : heads) {
+    SvSet& ss = sv->sets[h.second];
+    while (!ss.queue.empty() && !ss.estimating) {
+      SvRequest* q = ss.queue.front();
+      if (!q->is_estimate) {
+        if ((int)sv->inflight.size() >= sv->slots || sv->used + q->bytes > sv->budget) break;
+        ss.queue.pop_front();
+        sv->used += q->bytes;
+        const sk_status st = launch_update(sv, ss, q);
+        if (st != SK_OK) {
+          if (q->ev) cudaEventDestroy(q->ev);
+          q->ev = nullptr;
+          sv->used -= q->bytes;
+          finish(sv, q, st);
+          continue;
+        }
+        sv->inflight.push_back(q);
+      } else {
+        if (sv->est_free == 0 || sv->used + ss.est_bytes > sv->budget) break;
+        ss.queue.pop_front();
+        q->bytes = ss.est_bytes;
+        sv->used += q->bytes;
+        sv->est_free--;
+        ss.estimating = true;
+        sv->est_queue.push_back(q);
+        sv->est_cv.notify_one();
+        break;
+      }
+    }
+  }
+}
+
+void scheduler(sk_server* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  for (;;) {
+    sv->cv.wait(lk, [&] { return sv->changed || sv->stop; });
+    if (sv->stop) return;
+    sv->changed = false;
+    admit(sv);
+    sv->cv.notify_all();   // new in-flight updates for the retire thread
+  }
+}
+
+void retirer(sk_server* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  for (;;) {
+    sv->cv.wait(lk, [&] { return !sv->inflight.empty() || sv->stop; });
+    if (sv->inflight.empty()) return;   // stop with nothing in flight
+    SvRequest* q = sv->inflight.front();
+    lk.unlock();
+    const cudaError_t e = cudaEventSynchronize(q->ev);
+    lk.lock();
+    sv->inflight.pop_front();
+    cudaEventDestroy(q->ev);
+    q->ev = nullptr;
+    sv->used -= q->bytes;
+    finish(sv, q, set_status_from_cuda(e));
+    sv->cv.notify_all();
+  }
+}
+
+void estimator(sk_server* sv, cudaStream_t stream) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  for (;;) {
+    sv->est_cv.wait(lk, [&] { return !sv->est_queue.empty() || sv->stop; });
+    if (sv->est_queue.empty()) return;
+    SvRequest* q = sv->est_queue.front();
+    sv->est_queue.pop_front();
+    SvSet& ss = sv->sets[q->set_id];
+    sk_set* s = ss.set;
+    const bool wait = ss.has_update;
+    cudaEvent_t last = ss.last_update;
+    lk.unlock();
+    sk_status st = SK_OK;
+    if (wait) st = set_status_from_cuda(cudaStreamWaitEvent(stream, last, 0));
+    if (st == SK_OK) st = sk_estimate_join(s, &q->est, stream);
+    lk.lock();
+    ss.estimating = false;
+    sv->est_free++;
+    sv->used -= q->bytes;
+    finish(sv, q, st);
+    sv->cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32_t estimate_workers,
+                           int32_t estimate_priority, sk_server** out) {
+  if (!out || hbm_budget_bytes <= 0 || update_slots < 1 || estimate_workers < 1 || estimate_workers > 64)
+    return SK_ERR_INVALID_ARG;
+  *out = nullptr;
+  sk_server* sv = new (std::nothrow) sk_server();
+  if (!sv) return SK_ERR_NO_MEMORY;
+  sv->budget = (size_t)hbm_budget_bytes;
+  sv->slots = update_slots;
+  sv->est_free = estimate_workers;
+  sv->t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaGetDevice(&sv->device);
+  int lo = 0, hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->update_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < estimate_workers && e == cudaSuccess; i++) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, estimate_priority ? hi : lo);
+    if (e == cudaSuccess) sv->est_streams.push_back(s);
+  }
+  if (e != cudaSuccess) {
+    for (cudaStream_t s : sv->est_streams) cudaStreamDestroy(s);
+    if (sv->copy_stream) cudaStreamDestroy(sv->copy_stream);
+    if (sv->update_stream) cudaStreamDestroy(sv->update_stream);
+    delete sv;
+    return set_status_from_cuda(e);
+  }
+  sv->threads.emplace_back(scheduler, sv);
+  sv->threads.emplace_back(retirer, sv);
+  for (cudaStream_t s : sv->est_streams) sv->threads.emplace_back(estimator, sv, s);
+  *out = sv;
+  return SK_OK;
+}
+
+sk_status sk_server_register_set(sk_server* sv, int32_t set_id, sk_set* set) {
+  if (!sv || !set) return SK_ERR_INVALID_ARG;
+  const size_t cb = (size_t)set->r * set->d * set->m * 8;
+  const size_t slots = (size_t)std::max(2, set->r);
+  const size_t est = (slots + 1) * set->d * set->m * 32 + 2 * (size_t)set->d * 4 * set->m * 16 + (size_t)(set->m / 2) * 16;
+  cudaEvent_t ev = nullptr;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->sets.count(set_id)) return SK_ERR_INVALID_ARG;
+  if (sv->used + cb > sv->budget) return SK_ERR_OVER_BUDGET;
+  const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  SvSet& ss = sv->sets[set_id];
+  ss.set = set;
+  ss.counter_bytes = cb;
+  ss.est_bytes = est;
+  ss.last_update = ev;
+  sv->used += cb;
+  sv->resident += cb;
+  return SK_OK;
+}
+
+sk_status sk_server_submit_update(sk_server* sv, int32_t set_id, int32_t relation, int64_t n_rows,
+                                  const int64_t* host_cols, int64_t col_stride, const int64_t* host_weights,
+                                  int64_t* request_id) {
+  if (!sv || !request_id || n_rows < 0) return SK_ERR_INVALID_ARG;
+  std::unique_ptr<SvRequest> q(new (std::nothrow) SvRequest());
+  if (!q) return SK_ERR_NO_MEMORY;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->sets.find(set_id);
+  if (it == sv->sets.end()) return SK_ERR_INVALID_ARG;
+  sk_set* s = it->second.set;
+  if (relation < 0 || relation >= s->r || (n_rows > 0 && (!host_cols || col_stride < n_rows)))
+    return SK_ERR_INVALID_ARG;
+  q->id = sv->next_id++;
+  q->set_id = set_id;
+  q->relation = relation;
+  q->n = n_rows;
+  q->cols = host_cols;
+  q->stride = col_stride;
+  q->w = host_weights;
+  q->bytes = update_bytes(s, relation, n_rows, host_weights != nullptr);
+  q->arrival = now_s(sv->t0);
+  *request_id = q->id;
+  SvRequest* raw = q.get();
+  sv->reqs[q->id] = std::move(q);
+  sv->unfinished++;
+  if (n_rows == 0) {   // no tuples: nothing to order against, finished at once
+    finish(sv, raw, SK_OK);
+    sv->cv.notify_all();
+    return SK_OK;
+  }
+  if (raw->bytes > sv->budget - sv->resident) {   // could never be admitted
+    finish(sv, raw, SK_ERR_OVER_BUDGET);
+    sv->cv.notify_all();
+    return SK_OK;
+  }
+  it->second.queue.push_back(raw);
+  sv->changed = true;
+  sv->cv.notify_all();
+  return SK_OK;
+}
+
+sk_status sk_server_submit_estimate(sk_server* sv, int32_t set_id, int64_t* request_id) {
+  if (!sv || !request_id) return SK_ERR_INVALID_ARG;
+  std::unique_ptr<SvRequest> q(new (std::nothrow) SvRequest());
+  if (!q) return SK_ERR_NO_MEMORY;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->sets.find(set_id);
+  if (it == sv->sets.end()) return SK_ERR_INVALID_ARG;
+  q->id = sv->next_id++;
+  q->is_estimate = true;
+  q->set_id = set_id;
+  q->arrival = now_s(sv->t0);
+  *request_id = q->id;
+  SvRequest* raw = q.get();
+  sv->reqs[q->id] = std::move(q);
+  sv->unfinished++;
+  if (it->second.est_bytes > sv->budget - sv->resident) {   // could never be admitted
+    finish(sv, raw, SK_ERR_OVER_BUDGET);
+    sv->cv.notify_all();
+    return SK_OK;
+  }
+  it->second.queue.push_back(raw);
+  sv->changed = true;
+  sv->cv.notify_all();
+  return SK_OK;
+}
+
+sk_status sk_server_result(sk_server* sv, int64_t request_id, int32_t wait, int32_t* finished, sk_status* status,
+                           sk_estimate* est, double* arrival_s, double* done_s) {
+  if (!sv || !finished) return SK_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(request_id);
+  if (it == sv->reqs.end()) return SK_ERR_INVALID_ARG;
+  SvRequest* q = it->second.get();
+  if (wait) sv->cv.wait(lk, [&] { return q->finished; });
+  *finished = q->finished ? 1 : 0;
+  if (!q->finished) return SK_OK;
+  if (status) *status = q->status;
+  if (est) {
+    if (q->is_estimate) *est = q->est;
+    else std::memset(est, 0, sizeof(*est));
+  }
+  if (arrival_s) *arrival_s = q->arrival;
+  if (done_s) *done_s = q->done;
+  sv->reqs.erase(it);
+  return SK_OK;
+}
+
+sk_status sk_server_pending(sk_server* sv, int64_t* n) {
+  if (!sv || !n) return SK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *n = sv->unfinished;
+  return SK_OK;
+}
+
+sk_status sk_server_drain(sk_server* sv) {
+  if (!sv) return SK_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  sv->cv.wait(lk, [&] { return sv->unfinished == 0; });
+  return SK_OK;
+}
+
+sk_status sk_server_destroy(sk_server* sv) {
+  if (!sv) return SK_OK;
+  sk_server_drain(sv);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    sv->cv.notify_all();
+    sv->est_cv.notify_all();
+  }
+  for (std::thread& t : sv->threads) t.join();
+  cudaStreamSynchronize(sv->update_stream);
+  for (cudaStream_t s : sv->est_streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  cudaStreamDestroy(sv->copy_stream);
+  cudaStreamDestroy(sv->update_stream);
+  for (auto& kv : sv->sets)
+    if (kv.second.last_update) cudaEventDestroy(kv.second.last_update);
+  delete sv;
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -93,3 +93,24 @@ def test_register_beyond_budget_is_refused():
     assert srv.register_set(0, [1, 1], [(0, 0, 1, 0)], 1 << 12, 4, 1)      # 256 KB
     assert not srv.register_set(1, [1, 1], [(0, 0, 1, 0)], 1 << 16, 4, 1)  # 4 MB
     srv.close()
+
+
+def test_native_server_edges():
+    """Unknown sets and relations are refused at submission; an update that could never
+    fit the budget finishes with SK_ERR_OVER_BUDGET instead of waiting; an empty update
+    finishes at once; an estimate of an untouched set is all zero."""
+    srv = SketchServer(hbm_budget_bytes=1 << 26)
+    assert srv.register_set(0, [1, 1], [(0, 0, 1, 0)], 256, 3, 5)
+    with pytest.raises(pkg.SketchError):
+        srv.submit_estimate(7)
+    with pytest.raises(pkg.SketchError):
+        srv.submit_update(0, 5, torch.zeros((1, 3), dtype=torch.int64))
+    empty = srv.submit_update(0, 0, torch.zeros((1, 0), dtype=torch.int64))
+    big = srv.submit_update(0, 1, torch.zeros((1, 1 << 23), dtype=torch.int64))
+    est = srv.submit_estimate(0)
+    srv.serve()
+    assert srv.pending() == 0
+    assert empty.error is None and big.error == "SK_ERR_OVER_BUDGET"
+    assert est.error is None and est.result["rows"] == [0, 0, 0]
+    assert est.latency >= 0.0
+    srv.close()
