@@ -119,7 +119,10 @@ __device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
 // counter receives one atomic per warp (hot keys of skewed columns otherwise serialise
 // on one shared-memory address).  Lanes past the end or with a key outside the declared
 // domain take part with Delta = 0.
-template <int A, bool POW2, bool SMEM, bool AGG = false>
+//
+// DEG1: every attribute of the relation is in exactly one join (chains, stars), so each
+// attribute has one sign polynomial and the loop over its joins disappears.
+template <int A, bool POW2, bool SMEM, bool AGG = false, bool DEG1 = false>
 __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s_coef, int* s_sub, int64_t i,
                                              bool live = true) {
   const int na = A > 0 ? A : p.a;
@@ -165,7 +168,8 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
           bin += reduce_lazy(v) % p.m;
         }
         off += 2;
-        for (int e = 0; e < p.deg[u]; e++, off += 4) {
+        const int deg = DEG1 ? 1 : p.deg[u];
+        for (int e = 0; e < deg; e++, off += 4) {
           const ulonglong2 s01 = *(const ulonglong2*)(cr + off);
           const ulonglong2 s23 = *(const ulonglong2*)(cr + off + 2);
           uint64_t acc = mac_narrow(s23.y, xu, s23.x);
@@ -184,7 +188,8 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
         const uint64_t h = addmod(mulmod(cr[off + 1], xu), cr[off]);
         bin += reduce_m<POW2>(h, p.m);
         off += 2;
-        for (int e = 0; e < p.deg[u]; e++, off += 4) {
+        const int deg = DEG1 ? 1 : p.deg[u];
+        for (int e = 0; e < deg; e++, off += 4) {
           uint64_t acc = cr[off + 3];
           acc = addmod(mulmod(acc, xu), cr[off + 2]);
           acc = addmod(mulmod(acc, xu), cr[off + 1]);

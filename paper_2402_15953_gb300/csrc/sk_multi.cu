@@ -25,35 +25,38 @@ struct MultiItem {
   int64_t chunk0;   // first global chunk of this item
   int pow2;
   int use_smem;
+  int deg1;         // every attribute in exactly one join
 };
 
-template <int A, bool POW2>
+template <int A, bool POW2, bool DEG1>
 __device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
                                             int64_t t0, int64_t t1) {
   if (use_smem) {
     const int64_t dm = (int64_t)p.d * (int64_t)p.m;
     for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) s_sub[j] = 0;
     __syncthreads();
-    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) update_tuple<A, POW2, true>(p, s_coef, s_sub, i);
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+      update_tuple<A, POW2, true, false, DEG1>(p, s_coef, s_sub, i);
     __syncthreads();
     for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) {
       const int v = s_sub[j];
       if (v != 0) red_add_global(p.ctr + j, (unsigned long long)(int64_t)v);
     }
   } else {
-    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) update_tuple<A, POW2, false>(p, s_coef, s_sub, i);
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+      update_tuple<A, POW2, false, false, DEG1>(p, s_coef, s_sub, i);
   }
 }
 
-template <bool POW2>
+template <bool POW2, bool DEG1>
 __device__ __forceinline__ void multi_dispatch(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
                                                int64_t t0, int64_t t1) {
   switch (p.a) {
-    case 1: multi_chunk<1, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
-    case 2: multi_chunk<2, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
-    case 3: multi_chunk<3, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
-    case 4: multi_chunk<4, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
-    default: multi_chunk<5, POW2>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 1: multi_chunk<1, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 2: multi_chunk<2, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 3: multi_chunk<3, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    case 4: multi_chunk<4, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
+    default: multi_chunk<5, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
   }
 }
 
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
   // the current item's arguments: read in the tuple loop from shared memory rather than
   // from the item array (global memory the counter updates could alias)
   __shared__ UpdArgs s_args;
-  __shared__ int s_pow2, s_smem;
+  __shared__ int s_pow2, s_smem, s_deg1;
   uint64_t* s_coef = (uint64_t*)smem_raw;
   int* s_sub = (int*)(s_coef + coef_words);
   int cur = -1;
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
         s_args = mi.args;
         s_pow2 = mi.pow2;
         s_smem = mi.use_smem;
+        s_deg1 = mi.deg1;
       }
       const int nc = mi.args.d * mi.args.row_len;
       for (int j = threadIdx.x; j < nc; j += blockDim.x) s_coef[j] = mi.args.coef[j];
@@ -101,8 +105,13 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
     const UpdArgs& p = s_args;
     const int64_t t0 = (c - items[it].chunk0) * chunk;
     const int64_t t1 = min(p.n, t0 + chunk);
-    if (s_pow2) multi_dispatch<true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
-    else multi_dispatch<false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+    if (s_pow2) {
+      if (s_deg1) multi_dispatch<true, true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+      else multi_dispatch<true, false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+    } else {
+      if (s_deg1) multi_dispatch<false, true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+      else multi_dispatch<false, false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+    }
     __syncthreads();
   }
 }
@@ -185,6 +194,9 @@ sk_status plan_build(sk_update_plan* pl) {
     a.status = s->d_status;
     a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(cfg.chunk_tuples, 1);
     mi.pow2 = (s->m & (s->m - 1)) == 0;
+    mi.deg1 = 1;
+    for (int t = 0; t < rp.a; t++)
+      if (rp.deg[t] != 1) mi.deg1 = 0;
     const int64_t dm = (int64_t)s->d * s->m;
     // the int32 sub-sketch must also fit in shared memory next to the coefficients
     mi.use_smem = (cfg.smem_max_counters > 0 && dm <= cfg.smem_max_counters && dm * 4 <= 160 * 1024) ? 1 : 0;

@@ -28,7 +28,7 @@ namespace {
 using namespace dev;
 
 
-template <int A, bool POW2, bool SMEM>
+template <int A, bool POW2, bool SMEM, bool DEG1>
 __global__ void __launch_bounds__(256) k_update(UpdArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* s_coef = (uint64_t*)smem_raw;
@@ -45,10 +45,10 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs p) {
     // warp-uniform loop: every lane of a warp runs the same iterations (collectives inside)
     const int lane = threadIdx.x & 31;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); b < p.n; b += step)
-      update_tuple<A, POW2, SMEM, true>(p, s_coef, s_sub, b + lane, b + lane < p.n);
+      update_tuple<A, POW2, SMEM, true, DEG1>(p, s_coef, s_sub, b + lane, b + lane < p.n);
   } else {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += step)
-      update_tuple<A, POW2, SMEM>(p, s_coef, s_sub, i);
+      update_tuple<A, POW2, SMEM, false, DEG1>(p, s_coef, s_sub, i);
   }
   if (SMEM) {
     __syncthreads();
@@ -143,10 +143,18 @@ int update_grid_per_sm(int resident) {
   return x <= 0 ? (1 << 30) / 64 : x;
 }
 
+// true when each of the relation's A attributes is in exactly one join
+bool all_deg1(const UpdArgs& a) {
+  if (a.a < 1) return false;
+  for (int u = 0; u < a.a; u++)
+    if (a.deg[u] != 1) return false;
+  return true;
+}
+
 // grid <= 0 sizes the grid with update_grid_per_sm.
 template <int A, bool POW2, bool SMEM>
 cudaError_t launch_one(const UpdArgs& a, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_update<A, POW2, SMEM>;
+  auto kern = (A > 0 && all_deg1(a)) ? k_update<A, POW2, SMEM, (A > 0)> : k_update<A, POW2, SMEM, false>;
   cudaError_t e = allow_dynamic_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   if (grid <= 0) {
