@@ -241,7 +241,7 @@ __host__ __device__ inline int key_record_vectors(int d, bool narrow) {
 }
 
 // bin mod m and sign parity of attribute u's functions for one row at key x (< 2^32)
-template <bool POW2>
+template <bool POW2, bool DEG1 = false>
 __device__ __forceinline__ uint32_t key_row_hash(const UpdArgs& p, const uint64_t* c, int deg, uint32_t x,
                                                  uint32_t* parity) {
   const ulonglong2 bc = *(const ulonglong2*)c;
@@ -250,6 +250,7 @@ __device__ __forceinline__ uint32_t key_row_hash(const UpdArgs& p, const uint64_
   if (POW2) h = ((uint32_t)v + mersenne_q1(v)) & (uint32_t)(p.m - 1);
   else h = (uint32_t)(reduce_lazy(v) % p.m);
   uint32_t sx = 0;
+  if (DEG1) deg = 1;
   for (int k = 0; k < deg; k++) {
     const ulonglong2 s01 = *(const ulonglong2*)(c + 2 + 4 * k);
     const ulonglong2 s23 = *(const ulonglong2*)(c + 4 + 4 * k);
@@ -263,7 +264,7 @@ __device__ __forceinline__ uint32_t key_row_hash(const UpdArgs& p, const uint64_
 }
 
 // Record of attribute u for key x (< 2^31: the field element is the key itself).
-template <bool POW2>
+template <bool POW2, bool DEG1 = false>
 __device__ __forceinline__ void key_record(const UpdArgs& p, const TabArgs& t, const uint64_t* s_coef, int u,
                                            uint32_t x, uint32_t* out) {
   const int deg = p.deg[u];
@@ -285,7 +286,7 @@ __device__ __forceinline__ void key_record(const UpdArgs& p, const TabArgs& t, c
             const int row = 2 * wi + h;
             if (row < p.d) {
               uint32_t par;
-              const uint32_t b = key_row_hash<POW2>(p, cr + (int64_t)row * p.row_len, deg, x, &par);
+              const uint32_t b = key_row_hash<POW2, DEG1>(p, cr + (int64_t)row * p.row_len, deg, x, &par);
               e |= b << (16 * h);
               mask |= par << row;
             }
@@ -293,7 +294,7 @@ __device__ __forceinline__ void key_record(const UpdArgs& p, const TabArgs& t, c
         }
       } else if (wi < p.d) {
         uint32_t par;
-        const uint32_t b = key_row_hash<POW2>(p, cr + (int64_t)wi * p.row_len, deg, x, &par);
+        const uint32_t b = key_row_hash<POW2, DEG1>(p, cr + (int64_t)wi * p.row_len, deg, x, &par);
         e = b | (par << 31);
       }
       w[j] = e;

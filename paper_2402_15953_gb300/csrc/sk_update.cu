@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs p) {
 }
 
 // Key-table records for every declared domain key of every attribute (one thread per key).
-template <bool POW2>
+template <bool POW2, bool DEG1>
 __global__ void __launch_bounds__(256) k_key_table(UpdArgs p, TabArgs t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* s_coef = (uint64_t*)smem_raw;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_key_table(UpdArgs p, TabArgs t) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
     int u = 0;
     while (u + 1 < p.a && g >= t.base[u + 1]) u++;
-    key_record<POW2>(p, t, s_coef, u, (uint32_t)(g - t.base[u]), t.tbl + g * 4 * t.rvec);
+    key_record<POW2, DEG1>(p, t, s_coef, u, (uint32_t)(g - t.base[u]), t.tbl + g * 4 * t.rvec);
   }
 }
 
@@ -502,7 +502,9 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
       } else {
         t.tbl = (uint32_t*)buf;
         a.smem_wmax = 0;
-        auto kb = pow2 ? k_key_table<true> : k_key_table<false>;
+        const bool d1 = all_deg1(a);
+        auto kb = pow2 ? (d1 ? k_key_table<true, true> : k_key_table<true, false>)
+                       : (d1 ? k_key_table<false, true> : k_key_table<false, false>);
         e = cudaSuccess;
         if (coef_bytes > 48 * 1024) e = allow_dynamic_smem((const void*)kb);
         if (e == cudaSuccess) {
