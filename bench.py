@@ -56,6 +56,8 @@ def parse_args():
                     help="do not declare the key domains (every tuple is hashed; no key tables)")
     ap.add_argument("--estimate-priority", default="high", choices=["high", "normal"],
                     help="stream priority of the estimates that overlap the next step's update")
+    ap.add_argument("--plan-config", default=None,
+                    help="batched workload: chunk_tuples,threads,ctas_per_sm,smem_max_counters instead of autotuning")
     ap.add_argument("--estimator", default="fused", choices=["fft64", "ntt", "fused"],
                     help="exact estimator arithmetic of the star step (identical rows from each)")
     ap.add_argument("--no-pipeline", action="store_true",
@@ -561,7 +563,11 @@ def run_batched(args, world, rank):
     sb = [pkg.SketchSet(b.num_join_attrs, b.edges, b.m, b.d, b.hash_seed) for b in wl]
     plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(sb, wl)])
     stream = torch.cuda.current_stream()
-    best, tune_ms = plan.autotune()
+    if args.plan_config:
+        plan.set_config(*[int(x) for x in args.plan_config.split(",")])
+        best, tune_ms = plan.config(), 0.0
+    else:
+        best, tune_ms = plan.autotune()
 
     def step_a():
         for s, b in zip(sa, wl):
