@@ -133,3 +133,33 @@ def test_plan_zero_clears_only_the_planned_relations(workload):
     plan.close()
     for s in sets + fresh:
         s.close()
+
+
+def test_full_size_batched_workload_sampled_against_oracle():
+    """The bench's batched workload at full size (256 relations, 7.9e7 tuples, widths
+    2^10..2^18) through one zeroing and one persistent run in the configuration the
+    autotuner picks: the three smallest relations' sketches in full and two rows of the
+    largest relation's sketch equal the oracle's."""
+    from paper_2402_15953_gb300 import build
+    build.build()
+    O.build()
+    wl = synth.batched(seed=42, device="cuda")
+    sets = _sets(wl)
+    plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(sets, wl)])
+    plan.set_config(8192, 256, 8, 8192)
+    plan.zero()
+    plan.run()
+    torch.cuda.synchronize()
+    order = sorted(range(len(wl)), key=lambda i: wl[i].relation.n)
+    for i in order[:3] + order[-1:]:
+        b = wl[i]
+        q = O.canonical_query(b.num_join_attrs, b.edges)
+        co = O.draw_coefficients(b.hash_seed, b.d, q.n_comp, len(q.edges))
+        rows = list(range(b.d)) if i != order[-1] else [0, b.d - 1]
+        want = O.sketch_relation(q, co[rows], 0, b.relation.cols.cpu().numpy(), b.relation.weights.cpu().numpy(),
+                                 b.m, threads=16)
+        got = sets[i].counters[0].cpu().numpy()[rows]
+        assert np.array_equal(got, want), (i, b.relation.n, b.m)
+    plan.close()
+    for s in sets:
+        s.close()

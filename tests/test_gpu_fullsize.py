@@ -2,7 +2,9 @@
 tuples x 5 Zipf(1.1) int64 keys over [0, 10^6), five 10^6-row uniform dimensions,
 m = 2^16, d = 9, seed 42), on outputs the oracle can compute: every counter of the
 dimension sketches, two complete rows of the fact sketch, and the estimate of those
-two rows; the median is checked to be the lower median of the GPU's row values."""
+two rows; the median is checked to be the lower median of the GPU's row values.  Two
+configurations: the one the bench times (declared key domains, so the fact table goes
+through the key tables; fused estimator) and per-tuple hashing with the FP64 estimator."""
 import numpy as np
 import pytest
 import torch
@@ -16,15 +18,17 @@ pytestmark = pytest.mark.gpu
 ROWS = [0, 4]
 
 
-@pytest.fixture(scope="module")
-def star_run():
+@pytest.fixture(scope="module", params=["tables_fused", "per_tuple_fft64"])
+def star_run(request):
     from paper_2402_15953_gb300 import build
     build.build()
     O.build()
     wl = synth.star(device="cuda")
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
+    declared = request.param == "tables_fused"
+    s.set_estimator("fused" if declared else "fft64")
     for k, rel in enumerate(wl.relations):
-        s.update(k, rel.cols)
+        s.update(k, rel.cols, domain=wl.domains[k] if declared else None)
     s.sync()
     est = s.estimate()
     counters = s.counters.cpu().numpy()
