@@ -230,6 +230,7 @@ class BatchedSet:
     d: int
     hash_seed: int
     relation: Relation
+    domains: Optional[List[int]] = None   # relation 0's key domain per column: keys in [0, dom)
 
 
 def batched(count: int = 256, median_rows: float = 1e5, sigma: float = 1.5, min_rows: int = 1000,
@@ -247,12 +248,14 @@ def batched(count: int = 256, median_rows: float = 1e5, sigma: float = 1.5, min_
         n = sizes[i]
         n_ins = max(1, int(round(n / (1 + delete_frac))))
         cols = []
+        cols_dom = []
         for c in range(a):
             s_exp = float(rng.uniform(0.8, 1.4))
             dom = int(round(10 ** rng.uniform(4, 7)))
+            cols_dom.append(dom)
             cols.append(zipf_keys(n_ins, s_exp, dom, sub_seed(seed, i, c), device))
         rel = with_deletions(Relation(torch.stack(cols)), delete_frac, sub_seed(seed, i, 77))
         m = 1 << int(rng.integers(log2m[0], log2m[1] + 1))
         out.append(BatchedSet([a] + [1] * a, [(0, k, 1 + k, 0) for k in range(a)], m, d,
-                              sub_seed(seed, i, 5), rel))
+                              sub_seed(seed, i, 5), rel, cols_dom))
     return out
