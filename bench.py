@@ -762,10 +762,29 @@ def run_serving(args, world, rank):
         return {"requests": len(trace), "wall_s": wall, "requests_per_s": len(trace) / wall,
                 "tuples_per_s": tuples / wall}
 
+    def capacity(trace):
+        """The server's own throughput: every request queued on a held server, then
+        released at once (the timed region starts at the release)."""
+        srv = SketchServer(hbm_budget_bytes=32 << 30, update_slots=16, estimate_workers=4)
+        for i, (a, e, m, d, sd) in enumerate(sets):
+            srv.register_set(i, a, e, m, d, sd)
+            srv.sets[i].sset.set_estimator(args.estimator)
+        srv.hold(True)
+        reqs = [srv.submit_update(r[1], r[2], r[3], r[4]) if r[0] == "update" else srv.submit_estimate(r[1])
+                for r in trace]
+        t0 = time.perf_counter()
+        srv.hold(False)
+        srv.serve(until_idle=True)
+        wall = time.perf_counter() - t0
+        srv.close()
+        tuples = sum(r.cols.shape[1] for r in reqs if r.kind == "update")
+        return {"requests": len(reqs), "wall_s": wall, "requests_per_s": len(reqs) / wall,
+                "tuples_per_s": tuples / wall, "errors": sum(1 for r in reqs if r.error)}
+
     trace = make_trace(args.requests, 1)
     run(make_trace(200, 2), None)           # warm-up (scratch allocation, kernel attributes)
     sat = run(trace, None)
-    points = {"saturated": sat, "sequential_one_by_one": sequential(trace)}
+    points = {"saturated": sat, "server_capacity": capacity(trace), "sequential_one_by_one": sequential(trace)}
     for frac in (0.5, 0.9):
         points[f"rate_{int(frac * 100)}pct"] = run(trace, frac * sat["requests_per_s"])
     line = {"metric": "serving: p50/p99 request latency and throughput", "value": sat["tuples_per_s"],

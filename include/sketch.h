@@ -366,6 +366,9 @@ sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t c
  *   When *finished is 1 it also returns its status, the estimate (zeroed for an
  *   update), its submission and completion times in seconds since sk_server_create,
  *   and forgets the request (a later call with the same id is SK_ERR_INVALID_ARG).
+ * sk_server_hold: on != 0 pauses admission (submissions still queue; work already on the
+ *   device finishes), on == 0 resumes it; e.g. to queue a batch of requests and release
+ *   them at once.  sk_server_drain on a held server with queued requests does not return.
  * sk_server_pending: the number of submitted requests not yet finished.
  * sk_server_drain: blocks until every submitted request has finished.
  * sk_server_destroy: drains, stops the threads and releases the server (not the sets).
@@ -382,6 +385,7 @@ sk_status sk_server_submit_update(sk_server* server, int32_t set_id, int32_t rel
 sk_status sk_server_submit_estimate(sk_server* server, int32_t set_id, int64_t* request_id);
 sk_status sk_server_result(sk_server* server, int64_t request_id, int32_t wait, int32_t* finished,
                            sk_status* status, sk_estimate* est, double* arrival_s, double* done_s);
+sk_status sk_server_hold(sk_server* server, int32_t on);
 sk_status sk_server_pending(sk_server* server, int64_t* n);
 sk_status sk_server_drain(sk_server* server);
 sk_status sk_server_destroy(sk_server* server);

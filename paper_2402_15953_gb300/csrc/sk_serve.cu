@@ -93,6 +93,7 @@ struct sk_server {
   int64_t unfinished = 0;
   bool changed = false;
   bool stop = false;
+  bool hold = false;                 // admission paused (requests still queue)
   std::vector<std::thread> threads;
 };
 
@@ -182,7 +183,7 @@ void scheduler(sk_server* sv) {
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
   for (;;) {
-    sv->cv.wait(lk, [&] { return sv->changed || sv->stop; });
+    sv->cv.wait(lk, [&] { return (sv->changed && !sv->hold) || sv->stop; });
     if (sv->stop) return;
     sv->changed = false;
     admit(sv);
@@ -382,6 +383,17 @@ sk_status sk_server_result(sk_server* sv, int64_t request_id, int32_t wait, int3
   return SK_OK;
 }
 
+sk_status sk_server_hold(sk_server* sv, int32_t on) {
+  if (!sv) return SK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->hold = on != 0;
+  if (!sv->hold) {
+    sv->changed = true;
+    sv->cv.notify_all();
+  }
+  return SK_OK;
+}
+
 sk_status sk_server_pending(sk_server* sv, int64_t* n) {
   if (!sv || !n) return SK_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -398,6 +410,7 @@ sk_status sk_server_drain(sk_server* sv) {
 
 sk_status sk_server_destroy(sk_server* sv) {
   if (!sv) return SK_OK;
+  sk_server_hold(sv, 0);
   sk_server_drain(sv);
   {
     std::lock_guard<std::mutex> lk(sv->mu);

@@ -139,6 +139,10 @@ class SketchServer:
                 self.completed.append(req)
                 req.event.set()
 
+    def hold(self, on: bool = True) -> None:
+        """Pauses (on) or resumes admission; submitted requests queue while held."""
+        _ck(self._L.sk_server_hold(self.handle, 1 if on else 0), "sk_server_hold")
+
     def pending(self) -> int:
         n = ctypes.c_int64()
         _ck(self._L.sk_server_pending(self.handle, ctypes.byref(n)), "sk_server_pending")
@@ -158,6 +162,7 @@ class SketchServer:
         """Finishes every submitted request, collects the results and releases the server
         and its sets."""
         if self.handle:
+            self.hold(False)
             self.serve(until_idle=True)
             self._L.sk_server_destroy(self.handle)
             self.handle = None

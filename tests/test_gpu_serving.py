@@ -114,3 +114,28 @@ def test_native_server_edges():
     assert est.error is None and est.result["rows"] == [0, 0, 0]
     assert est.latency >= 0.0
     srv.close()
+
+
+def test_hold_then_release_equals_alone():
+    """Requests queued on a held server wait (nothing finishes); released at once they give
+    the results of running each set's requests one by one."""
+    import time
+    sets, reqs = _trace(5, n_sets=4, n_req=40)
+    alone = _alone(sets, reqs)
+    srv = SketchServer()
+    for i, (a, e, m, d, s) in enumerate(sets):
+        assert srv.register_set(i, a, e, m, d, s)
+    srv.hold(True)
+    handles = {}
+    for j, r in enumerate(reqs):
+        if r[0] == "update":
+            srv.submit_update(r[1], r[2], r[3], r[4])
+        else:
+            handles[j] = srv.submit_estimate(r[1])
+    time.sleep(0.05)
+    assert srv.pending() == len(reqs)
+    srv.hold(False)
+    srv.serve()
+    for j in alone:
+        assert handles[j].error is None and handles[j].result["rows"] == alone[j]["rows"]
+    srv.close()
