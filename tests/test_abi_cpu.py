@@ -71,3 +71,33 @@ def test_null_handles_are_rejected(lib):
     assert lib.sk_sync(None, None) == pkg.SK_ERR_INVALID_ARG
     assert lib.sk_sketch_merge(None, None, None) == pkg.SK_ERR_INVALID_ARG
     assert lib.sk_sketch_update_batch(None, 0, 0, None, 0, None, None, None) == pkg.SK_ERR_INVALID_ARG
+
+
+def test_batched_serving_and_many_argument_checks(lib):
+    """Host-side argument checks of the batched, many-set and serving entry points (no
+    GPU call is reached)."""
+    import ctypes
+    inv = pkg.SK_ERR_INVALID_ARG
+    assert lib.sk_update_plan_zero(None, None) == inv
+    assert lib.sk_update_plan_run(None, None) == inv
+    assert lib.sk_estimate_many(None, -1, None, None) == inv
+    assert lib.sk_estimate_many(None, 2, None, None) == inv
+    assert lib.sk_estimate_many(None, 0, None, None) == 0
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    out = (pkg.sk_estimate * 2)()
+    assert lib.sk_estimate_many(nulls, 2, out, None) == inv
+    h = ctypes.c_void_p()
+    for budget, slots, workers in [(0, 1, 1), (1 << 20, 0, 1), (1 << 20, 1, 0), (1 << 20, 1, 65)]:
+        assert lib.sk_server_create(budget, slots, workers, 0, ctypes.byref(h)) == inv
+    assert lib.sk_server_create(1 << 20, 1, 1, 0, None) == inv
+    rid, n = ctypes.c_int64(), ctypes.c_int64()
+    fin = ctypes.c_int32()
+    assert lib.sk_server_register_set(None, 0, None) == inv
+    assert lib.sk_server_submit_update(None, 0, 0, 0, None, 0, None, ctypes.byref(rid)) == inv
+    assert lib.sk_server_submit_estimate(None, 0, ctypes.byref(rid)) == inv
+    assert lib.sk_server_result(None, 1, 0, ctypes.byref(fin), None, None, None, None) == inv
+    assert lib.sk_server_hold(None, 1) == inv
+    assert lib.sk_server_pending(None, ctypes.byref(n)) == inv
+    assert lib.sk_server_drain(None) == inv
+    assert lib.sk_server_destroy(None) == 0
+    assert pkg.sk_status_string(-15) == "SK_ERR_OVER_BUDGET"
