@@ -453,6 +453,7 @@ __device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const 
                             int64_t twstride, bool inv, typename Ops::T r4) {
   using T = typename Ops::T;
   const int L = 1 << logL;
+  const int lc = __ffs(cnt) - 1;   // cnt is a power of two: indices by shifts, not divisions
   int lh = logL - 1;   // log2 of the larger half size of the pair
   for (; lh >= 1; lh -= 2) {
     const int q = 1 << (lh - 1);
@@ -461,7 +462,7 @@ __device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const 
     const int total4 = cnt * (L >> 2);
     const int qS = q * S;
     for (int b = threadIdx.x; b < total4; b += blockDim.x) {
-      const int v = b % cnt, jj = b / cnt;
+      const int v = b & (cnt - 1), jj = b >> lc;
       const int grp = jj >> (lh - 1), pos = jj & (q - 1);
       T* e = s + (grp * 4 * q + pos) * S + v;
       const T w4 = Ops::tw(tw, (int64_t)pos * s4, inv);
@@ -480,7 +481,7 @@ __device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const 
   if (lh == 0) {   // odd logL: the last stage, half size 1 (twiddle 1)
     const int total = cnt * (L >> 1);
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
-      const int v = b % cnt, g = b / cnt;
+      const int v = b & (cnt - 1), g = b >> lc;
       T* e = s + (2 * g) * S + v;
       const T a0 = e[0], a1 = e[S];
       e[0] = Ops::add(a0, a1);
@@ -501,19 +502,20 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
   const int R = 1 << logR, C = 1 << logC;
   const int S = cb + 1;
   const int64_t N = (int64_t)R * C;
-  const int blocks_per_vec = C / cb;
-  const int64_t vec = blockIdx.x / blocks_per_vec;
-  const int c0 = (blockIdx.x % blocks_per_vec) * cb;
+  const int lcb = __ffs(cb) - 1;   // cb is a power of two
+  const int blocks_per_vec = C >> lcb;
+  const int64_t vec = blockIdx.x >> (logC - lcb);
+  const int c0 = (blockIdx.x & (blocks_per_vec - 1)) * cb;
   T* v = buf + vec * N;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
-    const int c = idx % cb, n1 = idx / cb;
+    const int c = idx & (cb - 1), n1 = idx >> lcb;
     sm[n1 * S + c] = v[(int64_t)n1 * C + c0 + c];
   }
   __syncthreads();
   smem_dif_il<Ops>(sm, cb, S, logR, tw, C, inv, r4);
   const int64_t half = N >> 1;
   for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
-    const int c = idx % cb, k1 = idx / cb;
+    const int c = idx & (cb - 1), k1 = idx >> lcb;
     const int64_t n2 = c0 + c;
     const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
     v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
@@ -531,19 +533,20 @@ __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::
   const int R = 1 << logR, C = 1 << logC;
   const int S = rb + 1;
   const int64_t N = (int64_t)R * C;
-  const int blocks_per_vec = R / rb;
-  const int64_t vec = blockIdx.x / blocks_per_vec;
-  const int r0 = (blockIdx.x % blocks_per_vec) * rb;
+  const int lrb = __ffs(rb) - 1;   // rb is a power of two
+  const int blocks_per_vec = R >> lrb;
+  const int64_t vec = blockIdx.x >> (logR - lrb);
+  const int r0 = (blockIdx.x & (blocks_per_vec - 1)) * rb;
   const T* vi = in + vec * N;
   T* vo = out + vec * N;
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
-    const int rr = idx / C, n2 = idx % C;
+    const int rr = idx >> logC, n2 = idx & (C - 1);
     sm[n2 * S + rr] = vi[(int64_t)(r0 + rr) * C + n2];
   }
   __syncthreads();
   smem_dif_il<Ops>(sm, rb, S, logC, tw, R, inv, r4);
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
-    const int rr = idx % rb, k2 = idx / rb;
+    const int rr = idx & (rb - 1), k2 = idx >> lrb;
     vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[bitrev(k2, logC) * S + rr];
   }
 }
@@ -982,6 +985,7 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   const int64_t want = 2 * (int64_t)num_sms();
   while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
   while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
+  if ((cb & (cb - 1)) || (rb & (rb - 1))) return SK_ERR_INVALID_ARG;   // the kernels index by shifts
   const size_t smc = (size_t)(cb + 1) * R * esz, smr = (size_t)(rb + 1) * C * esz;   // padded tiles
   SK_CK(allow_dynamic_smem((const void*)k_xf_cols<Ops>));
   SK_CK(allow_dynamic_smem((const void*)k_xf_rows<Ops>));
