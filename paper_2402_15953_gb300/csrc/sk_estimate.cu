@@ -676,8 +676,9 @@ __global__ void k_split(CorrArgs p) {
   const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t half = 1ll << (p.B - 1), full = 1ll << p.B;
+  const int lM = __ffsll((unsigned long long)p.M) - 1;   // M is a power of two
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.M, j = g % p.M;
+    const int64_t row = g >> lM, j = g & (p.M - 1);
     double2* F = p.F + (row * p.nf) * p.M + j;
     const bool in = j < p.m;
     const int64_t e = row * p.m + j;
@@ -713,8 +714,9 @@ __global__ void k_split(CorrArgs p) {
 __global__ void k_product(CorrArgs p) {
   const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int lM = __ffsll((unsigned long long)p.M) - 1;   // M is a power of two
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.M, k = g % p.M;
+    const int64_t row = g >> lM, k = g & (p.M - 1);
     const int64_t mk = (p.M - k) & (p.M - 1);
     const double2* F = p.F + (row * p.nf) * p.M;
     double2 A[kMaxLimbs], X[kMaxLimbs];
@@ -766,8 +768,10 @@ __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
   const int ns = p.La + p.Lx - 1;
   double worst = 0.0;
   int zb = 0;
+  const bool mp2 = (p.m & (p.m - 1)) == 0;
+  const int lm = __ffsll((unsigned long long)p.m) - 1;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.m, j = g % p.m;
+    const int64_t row = mp2 ? g >> lm : g / p.m, j = g - row * p.m;
     const double2* y = Y + (row * p.ni) * p.M + j;
     I256 z{{0, 0, 0, 0}};
     for (int s = 0; s < ns; s++) {
@@ -817,8 +821,9 @@ __global__ void k_nsplit(NttArgs p) {
   const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t half = 1ll << (p.B - 1), full = 1ll << p.B;
+  const int lM = __ffsll((unsigned long long)p.M) - 1;   // M is a power of two
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.M, j = g % p.M;
+    const int64_t row = g >> lM, j = g & (p.M - 1);
     uint64_t* F = p.F + (row * p.nl) * p.M + j;
     const bool in = j < p.m;
     const int64_t e = row * p.m + j;
@@ -847,8 +852,9 @@ __global__ void k_nsplit(NttArgs p) {
 __global__ void k_nproduct(NttArgs p) {
   const int64_t total = (int64_t)p.d * p.M;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int lM = __ffsll((unsigned long long)p.M) - 1;   // M is a power of two
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.M, k = g % p.M;
+    const int64_t row = g >> lM, k = g & (p.M - 1);
     const int64_t mk = (p.M - k) & (p.M - 1);
     const uint64_t* F = p.F + (row * p.nl) * p.M;
     uint64_t A[kMaxLimbs], X[kMaxLimbs];
@@ -870,8 +876,10 @@ __global__ void k_nrecombine(NttArgs p, const uint64_t* __restrict__ Y) {
   const bool warp_rows = (p.m & 31) == 0;
   const bool padded = p.M != p.m;
   int zb = 0;
+  const bool mp2 = (p.m & (p.m - 1)) == 0;
+  const int lm = __ffsll((unsigned long long)p.m) - 1;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / p.m, j = g % p.m;
+    const int64_t row = mp2 ? g >> lm : g / p.m, j = g - row * p.m;
     const uint64_t* y = Y + (row * p.ns) * p.M + j;
     I256 z{{0, 0, 0, 0}};
     for (int s = 0; s < p.ns; s++) {
@@ -1322,11 +1330,14 @@ double fu_row_bits(const double* l1, const double* l2, int r, int64_t stride, bo
 template <int PI>
 __global__ void k_fu_load(const int64_t* const* rel, int r, int d, int64_t m, uint32_t r2, uint32_t r3, uint32_t* out) {
   using O = MontOps<PI>;
-  const int64_t dm = (int64_t)d * m, total = (int64_t)r * dm;
+  const int64_t dm = (int64_t)d * m;
   const uint32_t p = c_fu_p[PI];
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t c = rel[g / dm][g % dm];
+  const int k = blockIdx.y;            // relation: its d x m counters are contiguous
+  const int64_t* src = rel[k];
+  out += (int64_t)k * dm;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < dm; g += step) {
+    const int64_t c = src[g];
     const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
     uint32_t h = (uint32_t)(mag >> 32);
     if (h >= p) h -= p;
@@ -1383,7 +1394,8 @@ sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, ui
   const uint64_t p = fp.p;
   const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
   const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
-  k_fu_load<PI><<<grid_for((int64_t)r * d * M), 256, 0, st>>>(s->d_fu_rel, r, d, M, fp.r2, fp.r3, V);
+  k_fu_load<PI><<<dim3((unsigned)std::max(1, grid_for((int64_t)r * d * M) / r), (unsigned)r), 256, 0, st>>>(
+      s->d_fu_rel, r, d, M, fp.r2, fp.r3, V);
   count_launch();
   SK_CK(cudaGetLastError());
   sk_status fs = xform<MontOps<PI>>(V, W, (int64_t)r * d, M, tw, false, r4, st);
@@ -1647,8 +1659,9 @@ __global__ void k_crt_leaf(const int64_t* __restrict__ c, int d, int64_t m, int6
   using O = MontOps<PI>;
   const uint32_t p = c_fu_p[PI];
   const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  const int lM = __ffsll((unsigned long long)M) - 1;   // M is a power of two
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / M, j = g - row * M;
+    const int64_t row = g >> lM, j = g - row * M;
     uint32_t v = 0;
     if (j < m) {
       const int64_t x = c[row * m + j];
@@ -1676,8 +1689,9 @@ __global__ void k_crt_product(const uint32_t* __restrict__ A, uint32_t* __restri
                               uint32_t minv) {
   using O = MontOps<PI>;
   const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  const int lM = __ffsll((unsigned long long)M) - 1;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / M, k = g - row * M;
+    const int64_t row = g >> lM, k = g - row * M;
     X[g] = O::mul(O::mul(A[row * M + ((M - k) & (M - 1))], X[g]), minv);
   }
 }
@@ -1687,8 +1701,9 @@ __global__ void k_crt_product(const uint32_t* __restrict__ A, uint32_t* __restri
 template <int PI>
 __global__ void k_crt_fold(const uint32_t* __restrict__ L, uint32_t* __restrict__ x, int d, int64_t m, int64_t M) {
   const int64_t total = (int64_t)d * M, step = (int64_t)gridDim.x * blockDim.x;
+  const int lM = __ffsll((unsigned long long)M) - 1;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
-    const int64_t row = g / M, j = g - row * M;
+    const int64_t row = g >> lM, j = g - row * M;
     x[g] = j < m ? MontOps<PI>::add(L[g], L[row * M + M - m + j]) : 0u;
   }
 }
