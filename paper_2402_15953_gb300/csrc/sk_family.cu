@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t attr_row(const UpdArgs& p, const uint64_t* c
   if (narrow) {
     const uint32_t x32 = (uint32_t)x;
     const uint64_t v = mac_narrow(cr[1], x32, cr[0]);
-    h = POW2 ? (uint32_t)v + mersenne_q1(v) : (uint32_t)(reduce_lazy(v) % p.m);
+    h = POW2 ? (uint32_t)v + mersenne_q1(v) : (uint32_t)mod_m(reduce_lazy(v), p.m, p.mrec);
     for (int e = 0; e < nsl; e++) {
       const uint64_t* sc = cr + 2 + 4 * e;
       uint64_t acc = mac_narrow(sc[3], x32, sc[2]);
@@ -59,7 +59,7 @@ __device__ __forceinline__ uint32_t attr_row(const UpdArgs& p, const uint64_t* c
     }
   } else {
     const uint64_t hv = addmod(mulmod(cr[1], x), cr[0]);
-    h = POW2 ? (uint32_t)hv : (uint32_t)(hv % p.m);
+    h = POW2 ? (uint32_t)hv : (uint32_t)mod_m(hv, p.m, p.mrec);
     for (int e = 0; e < nsl; e++) {
       const uint64_t* sc = cr + 2 + 4 * e;
       uint64_t acc = sc[3];
@@ -520,6 +520,7 @@ sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_row
   a.a = fr.a;
   for (int t = 0; t < kMaxAttrs; t++) a.deg[t] = t < fr.a ? (int)fr.slot_join[t].size() : 0;
   a.m = (uint64_t)fam->m;
+  a.mrec = ~0ull / a.m;
   a.has_dom = domain_hint != nullptr;
   for (int t = 0; t < kMaxAttrs; t++) a.dom[t] = (domain_hint && t < fr.a) ? domain_hint[t] : 0;
   a.status = fam->d_status;

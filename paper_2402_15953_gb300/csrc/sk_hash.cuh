@@ -20,6 +20,7 @@ struct UpdArgs {
   int a;
   int deg[kMaxAttrs];
   uint64_t m;
+  uint64_t mrec;             // floor((2^64 - 1) / m), for reductions mod m when m is not a power of two
   int has_dom;
   int64_t dom[kMaxAttrs];
   int* status;
@@ -104,9 +105,19 @@ __device__ __forceinline__ int64_t ld_key_stream(const int64_t* ptr) {
   return v;
 }
 
+// v mod m for any v < 2^64 and m >= 1, with mrec = floor((2^64 - 1) / m): the quotient
+// estimate hi64(v mrec) lies between floor(v / m) - 2 and floor(v / m), so at most two
+// subtractions of m give the remainder exactly (no division instruction sequence).
+__device__ __forceinline__ uint64_t mod_m(uint64_t v, uint64_t m, uint64_t mrec) {
+  uint64_t r = v - __umul64hi(v, mrec) * m;
+  if (r >= m) r -= m;
+  if (r >= m) r -= m;
+  return r;
+}
+
 template <bool POW2>
-__device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m) {
-  return POW2 ? (v & (m - 1)) : (v % m);
+__device__ __forceinline__ uint64_t reduce_m(uint64_t v, uint64_t m, uint64_t mrec) {
+  return POW2 ? (v & (m - 1)) : mod_m(v, m, mrec);
 }
 
 // A = number of attributes when known at compile time (1..4), 0 = runtime a.
@@ -165,7 +176,7 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
         if (POW2) {
           bin32 += (uint32_t)v + mersenne_q1(v);   // == h(x) mod 2^32
         } else {
-          bin += reduce_lazy(v) % p.m;
+          bin += mod_m(reduce_lazy(v), p.m, p.mrec);
         }
         off += 2;
         const int deg = DEG1 ? 1 : p.deg[u];
@@ -186,7 +197,7 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
         if (A == 0 && u >= na) break;
         const uint64_t xu = x[u];
         const uint64_t h = addmod(mulmod(cr[off + 1], xu), cr[off]);
-        bin += reduce_m<POW2>(h, p.m);
+        bin += reduce_m<POW2>(h, p.m, p.mrec);
         off += 2;
         const int deg = DEG1 ? 1 : p.deg[u];
         for (int e = 0; e < deg; e++, off += 4) {
@@ -198,7 +209,7 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
         }
       }
     }
-    bin = reduce_m<POW2>(bin, p.m);
+    bin = reduce_m<POW2>(bin, p.m, p.mrec);
     const int64_t v = sbit ? -delta : delta;
     if (AGG) {
       const unsigned lane = threadIdx.x & 31u;
@@ -248,7 +259,7 @@ __device__ __forceinline__ uint32_t key_row_hash(const UpdArgs& p, const uint64_
   const uint64_t v = mac_narrow(bc.y, x, bc.x);
   uint32_t h;
   if (POW2) h = ((uint32_t)v + mersenne_q1(v)) & (uint32_t)(p.m - 1);
-  else h = (uint32_t)(reduce_lazy(v) % p.m);
+  else h = (uint32_t)mod_m(reduce_lazy(v), p.m, p.mrec);
   uint32_t sx = 0;
   if (DEG1) deg = 1;
   for (int k = 0; k < deg; k++) {

@@ -190,6 +190,7 @@ sk_status plan_build(sk_update_plan* pl) {
     a.a = rp.a;
     for (int t = 0; t < kMaxAttrs; t++) a.deg[t] = rp.deg[t];
     a.m = (uint64_t)s->m;
+    a.mrec = ~0ull / a.m;
     a.has_dom = 0;
     a.status = s->d_status;
     a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(cfg.chunk_tuples, 1);

@@ -460,6 +460,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
   a.a = rp.a;
   for (int t = 0; t < kMaxAttrs; t++) a.deg[t] = rp.deg[t];
   a.m = (uint64_t)s->m;
+  a.mrec = ~0ull / a.m;
   a.has_dom = domain != nullptr;
   for (int t = 0; t < kMaxAttrs; t++) a.dom[t] = (domain && t < rp.a) ? domain[t] : 0;
   a.status = s->d_status;
