@@ -420,7 +420,7 @@ def run_ours(args, world, rank, local):
         extra = {"roofline_l2": {"bound": "l2_tag_lookups", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
                                  "unit": "G lookups/s", "frac": l2_rate / l2_peak,
                                  "per_tuple": l2_req_per_tuple, "kernel": kernel,
-                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 84 % of peak"}}
+                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 82.5 % of peak"}}
     else:
         # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
         # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the
