@@ -426,18 +426,21 @@ def run_ours(args, world, rank, local):
         # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the
         # step rate of the same arithmetic without loads, atomics or combination (6.4 steps
         # per clock per SM measured) x 152 SMs x 2.07 GHz.  traffic: DRAM bytes of one ncu
-        # capture of k_update (2e7-row launch: 808.5 MB), scaled to this launch's row count.
+        # capture of k_update (2e7-row launch: 808.2 MB), scaled to this launch's row count.
         steps_per_s = args.fact_rows * mulmods_per_fact_tuple / fact_s
         alu_peak_steps = 6.4 * 152 * 2.07e9
-        traffic = 808.5e6 * args.fact_rows / 2e7 / 1e9
+        traffic = 808.2e6 * args.fact_rows / 2e7 / 1e9
         roofline = {"bound": "alu", "achieved": steps_per_s / 1e9, "peak": alu_peak_steps / 1e9, "unit": "Gstep/s",
                     "frac": steps_per_s / alu_peak_steps, "traffic": traffic,
-                    "kernel": "k_update<5,pow2,global> (fact table F)",
+                    "kernel": "k_update<5,pow2,global,DEG1> (fact table F)",
                     "work": f"{mulmods_per_fact_tuple} GF(2^61-1) Horner steps per fact tuple",
                     "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled)"}
         extra = {"roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                                   "frac": achieved_gbs / hbm_peak, "traffic": traffic, "traffic_unit": "GB per launch",
                                   "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}}
+    # counter updates of the fact table (one per row and tuple), as a rate over the same call
+    extra["counter_updates"] = {"per_tuple": wl.d, "achieved": wl.d * args.fact_rows / fact_s / 1e9,
+                                "unit": "G updates/s", "kind": "red.global.add.u64 into the L2-resident sketch"}
 
     serial = {"ms_per_step": ms_per_step, "value": value, "gpu_launches": launches}
     if pipe is not None and pipe["value"] > value:
