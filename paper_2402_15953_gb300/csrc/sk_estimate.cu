@@ -2197,31 +2197,66 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   };
   std::vector<double> l1, l2;
   std::vector<uint32_t> res((size_t)nout * kFuMaxPrimes);
+  // per set: the primes its own rows' bound needs; sets are then ordered by that count,
+  // largest first, so that prime i only loads, transforms and reduces the leading sets
+  // that need more than i primes
+  const int nset = (int)idx.size();
+  std::vector<int> set_np(nset, 0), order;
+  std::vector<int64_t> nvec_at(kFuMaxPrimes, 0);
+  std::vector<int> nout_at(kFuMaxPrimes, 0);
   int np = 0;
   do {
     cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), nvec * sizeof(void*), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_outs, outs.data(), nout * sizeof(FuOut), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
     const sk_status ls = fu_norms(d_rows, 1, nvec, M, d_l1, l1ch, l1, l2, st);
     if (ls != SK_OK) { fail(ls); break; }
-    double bits = 0.0;
-    for (const FuOut& f : outs)
-      bits = std::max(bits, fu_row_bits(&l1[f.base + f.row], &l2[f.base + f.row], f.r, f.d, true));
-    double cover = 0.0;
-    while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
-    if (cover < bits + 3.0) { np = 0; break; }   // left to the per-set estimates
+    int o = 0;
+    for (int t = 0; t < nset; t++) {
+      const sk_set* s = sets[idx[t]];
+      double bits = 0.0;
+      for (int row = 0; row < s->d; row++, o++)
+        bits = std::max(bits, fu_row_bits(&l1[outs[o].base + row], &l2[outs[o].base + row], s->r, s->d, true));
+      int k = 0;
+      double cover = 0.0;
+      while (k < kFuMaxPrimes && cover < bits + 3.0) cover += pr[k++].log2p;
+      set_np[t] = cover < bits + 3.0 ? 0 : k;   // 0: beyond nine primes, left to the caller
+      if (set_np[t] > 0) order.push_back(t);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return set_np[x] > set_np[y]; });
+    if (order.empty()) break;
+    np = set_np[order[0]];
+    // rows and outputs again in that order
+    std::vector<const int64_t*> rows2;
+    std::vector<FuOut> outs2;
+    for (int t : order) {
+      const sk_set* s = sets[idx[t]];
+      unsigned long long negmask = 0;
+      fu_eligible(s, &negmask);
+      const int64_t base = (int64_t)rows2.size();
+      for (int k = 0; k < s->r; k++)
+        for (int row = 0; row < s->d; row++) rows2.push_back(s->rel_ctr[k] + (int64_t)row * M);
+      for (int row = 0; row < s->d; row++) outs2.push_back({base, s->r, s->d, row, negmask});
+      for (int i = 0; i < set_np[t]; i++) {
+        nvec_at[i] = (int64_t)rows2.size();
+        nout_at[i] = (int)outs2.size();
+      }
+    }
+    e = cudaMemcpyAsync(d_rows, rows2.data(), rows2.size() * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_outs, outs2.data(), outs2.size() * sizeof(FuOut), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { fail(set_status_from_cuda(e)); break; }
     for (int i = 0; i < np && status == SK_OK; i++) {
+      const int64_t nv = nvec_at[i];
+      const int no = nout_at[i];
       sk_status ps;
       switch (i) {
-        case 0: ps = fu_group_pass<0>(pr[0], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 1: ps = fu_group_pass<1>(pr[1], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 2: ps = fu_group_pass<2>(pr[2], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 3: ps = fu_group_pass<3>(pr[3], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 4: ps = fu_group_pass<4>(pr[4], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 5: ps = fu_group_pass<5>(pr[5], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 6: ps = fu_group_pass<6>(pr[6], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        case 7: ps = fu_group_pass<7>(pr[7], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
-        default: ps = fu_group_pass<8>(pr[8], M, d_rows, nvec, d_outs, nout, d_tw, V, W, d_part, nchunk, d_res, st); break;
+#define SK_GP_CASE(I)                                                                                     \
+  case I:                                                                                                 \
+    ps = fu_group_pass<I>(pr[I], M, d_rows, nv, d_outs, no, d_tw, V, W, d_part, nchunk, d_res, st);        \
+    break;
+        SK_GP_CASE(0) SK_GP_CASE(1) SK_GP_CASE(2) SK_GP_CASE(3) SK_GP_CASE(4) SK_GP_CASE(5) SK_GP_CASE(6)
+        SK_GP_CASE(7) default: SK_GP_CASE(8)
+#undef SK_GP_CASE
       }
       fail(ps);
     }
@@ -2235,16 +2270,17 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
   if (ef != cudaSuccess) return set_status_from_cuda(ef);
   if (np == 0) return SK_OK;
   int o = 0;
-  for (int i : idx) {
+  for (int t : order) {
+    const int i = idx[t];
     sk_set* s = sets[i];
     I256 r_rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
     for (int row = 0; row < s->d; row++, o++)
-      if (!fu_crt(res.data() + (size_t)o * kFuMaxPrimes, np, pr, &r_rows[row])) return SK_ERR_OVERFLOW;
+      if (!fu_crt(res.data() + (size_t)o * kFuMaxPrimes, set_np[t], pr, &r_rows[row])) return SK_ERR_OVERFLOW;
     std::memcpy(sorted, r_rows, sizeof(I256) * s->d);
     std::sort(sorted, sorted + s->d, [](const I256& a, const I256& b) { return i256_lt(a, b); });
     fill_estimate(&out[i], r_rows, sorted, s->d);
     out[i].max_residual = 0.0;
-    out[i].max_limbs = np;
+    out[i].max_limbs = set_np[t];
     out[i].limb_bits = 0;
     out[i].corr_steps = s->corr_steps;
     out[i].retries = 0;

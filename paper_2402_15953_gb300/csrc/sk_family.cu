@@ -545,6 +545,16 @@ sk_status sk_family_estimate(sk_family* fam, sk_estimate* out, void* cuda_stream
   const int n = (int)fam->sub.size();
   std::memset(out, 0, sizeof(sk_estimate) * n);
   cudaStream_t caller = (cudaStream_t)cuda_stream;
+  // Fused estimator throughout: the sub-queries go to the many-set estimate, which
+  // transforms the rows of all sub-queries of one width together (chains and stars; the
+  // others run on its worker streams).
+  bool all_fused = n > 0;
+  for (const auto& sq : fam->sub) all_fused = all_fused && sq.est->estimator == SK_ESTIMATOR_FUSED;
+  if (all_fused) {
+    std::vector<sk_set*> v(n);
+    for (int i = 0; i < n; i++) v[i] = fam->sub[i].est;
+    return run_estimate_many(v.data(), n, out, caller);
+  }
   cudaEvent_t ready;
   cudaError_t ce = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
   if (ce != cudaSuccess) return set_status_from_cuda(ce);
