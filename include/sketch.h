@@ -349,8 +349,9 @@ sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t c
  * 8 * m bytes.
  *
  * sk_server_create: update_slots in-flight update batches (>= 1), estimate_workers
- *   concurrent estimates (1..64), estimate streams at the device's highest priority
- *   when estimate_priority != 0.
+ *   estimate threads and streams (1..64), each running up to 8 admitted estimates of
+ *   distinct sets together (as sk_estimate_many), estimate streams at the device's
+ *   highest priority when estimate_priority != 0.
  * sk_server_register_set: makes `set` (created and owned by the caller, alive until
  *   sk_server_destroy) a live set named set_id; SK_ERR_OVER_BUDGET when its counters
  *   do not fit.  Sets must not be updated or estimated outside the server meanwhile.

@@ -14,7 +14,10 @@
 //  - Updates: the host columns are copied into a stream-ordered staging buffer on the
 //    copy stream; the update runs on the update stream after that copy; an event marks
 //    its end and the set's last admitted update.  Estimates: one worker thread per
-//    estimate stream; the stream first waits for the set's last update.
+//    estimate stream takes up to kEstBatch admitted estimates at a time (of distinct
+//    sets: a set has one admitted estimate at most), its stream waits for each set's
+//    last update, and one many-set estimate runs them (fused sets of one width share
+//    their transforms).
 //  - A retire thread waits on the oldest in-flight update's event (updates complete in
 //    launch order on the single update stream) and releases its slot and memory; the
 //    scheduler sleeps on a condition variable until a submission, a retired update or a
@@ -40,6 +43,7 @@ using sk::set_status_from_cuda;
 
 namespace {
 
+constexpr int kEstBatch = 8;   // estimates a worker runs together
 struct SvRequest {
   int64_t id = 0;
   bool is_estimate = false;
@@ -213,24 +217,44 @@ void retirer(sk_server* sv) {
 void estimator(sk_server* sv, cudaStream_t stream) {
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
+  std::vector<SvRequest*> batch;
+  std::vector<sk_set*> sets;
+  std::vector<cudaEvent_t> waits;
+  std::vector<sk_estimate> outs;
   for (;;) {
     sv->est_cv.wait(lk, [&] { return !sv->est_queue.empty() || sv->stop; });
     if (sv->est_queue.empty()) return;
-    SvRequest* q = sv->est_queue.front();
-    sv->est_queue.pop_front();
-    SvSet& ss = sv->sets[q->set_id];
-    sk_set* s = ss.set;
-    const bool wait = ss.has_update;
-    cudaEvent_t last = ss.last_update;
+    batch.clear();
+    sets.clear();
+    waits.clear();
+    while (!sv->est_queue.empty() && (int)batch.size() < kEstBatch) {
+      SvRequest* q = sv->est_queue.front();
+      sv->est_queue.pop_front();
+      SvSet& ss = sv->sets[q->set_id];
+      batch.push_back(q);
+      sets.push_back(ss.set);
+      if (ss.has_update) waits.push_back(ss.last_update);
+    }
     lk.unlock();
     sk_status st = SK_OK;
-    if (wait) st = set_status_from_cuda(cudaStreamWaitEvent(stream, last, 0));
-    if (st == SK_OK) st = sk_estimate_join(s, &q->est, stream);
+    for (cudaEvent_t ev : waits)
+      if (st == SK_OK) st = set_status_from_cuda(cudaStreamWaitEvent(stream, ev, 0));
+    if (st == SK_OK) {
+      if (batch.size() == 1) {
+        st = sk_estimate_join(sets[0], &batch[0]->est, stream);
+      } else {
+        outs.assign(batch.size(), sk_estimate());
+        st = sk::run_estimate_many(sets.data(), (int)sets.size(), outs.data(), stream);
+        for (size_t i = 0; i < batch.size(); i++) batch[i]->est = outs[i];
+      }
+    }
     lk.lock();
-    ss.estimating = false;
-    sv->est_free++;
-    sv->used -= q->bytes;
-    finish(sv, q, st);
+    for (SvRequest* q : batch) {
+      sv->sets[q->set_id].estimating = false;
+      sv->est_free++;
+      sv->used -= q->bytes;
+      finish(sv, q, st);
+    }
     sv->cv.notify_all();
   }
 }
@@ -248,7 +272,7 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
   if (!sv) return SK_ERR_NO_MEMORY;
   sv->budget = (size_t)hbm_budget_bytes;
   sv->slots = update_slots;
-  sv->est_free = estimate_workers;
+  sv->est_free = estimate_workers * kEstBatch;
   sv->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&sv->device);
   int lo = 0, hi = 0;
