@@ -322,6 +322,7 @@ __host__ __device__ __forceinline__ uint64_t gl_pow(uint64_t b, uint64_t e) {
 // ---------------------------------------------------------------------------
 struct CplxOps {
   using T = double2;
+  static constexpr bool kExact = false;   // rounding: twiddles always come from the table
   static __device__ __forceinline__ T mul(T a, T b) { return cmul(a, b); }
   static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -339,6 +340,7 @@ struct CplxOps {
 
 struct GlOps {
   using T = uint64_t;
+  static constexpr bool kExact = true;
   static __device__ __forceinline__ T mul(T a, T b) { return gl_mul(a, b); }
   static __device__ __forceinline__ T add(T a, T b) { return gl_add(a, b); }
   static __device__ __forceinline__ T sub(T a, T b) { return gl_sub(a, b); }
@@ -514,11 +516,25 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
   __syncthreads();
   smem_dif_il<Ops>(sm, cb, S, logR, tw, C, inv, r4);
   const int64_t half = N >> 1;
-  for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
-    const int c = idx & (cb - 1), k1 = idx >> lcb;
+  if (Ops::kExact && (blockDim.x & (cb - 1)) == 0) {
+    // each thread keeps one column n2 and walks rows k1 = k1_0 + j kstep: the twiddle
+    // w^(n2 k1) advances by the factor w^(n2 kstep) (exact modular products), instead of a
+    // table load per element at the scattered index n2 k1
+    const int c = threadIdx.x & (cb - 1), kstep = blockDim.x >> lcb;
     const int64_t n2 = c0 + c;
-    const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
-    v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
+    T w = twid<Ops>(tw, (n2 * (threadIdx.x >> lcb)) & (N - 1), half, inv);
+    const T ws = twid<Ops>(tw, (n2 * kstep) & (N - 1), half, inv);
+    for (int k1 = threadIdx.x >> lcb; k1 < R; k1 += kstep) {
+      v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
+      w = Ops::mul(w, ws);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
+      const int c = idx & (cb - 1), k1 = idx >> lcb;
+      const int64_t n2 = c0 + c;
+      const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
+      v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
+    }
   }
 }
 
@@ -1208,6 +1224,7 @@ __device__ __forceinline__ uint32_t mont32(uint32_t a, uint32_t b, uint32_t p, u
 template <int PI>
 struct MontOps {
   using T = uint32_t;
+  static constexpr bool kExact = true;
   static __device__ __forceinline__ T mul(T a, T b) { return mont32(a, b, c_fu_p[PI], c_fu_pinv[PI]); }
   static __device__ __forceinline__ T add(T a, T b) {
     const uint32_t p = c_fu_p[PI], s = a + b;
