@@ -231,8 +231,9 @@ sk_status sk_estimate_join(sk_set* set, sk_estimate* out, void* cuda_stream);
  * sk_estimate_many: sk_estimate_join for n distinct sets in one call; out[i] is
  * set i's estimate, identical to what sk_estimate_join would give.  Sets using
  * SK_ESTIMATOR_FUSED whose queries qualify are grouped by width and estimated
- * together (per CRT prime: one load, one batch of transforms and one product-sum
- * over all their relations' rows); the others are estimated concurrently on
+ * together (each set takes the number of CRT primes its own bound needs; per prime:
+ * one load, one batch of transforms and one product-sum over the rows of every set
+ * that needs that prime); the others are estimated concurrently on
  * internal worker streams (SK_MANY_WORKERS, default 4), which first wait for the
  * work already queued on cuda_stream, and cuda_stream continues after them.  The
  * call returns when every estimate is on the host; grouped work takes one
@@ -448,9 +449,11 @@ sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_row
                                  void* cuda_stream);
 
 /* sk_family_estimate: Algorithm 3 and the median for every sub-query; out has
- * n_sub entries, entry i for sub-query i (as sk_estimate_join).  The sub-queries
- * are estimated concurrently on the family's worker streams, which first wait
- * for the work already queued on cuda_stream; the call returns when every
+ * n_sub entries, entry i for sub-query i (as sk_estimate_join).  With
+ * SK_ESTIMATOR_FUSED on every sub-query they are estimated as sk_estimate_many
+ * does (qualifying sub-queries of one width transformed together); otherwise
+ * concurrently on the family's worker streams.  Either way the work starts after
+ * the work already queued on cuda_stream, and the call returns when every
  * estimate is on the host.  Returns the first error of any sub-query.
  * Errors: as sk_estimate_join. */
 sk_status sk_family_estimate(sk_family* fam, sk_estimate* out, void* cuda_stream);
