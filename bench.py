@@ -57,7 +57,8 @@ def parse_args():
     ap.add_argument("--estimate-priority", default="high", choices=["high", "normal"],
                     help="stream priority of the estimates that overlap the next step's update")
     ap.add_argument("--plan-config", default=None,
-                    help="batched workload: chunk_tuples,threads,ctas_per_sm,smem_max_counters instead of autotuning")
+                    help="batched workload: chunk_tuples,threads,ctas_per_sm,smem_max_counters[,smem16_max_counters] "
+                         "instead of autotuning")
     ap.add_argument("--estimator", default="fused", choices=["fft64", "ntt", "fused"],
                     help="exact estimator arithmetic of the star step (identical rows from each)")
     ap.add_argument("--no-pipeline", action="store_true",

@@ -173,9 +173,13 @@ sk_status sk_sketch_update_batch(sk_set* set, int32_t relation, int64_t n_rows, 
  *
  * sk_update_plan_config: chunk_tuples (tuples per work item), threads (per CTA),
  * ctas_per_sm, smem_max_counters (items with d*m at most this, and at most 40960,
- * use a per-chunk int32 shared-memory sub-sketch; 0 = never).  sk_update_plan_autotune times a set
- * of configurations on the plan itself (every timed run updates the counters:
- * reset them afterwards) and keeps the fastest.
+ * use a per-chunk int32 shared-memory sub-sketch; 0 = never), smem16_max_counters
+ * (other items with d*m at most this, and at most 81920, use a per-chunk sub-sketch
+ * of 16-bit counters, two per 32-bit word, each biased by 2^15; only tuples with
+ * |Delta| <= 32767 / chunk_tuples go there, so no counter leaves [0, 2^16) within a
+ * chunk and the packed adds are exact; the others update global memory; 0 = never).
+ * sk_update_plan_autotune times a set of configurations on the plan itself (every
+ * timed run updates the counters: reset them afterwards) and keeps the fastest.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
 typedef struct {
   sk_set* set;
@@ -191,6 +195,7 @@ typedef struct {
   int32_t threads;
   int32_t ctas_per_sm;
   int32_t smem_max_counters;
+  int32_t smem16_max_counters;
 } sk_update_plan_config;
 
 typedef struct sk_update_plan sk_update_plan;

@@ -73,7 +73,7 @@ class sk_update_item(ctypes.Structure):
 
 class sk_update_plan_config(ctypes.Structure):
     _fields_ = [("chunk_tuples", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("smem_max_counters", ctypes.c_int32)]
+                ("smem_max_counters", ctypes.c_int32), ("smem16_max_counters", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -285,8 +285,8 @@ def sk_update_plan_get_config(plan: int) -> sk_update_plan_config:
 
 
 def sk_update_plan_set_config(plan: int, chunk_tuples: int, threads: int, ctas_per_sm: int,
-                              smem_max_counters: int) -> None:
-    c = sk_update_plan_config(chunk_tuples, threads, ctas_per_sm, smem_max_counters)
+                              smem_max_counters: int, smem16_max_counters: int = 0) -> None:
+    c = sk_update_plan_config(chunk_tuples, threads, ctas_per_sm, smem_max_counters, smem16_max_counters)
     _check(load().sk_update_plan_set_config(plan, ctypes.byref(c)), "sk_update_plan_set_config")
 
 
@@ -414,8 +414,10 @@ class UpdatePlan:
     def config(self) -> dict:
         return sk_update_plan_get_config(self.handle).as_dict()
 
-    def set_config(self, chunk_tuples: int, threads: int, ctas_per_sm: int, smem_max_counters: int) -> None:
-        sk_update_plan_set_config(self.handle, chunk_tuples, threads, ctas_per_sm, smem_max_counters)
+    def set_config(self, chunk_tuples: int, threads: int, ctas_per_sm: int, smem_max_counters: int,
+                   smem16_max_counters: int = 0) -> None:
+        sk_update_plan_set_config(self.handle, chunk_tuples, threads, ctas_per_sm, smem_max_counters,
+                                  smem16_max_counters)
 
     def autotune(self):
         return sk_update_plan_autotune(self.handle, self._stream())

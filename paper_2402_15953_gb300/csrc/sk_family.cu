@@ -526,6 +526,7 @@ sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_row
   a.status = fam->d_status;
   a.smem_wmax = 0;
   a.agg = 0;
+  a.s16 = 0;
   ViewArgs v;
   v.nv = (int)fr.amask.size();
   for (int i = 0; i < v.nv; i++) {

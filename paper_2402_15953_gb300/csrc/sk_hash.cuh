@@ -26,6 +26,7 @@ struct UpdArgs {
   int* status;
   int64_t smem_wmax;         // |Delta| <= smem_wmax goes to the int32 sub-sketch
   int agg;                   // warp-aggregate shared-memory counter updates
+  int s16;                   // shared sub-sketch of biased 16-bit counters, two per 32-bit word
 };
 
 __device__ __forceinline__ uint64_t field_of(int64_t key) {
@@ -219,7 +220,13 @@ __device__ __forceinline__ void update_tuple(const UpdArgs& p, const uint64_t* s
       if (small && lane == (unsigned)(__ffs(same) - 1) && sum != 0) atomicAdd(s_sub + key, sum);
       if (!small && v != 0) red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
     } else if (SMEM && small) {
-      atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
+      if (p.s16) {   // counter j in half (j & 1) of word j / 2; the bias keeps it from carrying
+        const int64_t j = (int64_t)row * p.m + bin;
+        const uint32_t add = (uint32_t)(int32_t)v << (16 * (uint32_t)(j & 1));
+        atomicAdd((unsigned int*)s_sub + (j >> 1), add);
+      } else {
+        atomicAdd(s_sub + (int64_t)row * p.m + bin, (int)v);
+      }
     } else {
       red_add_global(p.ctr + (int64_t)row * p.m + bin, (unsigned long long)v);
     }

@@ -3,7 +3,8 @@
 // tuples from a device work counter in item order; a CTA reloads an item's hash
 // coefficients and arguments into shared memory only when it moves to another item.  Items with
 // a small d x m accumulate each chunk in an int32 shared-memory sub-sketch that is
-// flushed into the int64 counters at the end of the chunk.
+// flushed into the int64 counters at the end of the chunk; items up to twice as large
+// can use 16-bit counters packed two per word instead (see sk_update_plan_config).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -24,14 +25,14 @@ struct MultiItem {
   UpdArgs args;
   int64_t chunk0;   // first global chunk of this item
   int pow2;
-  int use_smem;
+  int use_smem;     // 0 global counters, 1 int32 shared sub-sketch, 2 packed 16-bit one
   int deg1;         // every attribute in exactly one join
 };
 
 template <int A, bool POW2, bool DEG1>
-__device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
+__device__ __forceinline__ void multi_chunk(const UpdArgs& p, int use_smem, const uint64_t* s_coef, int* s_sub,
                                             int64_t t0, int64_t t1) {
-  if (use_smem) {
+  if (use_smem == 1) {
     const int64_t dm = (int64_t)p.d * (int64_t)p.m;
     for (int64_t j = threadIdx.x; j < dm; j += blockDim.x) s_sub[j] = 0;
     __syncthreads();
@@ -42,6 +43,21 @@ __device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, con
       const int v = s_sub[j];
       if (v != 0) red_add_global(p.ctr + j, (unsigned long long)(int64_t)v);
     }
+  } else if (use_smem == 2) {
+    // 16-bit counters biased by 2^15, two per word (counter j in half j & 1 of word j / 2)
+    const int64_t dm = (int64_t)p.d * (int64_t)p.m, words = (dm + 1) >> 1;
+    unsigned int* w = (unsigned int*)s_sub;
+    for (int64_t k = threadIdx.x; k < words; k += blockDim.x) w[k] = 0x80008000u;
+    __syncthreads();
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+      update_tuple<A, POW2, true, false, DEG1>(p, s_coef, s_sub, i);
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < words; k += blockDim.x) {
+      const unsigned int x = w[k];
+      const int lo = (int)(x & 0xffffu) - 32768, hi = (int)(x >> 16) - 32768;
+      if (lo != 0) red_add_global(p.ctr + 2 * k, (unsigned long long)(int64_t)lo);
+      if (hi != 0 && 2 * k + 1 < dm) red_add_global(p.ctr + 2 * k + 1, (unsigned long long)(int64_t)hi);
+    }
   } else {
     for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x)
       update_tuple<A, POW2, false, false, DEG1>(p, s_coef, s_sub, i);
@@ -49,7 +65,7 @@ __device__ __forceinline__ void multi_chunk(const UpdArgs& p, bool use_smem, con
 }
 
 template <bool POW2, bool DEG1>
-__device__ __forceinline__ void multi_dispatch(const UpdArgs& p, bool use_smem, const uint64_t* s_coef, int* s_sub,
+__device__ __forceinline__ void multi_dispatch(const UpdArgs& p, int use_smem, const uint64_t* s_coef, int* s_sub,
                                                int64_t t0, int64_t t1) {
   switch (p.a) {
     case 1: multi_chunk<1, POW2, DEG1>(p, use_smem, s_coef, s_sub, t0, t1); break;
@@ -106,11 +122,11 @@ __global__ void __launch_bounds__(256, 4) k_update_multi(const MultiItem* __rest
     const int64_t t0 = (c - items[it].chunk0) * chunk;
     const int64_t t1 = min(p.n, t0 + chunk);
     if (s_pow2) {
-      if (s_deg1) multi_dispatch<true, true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
-      else multi_dispatch<true, false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+      if (s_deg1) multi_dispatch<true, true>(p, s_smem, s_coef, s_sub, t0, t1);
+      else multi_dispatch<true, false>(p, s_smem, s_coef, s_sub, t0, t1);
     } else {
-      if (s_deg1) multi_dispatch<false, true>(p, s_smem != 0, s_coef, s_sub, t0, t1);
-      else multi_dispatch<false, false>(p, s_smem != 0, s_coef, s_sub, t0, t1);
+      if (s_deg1) multi_dispatch<false, true>(p, s_smem, s_coef, s_sub, t0, t1);
+      else multi_dispatch<false, false>(p, s_smem, s_coef, s_sub, t0, t1);
     }
     __syncthreads();
   }
@@ -193,18 +209,25 @@ sk_status plan_build(sk_update_plan* pl) {
     a.mrec = ~0ull / a.m;
     a.has_dom = 0;
     a.status = s->d_status;
-    a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(cfg.chunk_tuples, 1);
+    a.agg = 0;
     mi.pow2 = (s->m & (s->m - 1)) == 0;
     mi.deg1 = 1;
     for (int t = 0; t < rp.a; t++)
       if (rp.deg[t] != 1) mi.deg1 = 0;
     const int64_t dm = (int64_t)s->d * s->m;
-    // the int32 sub-sketch must also fit in shared memory next to the coefficients
-    mi.use_smem = (cfg.smem_max_counters > 0 && dm <= cfg.smem_max_counters && dm * 4 <= 160 * 1024) ? 1 : 0;
+    // the sub-sketch must also fit in shared memory next to the coefficients
+    const bool fits32 = cfg.smem_max_counters > 0 && dm <= cfg.smem_max_counters && dm * 4 <= 160 * 1024;
+    const bool fits16 = !fits32 && cfg.smem16_max_counters > 0 && dm <= cfg.smem16_max_counters &&
+                        dm * 2 <= 160 * 1024;
+    mi.use_smem = fits32 ? 1 : (fits16 ? 2 : 0);
+    a.s16 = mi.use_smem == 2 ? 1 : 0;
+    // |Delta| below which a tuple goes to the sub-sketch: a chunk's sum per counter then
+    // stays within int32 (1) or within +-32767 (2, the 16-bit halves never carry)
+    a.smem_wmax = (int64_t)(mi.use_smem == 2 ? 0x7fff : 0x7fffffff) / std::max<int64_t>(cfg.chunk_tuples, 1);
     mi.chunk0 = chunk0;
     chunk0 += (it.n_rows + cfg.chunk_tuples - 1) / cfg.chunk_tuples;
     coef_words = std::max(coef_words, s->d * rp.coef_row_len);
-    if (mi.use_smem) sub_words = std::max(sub_words, dm);
+    if (mi.use_smem) sub_words = std::max(sub_words, mi.use_smem == 1 ? dm : (dm + 1) / 2);
     pl->host.push_back(mi);
   }
   pl->n_active = (int)pl->host.size();
@@ -293,7 +316,7 @@ sk_status sk_update_plan_get_config(const sk_update_plan* pl, sk_update_plan_con
 sk_status sk_update_plan_set_config(sk_update_plan* pl, const sk_update_plan_config* c) {
   if (!pl || !c) return SK_ERR_INVALID_ARG;
   if (c->chunk_tuples < 256 || c->threads < 32 || c->threads > 256 || (c->threads & 31) || c->ctas_per_sm < 1 ||
-      c->ctas_per_sm > 32 || c->smem_max_counters < 0)
+      c->ctas_per_sm > 32 || c->smem_max_counters < 0 || c->smem16_max_counters < 0)
     return SK_ERR_INVALID_ARG;
   const sk_update_plan_config old = pl->cfg;
   pl->cfg = *c;
@@ -312,6 +335,7 @@ sk_status sk_update_plan_autotune(sk_update_plan* pl, void* cuda_stream, sk_upda
   const int chunks[] = {8192, 32768, 131072};
   const int ctas[] = {4, 8};
   const int smem[] = {0, 8192, 32768};
+  const int smem16[] = {0, 32768};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SK_ERR_CUDA;
   sk_update_plan_config bestc = pl->cfg;
@@ -319,26 +343,28 @@ sk_status sk_update_plan_autotune(sk_update_plan* pl, void* cuda_stream, sk_upda
   sk_status rs = SK_OK;
   for (int ch : chunks)
     for (int ct : ctas)
-      for (int sm : smem) {
-        sk_update_plan_config c{ch, 256, ct, sm};
-        if (sk_update_plan_set_config(pl, &c) != SK_OK) continue;
-        if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;   // warm-up
-        float total = 0.f;
-        for (int rep = 0; rep < 3; rep++) {
-          cudaEventRecord(e0, st);
-          if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          total += ms;
+      for (int sm : smem)
+        for (int s16 : smem16) {
+          if (s16 && s16 <= sm) continue;   // nothing would use the 16-bit sub-sketch
+          sk_update_plan_config c{ch, 256, ct, sm, s16};
+          if (sk_update_plan_set_config(pl, &c) != SK_OK) continue;
+          if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;   // warm-up
+          float total = 0.f;
+          for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, st);
+            if ((rs = sk_update_plan_run(pl, st)) != SK_OK) break;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+          }
+          if (rs != SK_OK) break;
+          if (total / 3 < bestt) {
+            bestt = total / 3;
+            bestc = c;
+          }
         }
-        if (rs != SK_OK) break;
-        if (total / 3 < bestt) {
-          bestt = total / 3;
-          bestc = c;
-        }
-      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rs != SK_OK) return rs;

@@ -465,6 +465,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
   for (int t = 0; t < kMaxAttrs; t++) a.dom[t] = (domain && t < rp.a) ? domain[t] : 0;
   a.status = s->d_status;
   a.agg = warp_agg_enabled() ? 1 : 0;
+  a.s16 = 0;
   const bool pow2 = (s->m & (s->m - 1)) == 0;
   const size_t coef_bytes = (size_t)s->d * rp.coef_row_len * sizeof(uint64_t);
   const size_t sub_bytes = (size_t)s->d * (size_t)s->m * sizeof(int);

@@ -31,7 +31,10 @@ def test_plan_equals_item_by_item_and_oracle(workload):
         s.update(0, b.relation.cols, b.relation.weights)
     got = _sets(workload)
     plan = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(got, workload)])
-    for cfg in [(32768, 256, 6, 16384), (1024, 128, 2, 0), (4096, 256, 8, 1 << 20)]:
+    # int32 sub-sketches, global counters only, everything in int32 shared memory, and packed
+    # 16-bit sub-sketches (alone and beside int32 ones; chunk 32768 admits only |Delta| = 0)
+    for cfg in [(32768, 256, 6, 16384), (1024, 128, 2, 0), (4096, 256, 8, 1 << 20), (4096, 256, 8, 0, 1 << 20),
+                (8192, 256, 4, 1024, 32768), (32768, 256, 4, 0, 1 << 20)]:
         for s in got:
             s.reset()
         plan.set_config(*cfg)
