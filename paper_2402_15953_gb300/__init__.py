@@ -9,7 +9,9 @@ PyTorch is used for device memory and streams.
 The C functions are exposed under their own names (sk_sketch_create,
 sk_sketch_update_batch, sk_sketch_merge, sk_estimate_join, ...), each raising
 SketchError on a non-zero status; SketchSet wraps a handle together with its
-torch-owned counters.
+torch-owned counters, UpdatePlan a batched plan (sk_update_plan_*), SketchFamily
+a sub-query family (sk_family_*), estimate_many the many-set estimate, and
+serve.SketchServer the native serving loop (sk_server_*).
 """
 from __future__ import annotations
 
