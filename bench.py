@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=4000)
     ap.add_argument("--no-domains", action="store_true",
                     help="do not declare the key domains (every tuple is hashed; no key tables)")
-    ap.add_argument("--estimate-priority", default="high", choices=["high", "normal"],
-                    help="stream priority of the estimates that overlap the next step's update")
+    ap.add_argument("--estimate-priority", default="normal", choices=["high", "normal"],
+                    help="stream priority of the estimates that overlap the next step's update (fused "
+                         "estimator: normal 5.93 vs high 6.09 ms per step; FP64: high 6.89 vs normal 7.71)")
     ap.add_argument("--plan-config", default=None,
                     help="batched workload: chunk_tuples,threads,ctas_per_sm,smem_max_counters[,smem16_max_counters] "
                          "instead of autotuning")
