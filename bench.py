@@ -452,9 +452,8 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic", "estimator": args.estimator,
-        "config": {**star_config(args, total),
-                   "parallelism": f"replicas x{world}",
-                   "pipelined": pipe is not None and value == pipe["value"]},
+        "config": star_config(args, total),
+        "parallelism": f"replicas x{world}", "pipelined": pipe is not None and value == pipe["value"],
         "serial_steps": serial, "pipelined_steps": pipe,
         "estimates_per_s": world * 1e3 / ms_per_step,
         "p50_ms": statistics.median(step_ms), "p99_ms": percentile(step_ms, 99.0),

@@ -221,10 +221,11 @@ sk_status sk_sketch_merge(sk_set* dst, const sk_set* src, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * sk_estimate_join: Algorithm 3 for every median row, then the lower median.
- * Root attribute: attribute 0 of relation 0.  Each circular cross-correlation
- * IFFT(conj(FFT(a)) o FFT(x)) is computed with FP64 FFTs on signed limbs of the
- * exact operands and rounded back to exact integers; Hadamard products and sums
- * are exact signed 256-bit integers.  2 <= m <= 2^22 for a power of two m; any other
+ * Root attribute: attribute 0 of relation 0.  Every row is the exact integer of Eq. 5;
+ * the arithmetic that computes each circular cross-correlation IFFT(conj(FFT(a)) o FFT(x))
+ * exactly is the set's estimator (sk_sketch_set_estimator; default SK_ESTIMATOR_FUSED,
+ * exact by construction); Hadamard products and sums are exact signed 256-bit
+ * integers.  2 <= m <= 2^22 for a power of two m; any other
  * 2 <= m <= 2^21 is handled with zero-padded transforms of the next power of two >= 2m - 1
  * (the circular correlation mod m is the padded linear correlation folded back).
  * Synchronises cuda_stream and fills *out (host memory).
@@ -250,11 +251,17 @@ sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, voi
 /* ---------------------------------------------------------------------------
  * sk_sketch_set_estimator: selects how sk_estimate_join computes each circular
  * cross-correlation (Definition 3.1); all give the identical exact result.
- *   SK_ESTIMATOR_FFT64 (default): FP64 FFTs on signed limbs, outputs rounded to
- *     integers and certified (largest distance to an integer <= 1/4, exact row-sum
- *     identity and, for power-of-two m, Z(w) = A(1/w) X(w) modulo 2^64 - 2^32 + 1 at
- *     a random primitive m-th root of unity w), redone with narrower limbs if the
- *     certificate fails;
+ * Default (sk_sketch_create): SK_ESTIMATOR_FUSED.
+ *   SK_ESTIMATOR_FFT64: the paper's transform, FP64 FFTs on signed limbs, outputs
+ *     rounded to integers.  The limb width comes from a first-order model of the FFT
+ *     rounding error, not from a proven bound, so each step is certified a posteriori
+ *     instead: largest distance to an integer <= 1/4, the exact row-sum identity
+ *     sum z = (sum a)(sum x) mod 2^64 and, for power-of-two m, Z(w) = A(1/w) X(w)
+ *     modulo q = 2^64 - 2^32 + 1 at a random primitive m-th root of unity w; a step
+ *     that fails is redone with narrower limbs.  This certificate is probabilistic:
+ *     a wrong output that keeps its residual and row sums passes the evaluation check
+ *     with probability at most (m - 1) / q per row (for other widths only the residual
+ *     and row-sum checks apply).  The other two arithmetics need no certificate;
  *   SK_ESTIMATOR_NTT: number-theoretic transforms over GF(2^64 - 2^32 + 1) on signed
  *     limbs narrow enough that every output lies below q/2 in magnitude, exact by
  *     construction (GB300's integer pipes are much faster than its FP64 pipe);
@@ -271,18 +278,25 @@ sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, voi
  *     folded back) and recombine the row sums by CRT; only bounds beyond 9 primes
  *     are estimated as with SK_ESTIMATOR_NTT.  In the result, max_limbs is the
  *     number of primes and limb_bits 0.
- * The environment variable SK_ESTIMATOR=ntt (or =fused) selects that arithmetic for
+ * The environment variable SK_ESTIMATOR=ntt (or =fft64) selects that arithmetic for
  * sets created after it is set.  Errors: SK_ERR_INVALID_ARG. */
 enum { SK_ESTIMATOR_FFT64 = 0, SK_ESTIMATOR_NTT = 1, SK_ESTIMATOR_FUSED = 2 };
 sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator);
 
 /* ---------------------------------------------------------------------------
- * sk_estimate_join_noalloc: the same estimate as sk_estimate_join (identical rows,
- * median and diagnostics; always with the FP64 FFT backend), for callers that cannot allocate device memory while
- * they estimate -- e.g. code running in a host callback or driver hook that must
- * not enter the CUDA allocator, a process whose device memory is fully held by
- * another pool, or a latency-critical path that forbids allocation.  No
- * counterpart in the paper.
+ * sk_estimate_join_noalloc: the estimate of sk_estimate_join without any device
+ * allocation, for callers that cannot allocate device memory while they estimate --
+ * e.g. code running in a host callback or driver hook that must not enter the CUDA
+ * allocator, a process whose device memory is fully held by another pool, or a
+ * latency-critical path that forbids allocation.  No counterpart in the paper.
+ * It always uses FP64 FFTs (whatever the set's estimator) with the certificate
+ * described for SK_ESTIMATOR_FFT64 -- residual, exact per-row sums and the evaluation
+ * at a random root of unity, each step redone up to three times with narrower limbs
+ * -- so rows, median, fits_i64, median_i64, median_f64 and mid_mean_f64 equal those of
+ * sk_estimate_join; the diagnostics (max_residual, max_limbs, limb_bits, retries)
+ * describe this call's own arithmetic.  Only power-of-two m (2 <= m <= 2^22) is
+ * accepted; other widths return SK_ERR_UNSUPPORTED_WIDTH.  The set's device must be
+ * the current device (else SK_ERR_INVALID_ARG).
  * It calls no cudaMalloc/cudaFree and no allocating library routine: all scratch
  * lives in one static device array of 32 MiB (SK_NOALLOC_SCRATCH_BYTES) that every
  * GPU loading this library holds until the process exits.  The array's device
@@ -297,7 +311,9 @@ sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator);
  * correlation step (2 * d * ceil(limbs / 2) * m * 16 bytes) must fit in what is
  * left, or the call returns SK_ERR_SCRATCH_TOO_SMALL at that step.
  * Synchronises cuda_stream and fills *out.
- * Errors: those of sk_estimate_join, plus SK_ERR_SCRATCH_TOO_SMALL. */
+ * Errors: SK_ERR_INVALID_ARG, SK_ERR_UNSUPPORTED_WIDTH, SK_ERR_SCRATCH_TOO_SMALL,
+ * SK_ERR_OVERFLOW, SK_ERR_INEXACT, SK_ERR_KEY_OUT_OF_DOMAIN (from earlier updates),
+ * SK_ERR_CUDA. */
 #define SK_NOALLOC_SCRATCH_BYTES (32ull << 20)
 sk_status sk_estimate_join_noalloc(sk_set* set, sk_estimate* out, void* cuda_stream);
 

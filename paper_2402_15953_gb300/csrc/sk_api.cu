@@ -379,9 +379,12 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
     return st;
   }
   build_plan(s);
+  // Default: the fused arithmetic (exact by construction: CRT primes, or Algorithm 3's steps
+  // modulo them; GF(q) steps beyond nine primes).  SK_ESTIMATOR picks another at creation.
+  s->estimator = SK_ESTIMATOR_FUSED;
   const char* ev = std::getenv("SK_ESTIMATOR");
   if (ev && std::strcmp(ev, "ntt") == 0) s->estimator = SK_ESTIMATOR_NTT;
-  if (ev && std::strcmp(ev, "fused") == 0) s->estimator = SK_ESTIMATOR_FUSED;
+  if (ev && std::strcmp(ev, "fft64") == 0) s->estimator = SK_ESTIMATOR_FFT64;
   *out = s;
   return SK_OK;
 }

@@ -26,6 +26,7 @@
 // with the twiddle W_m^(n2 k1) fused, then row FFTs).  Twiddles come from
 // sincospi.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -799,7 +800,9 @@ __global__ void k_recombine(CorrArgs p, const double2* __restrict__ Y) {
       }
       const double rv = rint(v);
       worst = fmax(worst, fabs(v - rv));
-      if (fabs(rv) >= 4503599627370496.0) record(p.status, SK_ERR_INEXACT);   // 2^52
+      // beyond 2^52 a double no longer resolves integers: fail this step's certificate (the
+      // residual check), so the step is redone with narrower limbs
+      if (fabs(rv) >= 4503599627370496.0) worst = 1.0;   // 2^52
       z = i256_add(z, i256_shl_i64((int64_t)rv, p.B * s));
     }
     p.z[g] = z;
@@ -1842,6 +1845,39 @@ sk_status run_estimate_fused(sk_set* s, sk_estimate* out, cudaStream_t st, bool*
   return run_estimate_crt(s, out, st, done);
 }
 
+// Evaluation point of one certificate: a random primitive m-th root of unity w in GF(q)
+// (power-of-two m dividing 2^32), (7^((q-1)/m))^r with r odd, drawn from the set's seed and
+// a per-set counter, so that successive estimates use fresh points.
+EvalArgs draw_eval_point(sk_set* s, int64_t m, int nchunk, uint64_t* part) {
+  EvalArgs ev;
+  uint64_t z = s->seed ^ (0x9E3779B97F4A7C15ull * (++s->eval_draws));
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const uint64_t r = (z % (uint64_t)m) | 1ull;
+  const uint64_t wm = gl_pow(7, (kGL - 1) / (uint64_t)m);
+  ev.w = gl_pow(wm, r);
+  ev.winv = gl_pow(ev.w, kGL - 2);
+  ev.wstep = gl_pow(ev.w, 256);
+  ev.winvstep = gl_pow(ev.winv, 256);
+  ev.e1 = kGLEps;
+  ev.e2 = gl_mul(ev.e1, ev.e1);
+  ev.e3 = gl_mul(ev.e2, ev.e1);
+  ev.e4 = gl_mul(ev.e3, ev.e1);
+  ev.m = m;
+  ev.nchunk = nchunk;
+  ev.part = part;
+  return ev;
+}
+
+// Chunks per row of the evaluation certificate: the d rows give up to 1024 blocks of 256
+// threads, each chunk at least 512 elements.
+int eval_chunks(int64_t m, int d) {
+  int nchunk = 1;
+  while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
+  return nchunk;
+}
+
 // Algorithm 3 over the schedule.  One host round trip per correlation step: before a
 // step the host reads the bit lengths of its two operands (written by the kernels that
 // produced them) together with the previous step's certificate (largest rounding
@@ -1894,34 +1930,14 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   // evaluation certificate: FP64 path with a power-of-two m (an m-th root of unity exists in
   // GF(q) for m | 2^32); chunks per row so that the d rows give up to 1024 blocks
   const bool eval_cert = s->estimator == SK_ESTIMATOR_FFT64 && M == m && logm <= 32;
-  int nchunk = 1;
-  while ((int64_t)nchunk * 2 * 256 <= m && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
+  const int nchunk = eval_chunks(m, d);
 
   std::vector<int> bmax(ncorr, 64);     // per-step cap on the limb width (lowered on failure)
   std::vector<unsigned long long> cert(cert_words);
   int retries = 0;
   for (int attempt = 0; attempt < 4; attempt++) {
     EvalArgs ev;
-    if (eval_cert) {
-      // a random primitive m-th root of unity: (7^((q-1)/m))^r with r odd
-      uint64_t z = s->seed ^ (0x9E3779B97F4A7C15ull * (++s->eval_draws));
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      z ^= z >> 31;
-      const uint64_t r = (z % (uint64_t)m) | 1ull;
-      const uint64_t wm = gl_pow(7, (kGL - 1) / (uint64_t)m);
-      ev.w = gl_pow(wm, r);
-      ev.winv = gl_pow(ev.w, kGL - 2);
-      ev.wstep = gl_pow(ev.w, 256);
-      ev.winvstep = gl_pow(ev.winv, 256);
-      ev.e1 = kGLEps;
-      ev.e2 = gl_mul(ev.e1, ev.e1);
-      ev.e3 = gl_mul(ev.e2, ev.e1);
-      ev.e4 = gl_mul(ev.e3, ev.e1);
-      ev.m = m;
-      ev.nchunk = nchunk;
-      ev.part = d_part;
-    }
+    if (eval_cert) ev = draw_eval_point(s, m, nchunk, d_part);
     std::vector<int> phys(nslots);
     for (int i = 0; i < nslots; i++) phys[i] = i;
     auto slot = [&](int i) { return (I256*)(base + slot_bytes * phys[i]); };
@@ -2397,20 +2413,28 @@ constexpr size_t kNoAllocScratchBytes = SK_NOALLOC_SCRATCH_BYTES;   // 32 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+std::atomic<void*> g_noalloc_addr[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
 
-sk_status noalloc_base(char** out) {
+// Device address of the scratch array on the current device, which must be the set's
+// device (the set's counters and the scratch must live on the same GPU).  The first call
+// on a device looks it up (under a lock; later calls read the cached address).
+sk_status noalloc_base(const sk_set* s, char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_status_from_cuda(e);
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return SK_ERR_INVALID_ARG;
-  if (!g_noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return set_status_from_cuda(e);
-    g_noalloc_addr[dev] = ptr;
+  if (dev < 0 || dev >= kNoAllocMaxDevices || dev != s->device) return SK_ERR_INVALID_ARG;
+  void* ptr = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    ptr = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return set_status_from_cuda(e);
+      g_noalloc_addr[dev].store(ptr, std::memory_order_release);
+    }
   }
-  *out = (char*)g_noalloc_addr[dev];
+  *out = (char*)ptr;
   return SK_OK;
 }
 
@@ -2418,6 +2442,11 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// Every correlation step is accepted on three checks, as in run_estimate's FP64 path: the
+// largest distance of an output to its integer (<= 1/4), the exact per-row identity
+// sum z = (sum a)(sum x) (here in signed 256-bit arithmetic), and Z(w) = A(1/w) X(w) modulo
+// q = 2^64 - 2^32 + 1 per row at a freshly drawn random primitive m-th root of unity w.
+// A step that fails is redone with narrower limbs (up to three times).
 sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const int64_t m = s->m;
   const int d = s->d;
@@ -2425,15 +2454,19 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const int logm = ilog2(m);
   const int nslots = s->n_slots + 1;
   if (nslots > 64) return SK_ERR_SCRATCH_TOO_SMALL;
-  // layout: small buffers | twiddles | slots | FFT A | FFT B
-  const size_t small_bytes = align256(4 * SK_MAX_ROWS * sizeof(I256) + 64);
+  const int nchunk = eval_chunks(m, d);
+  // layout: small buffers | twiddles | slots | FFT A | FFT B.  Small buffers: row sums of
+  // a, x, z and the sorted rows (I256 [64] each) | bit lengths (int [4]) | residual (u64) |
+  // evaluation partials (u64 [d][nchunk][3]) | row evaluations (u64 [d][3])
+  const size_t part_words = (size_t)d * nchunk * 3;
+  const size_t small_bytes = align256(4 * SK_MAX_ROWS * sizeof(I256) + 64 + part_words * 8 + 3 * SK_MAX_ROWS * 8);
   const size_t tw_bytes = align256((size_t)(m / 2) * sizeof(double2));
   const size_t slot_bytes = align256((size_t)dm * sizeof(I256));
   const size_t fixed = small_bytes + tw_bytes + slot_bytes * nslots;
   if (fixed > kNoAllocScratchBytes) return SK_ERR_SCRATCH_TOO_SMALL;
   const size_t fft_room = kNoAllocScratchBytes - fixed;
   char* base = nullptr;
-  sk_status bs = noalloc_base(&base);
+  sk_status bs = noalloc_base(s, &base);
   if (bs != SK_OK) return bs;
   I256* d_sa = (I256*)base;
   I256* d_sx = d_sa + SK_MAX_ROWS;
@@ -2441,6 +2474,8 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
   I256* d_sorted = d_sz + SK_MAX_ROWS;
   int* d_bits = (int*)(d_sorted + SK_MAX_ROWS);
   unsigned long long* d_resid = (unsigned long long*)(d_bits + 4);
+  uint64_t* d_part = (uint64_t*)((char*)d_bits + 64);            // after the 64-byte block of bits + residual
+  unsigned long long* d_eval = (unsigned long long*)(d_part + part_words);
   double2* tw = (double2*)(base + small_bytes);
   char* slot_base = base + small_bytes + tw_bytes;
   int phys[64];
@@ -2457,6 +2492,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
   int max_limbs = 0, last_B = 0, retries = 0;
   const int eg = grid_for(dm);
   I256 sa[SK_MAX_ROWS], sx[SK_MAX_ROWS], sz[SK_MAX_ROWS];
+  unsigned long long evals[3 * SK_MAX_ROWS];
 
   for (const EstOp& op : s->plan) {
     if (op.kind == OP_LEAF) {
@@ -2546,19 +2582,29 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
         count_launch();
         k_rowsum<<<d, 1024, 0, st>>>(p.z, m, d_sz);
         count_launch();
+        EvalArgs ev = draw_eval_point(s, m, nchunk, d_part);
+        ev.a = a;
+        ev.x = x;
+        ev.z = p.z;
+        k_eval_partial<<<d * nchunk, 256, 0, st>>>(ev);
+        k_eval_final<<<(3 * d + 255) / 256, 256, 0, st>>>(d_part, d, nchunk, d_eval);
+        count_launch(2);
         SK_CK(cudaGetLastError());
         unsigned long long rbits = 0;
         SK_CK(cudaMemcpyAsync(&rbits, d_resid, sizeof(rbits), cudaMemcpyDeviceToHost, st));
         SK_CK(cudaMemcpyAsync(sz, d_sz, d * sizeof(I256), cudaMemcpyDeviceToHost, st));
+        SK_CK(cudaMemcpyAsync(evals, d_eval, 3 * d * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         SK_CK(cudaStreamSynchronize(st));
         double resid;
         std::memcpy(&resid, &rbits, sizeof(resid));
         bool ok = resid <= 0.25;
         for (int r = 0; r < d && ok; r++) ok = i256_eq(sz[r], HostI256::mul(sa[r], sx[r]));
-        max_resid = std::max(max_resid, resid);
-        max_limbs = std::max(max_limbs, std::max(La, Lx));
-        last_B = B;
+        for (int r = 0; r < d && ok; r++)
+          ok = evals[3 * r + 2] == (unsigned long long)(((unsigned __int128)evals[3 * r] * evals[3 * r + 1]) % kGL);
         if (ok) {
+          max_resid = std::max(max_resid, resid);
+          max_limbs = std::max(max_limbs, std::max(La, Lx));
+          last_B = B;
           std::swap(phys[op.dst], phys[spare]);
           done = true;
         } else {
@@ -2585,24 +2631,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
     SK_CK(cudaStreamSynchronize(st));
     return (sk_status)status;
   }
-  auto to_double = [](const I256& v) {
-    const bool neg = i256_neg_p(v);
-    const I256 a = neg ? i256_neg(v) : v;
-    double r = 0.0;
-    for (int k = 3; k >= 0; k--) r = r * 18446744073709551616.0 + (double)a.w[k];
-    return neg ? -r : r;
-  };
-  out->d = d;
-  for (int r = 0; r < d; r++) std::memcpy(&out->row[r], &rows[r], sizeof(sk_i256));
-  const I256 med = sorted[(d - 1) / 2];
-  std::memcpy(&out->median, &med, sizeof(sk_i256));
-  const bool fits = (med.w[1] == med.w[2] && med.w[2] == med.w[3] &&
-                     (med.w[3] == 0 ? (int64_t)med.w[0] >= 0 : (med.w[3] == ~0ull && (int64_t)med.w[0] < 0)));
-  out->fits_i64 = fits ? 1 : 0;
-  out->median_i64 = fits ? (int64_t)med.w[0] : 0;
-  out->median_f64 = to_double(med);
-  out->mid_mean_f64 = (d & 1) ? to_double(sorted[d / 2])
-                              : 0.5 * (to_double(sorted[d / 2 - 1]) + to_double(sorted[d / 2]));
+  fill_estimate(out, rows, sorted, d);
   out->max_residual = max_resid;
   out->max_limbs = max_limbs;
   out->limb_bits = last_B;

@@ -484,7 +484,7 @@ sk_status sk_family_create(const sk_query* query, int32_t n_sub, const int32_t* 
     }
     const char* ev = std::getenv("SK_ESTIMATOR");
     if (ev && std::strcmp(ev, "ntt") == 0) fs.est->estimator = SK_ESTIMATOR_NTT;
-    if (ev && std::strcmp(ev, "fused") == 0) fs.est->estimator = SK_ESTIMATOR_FUSED;
+    if (ev && std::strcmp(ev, "fft64") == 0) fs.est->estimator = SK_ESTIMATOR_FFT64;
   }
   const int nw = std::min(env_workers(), n_sub);
   for (int w = 0; w < nw; w++) {

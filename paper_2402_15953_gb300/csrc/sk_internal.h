@@ -78,7 +78,7 @@ struct sk_set {
   sk::Scratch fft_scratch;                     // estimator FFT buffers (grown on demand)
   double* d_twiddle = nullptr;                 // FFT twiddles for width m
   int64_t twiddle_m = 0;
-  int estimator = SK_ESTIMATOR_FFT64;          // correlation backend
+  int estimator = SK_ESTIMATOR_FUSED;          // correlation backend
   uint64_t* d_gl_tw = nullptr;                 // GF(q) twiddles [w^t | w^-t] for the NTT length
   int64_t gl_m = 0;
   uint64_t gl_r4 = 1, gl_r4inv = 1, gl_minv = 1;

@@ -77,16 +77,19 @@ def test_chain8_full_estimate_linearity(chain8_full):
 
 def test_chain8_full_fft_and_ntt_backends_agree(chain8_full):
     """At full size (estimates near 10^46, operands split into up to 10 limbs) the certified
-    FP64 FFT and the exact GF(q) transform give the same 16 rows."""
+    FP64 FFT, the exact GF(q) transform and the fused CRT form give the same 16 rows."""
     wl = chain8_full
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
     for k, rel in enumerate(wl.relations):
         s.update(k, rel.cols)
+    s.set_estimator("fft64")
     a = s.estimate()
     s.set_estimator("ntt")
     b = s.estimate()
-    assert a["rows"] == b["rows"] and a["median"] == b["median"]
-    assert a["max_limbs"] >= 6
+    s.set_estimator("fused")
+    c = s.estimate()
+    assert a["rows"] == b["rows"] == c["rows"] and a["median"] == b["median"] == c["median"]
+    assert a["max_limbs"] >= 6 and a["max_residual"] <= 0.25
     s.close()
 
 

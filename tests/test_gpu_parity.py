@@ -152,9 +152,10 @@ def test_update_shared_memory_path_warp_aggregation(agg, monkeypatch):
     s.close()
 
 
-def test_chain3_config_exact():
+@pytest.mark.parametrize("estimator", ["fft64", "ntt", "fused"])
+def test_chain3_config_exact(estimator):
     """Chain R1(A) - R2(A,B) - R3(B), 10^4 rows each, m = 256, d = 5, seed 42: bit-exact
-    sketches, exact row estimates and median."""
+    sketches, exact row estimates and median in each arithmetic."""
     w = synth.chain3()
     rels = [(r.cols.numpy(), None) for r in w.relations]
     s = _gpu_sketch(w.num_join_attrs, w.edges, w.m, w.d, w.hash_seed, rels)
@@ -162,6 +163,7 @@ def test_chain3_config_exact():
     got = s.counters.cpu().numpy()
     for k in range(3):
         assert np.array_equal(got[k], sk[k])
+    s.set_estimator(estimator)
     est = s.estimate()
     ref = O.estimate(q, sk)
     assert est["rows"] == ref.rows
@@ -171,8 +173,9 @@ def test_chain3_config_exact():
     s.close()
 
 
+@pytest.mark.parametrize("estimator", ["fft64", "fused"])
 @pytest.mark.parametrize("m", [2, 4, 8, 64, 1024, 1 << 13, 1 << 14])
-def test_estimate_exact_random_queries(m):
+def test_estimate_exact_random_queries(m, estimator):
     rng = random.Random(1000 + m)
     trials = 6 if m <= 1024 else 2
     for trial in range(trials):
@@ -181,6 +184,7 @@ def test_estimate_exact_random_queries(m):
         d = rng.choice([1, 2, 5])
         seed = rng.randrange(1 << 62)
         s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        s.set_estimator(estimator)
         q, co, sk = _oracle(attrs, edges, m, d, seed, rels)
         est = s.estimate()
         ref = O.estimate(q, sk)
@@ -189,8 +193,9 @@ def test_estimate_exact_random_queries(m):
         s.close()
 
 
+@pytest.mark.parametrize("estimator", ["fft64", "fused"])
 @pytest.mark.parametrize("m", [3, 5, 12, 100, 1000, 10007])
-def test_estimate_exact_non_power_of_two_width(m):
+def test_estimate_exact_non_power_of_two_width(m, estimator):
     """Widths that are not powers of two (the paper's experiments use m = 10^6): zero-padded
     transforms folded back mod m give the exact Algorithm 3 rows."""
     rng = random.Random(2000 + m)
@@ -200,6 +205,7 @@ def test_estimate_exact_non_power_of_two_width(m):
         d = rng.choice([1, 3])
         seed = rng.randrange(1 << 62)
         s = _gpu_sketch(attrs, edges, m, d, seed, rels)
+        s.set_estimator(estimator)
         q, co, sk = _oracle(attrs, edges, m, d, seed, rels)
         assert np.array_equal(s.counters.cpu().numpy(), np.stack(sk))
         est = s.estimate()
@@ -208,7 +214,8 @@ def test_estimate_exact_non_power_of_two_width(m):
         s.close()
 
 
-def test_width_one_million_correlation_through_a_one_tuple_relation():
+@pytest.mark.parametrize("estimator", ["fft64", "fused"])
+def test_width_one_million_correlation_through_a_one_tuple_relation(estimator):
     """m = 10^6 (Section 4.4's width): R1 with one tuple turns each row estimate into one output
     of the circular correlation of R3's and R2's sketches, computed directly by the oracle."""
     attrs, edges = [1, 2, 1], [(0, 0, 1, 0), (1, 1, 2, 0)]
@@ -217,6 +224,7 @@ def test_width_one_million_correlation_through_a_one_tuple_relation():
     r3 = synth.zipf_keys(n, 1.2, 1 << 20, 5)[None, :].contiguous()
     m, d = 1_000_000, 3
     s = pkg.SketchSet(attrs, edges, m, d, 91)
+    s.set_estimator(estimator)
     s.update(0, torch.tensor([[777]], dtype=torch.int64, device="cuda"))
     s.update(1, r2.cuda())
     s.update(2, r3.cuda())
@@ -252,16 +260,28 @@ def test_estimate_exact_ntt_backend(m):
         s.close()
 
 
+def test_default_estimator_is_fused():
+    s = pkg.SketchSet([1, 1], [(0, 0, 1, 0)], 64, 2, 1)
+    s.update(0, torch.arange(50, dtype=torch.int64, device="cuda")[None, :])
+    s.update(1, torch.arange(50, dtype=torch.int64, device="cuda")[None, :])
+    e = s.estimate()
+    assert e["limb_bits"] == 0 and e["max_limbs"] >= 1      # CRT primes, no limbs
+    s.close()
+
+
 def test_ntt_and_fft_backends_agree_on_the_star_and_chain8_shapes():
     for wl in (synth.star(n_fact=2_000_000, n_dim=200_000, m=1 << 16, d=3, device="cuda"),
                synth.chain(r=8, n=200_000, m=1 << 14, d=2, device="cuda")):
         s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
         for k, rel in enumerate(wl.relations):
             s.update(k, rel.cols)
+        s.set_estimator("fft64")
         a = s.estimate()
         s.set_estimator("ntt")
         b = s.estimate()
-        assert a["rows"] == b["rows"] and a["median"] == b["median"]
+        s.set_estimator("fused")
+        c = s.estimate()
+        assert a["rows"] == b["rows"] == c["rows"] and a["median"] == b["median"] == c["median"]
         s.close()
     assert pkg.load().sk_sketch_set_estimator(None, 1) == pkg.SK_ERR_INVALID_ARG
 

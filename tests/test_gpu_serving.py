@@ -1,11 +1,13 @@
 """The serving loop: requests that run mixed and overlapped on the device give, for
-every estimate, exactly the result of running that set's requests one by one."""
+every estimate, exactly the result of running that set's requests one by one, and that
+result is the CPU oracle's Algorithm 3 over the updates of the set submitted before it."""
 import random
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import paper_2402_15953_gb300 as pkg
 from paper_2402_15953_gb300.serve import SketchServer
 from tests._helpers import random_relations, random_tree_query
@@ -32,6 +34,27 @@ def _trace(seed, n_sets=6, n_req=90):
     for sid in range(n_sets):
         reqs.append(("estimate", sid))
     return sets, reqs
+
+
+def _oracle_expected(sets, reqs):
+    """Per estimate request j: the oracle's rows and lower median (Algorithm 3, Section 3.3)
+    for the sketches of exactly the updates of its set submitted before it.  The oracle
+    sketches each update batch itself (Algorithm 2, Eq. 4) and the batches of one relation
+    add up (Eq. 4 is a sum over tuples)."""
+    qs, cos, acc = [], [], []
+    for (attrs, edges, m, d, seed) in sets:
+        q = O.canonical_query(attrs, edges)
+        qs.append(q)
+        cos.append(O.draw_coefficients(seed, d, q.n_comp, len(q.edges)))
+        acc.append([np.zeros((d, m), dtype=np.int64) for _ in attrs])
+    out = {}
+    for j, r in enumerate(reqs):
+        if r[0] == "update":
+            _, sid, rel, cols, w = r
+            acc[sid][rel] += O.sketch_relation(qs[sid], cos[sid], rel, cols.numpy(), w.numpy(), sets[sid][2])
+        else:
+            out[j] = O.estimate(qs[r[1]], acc[r[1]])
+    return out
 
 
 def _alone(sets, reqs):
@@ -66,15 +89,16 @@ def _mixed(sets, reqs, budget=32 << 30, slots=8, workers=4):
 
 
 @pytest.mark.parametrize("seed", [1, 2])
-def test_results_equal_alone_and_in_the_mix(seed):
+def test_results_equal_alone_in_the_mix_and_the_oracle(seed):
     sets, reqs = _trace(seed)
+    ref = _oracle_expected(sets, reqs)
     alone = _alone(sets, reqs)
     mixed, handles = _mixed(sets, reqs)
-    assert set(alone) == set(mixed)
+    assert set(alone) == set(mixed) == set(ref)
     for j in alone:
         assert handles[j].error is None, handles[j].error
-        assert mixed[j]["rows"] == alone[j]["rows"], j
-        assert mixed[j]["median"] == alone[j]["median"]
+        assert mixed[j]["rows"] == alone[j]["rows"] == ref[j].rows, j
+        assert mixed[j]["median"] == alone[j]["median"] == ref[j].median
 
 
 def test_tight_budget_queues_but_stays_exact():
@@ -82,10 +106,13 @@ def test_tight_budget_queues_but_stays_exact():
     resident = sum(len(a) * d * m * 8 for (a, e, m, d, s) in sets)
     est = max((max(2, len(a)) + 1) * d * m * 32 + 2 * d * 4 * m * 16 + (m // 2) * 16 for (a, e, m, d, s) in sets)
     budget = resident + est + 4 * 3000 * 8 * 2 + 4096
+    ref = _oracle_expected(sets, reqs)
     alone = _alone(sets, reqs)
     mixed, handles = _mixed(sets, reqs, budget=budget, slots=2, workers=1)
     for j in alone:
-        assert mixed[j]["rows"] == alone[j]["rows"]
+        assert handles[j].error is None, handles[j].error
+        assert mixed[j]["rows"] == alone[j]["rows"] == ref[j].rows
+        assert mixed[j]["median"] == ref[j].median
 
 
 def test_register_beyond_budget_is_refused():
@@ -136,6 +163,8 @@ def test_hold_then_release_equals_alone():
     assert srv.pending() == len(reqs)
     srv.hold(False)
     srv.serve()
+    ref = _oracle_expected(sets, reqs)
     for j in alone:
-        assert handles[j].error is None and handles[j].result["rows"] == alone[j]["rows"]
+        assert handles[j].error is None and handles[j].result["rows"] == alone[j]["rows"] == ref[j].rows
+        assert handles[j].result["median"] == ref[j].median
     srv.close()
