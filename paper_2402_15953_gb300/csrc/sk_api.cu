@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <set>
 
@@ -29,6 +30,46 @@ cudaError_t allow_dynamic_smem(const void* func) {
   cudaError_t e = cudaFuncGetAttributes(&fa, func);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+// Stream-ordered device memory pool of this library (one per device, created on first use)
+// for update scratch: key tables and the partitioned update's planes.  Up to
+// SK_POOL_KEEP_MB (default 4096) MiB stay reserved between calls, so a batch's scratch of a
+// few GB is not mapped again for every call; anything above that is returned to the
+// device at the next synchronisation.
+namespace {
+constexpr int kPoolMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kPoolMaxDevices] = {};
+}  // namespace
+
+cudaError_t pool_malloc_async(void** ptr, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kPoolMaxDevices) return cudaMallocAsync(ptr, bytes, st);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev], &props);
+      if (e != cudaSuccess) {
+        g_pools[dev] = nullptr;
+        return e;
+      }
+      const char* v = std::getenv("SK_POOL_KEEP_MB");
+      const long long mb = v ? std::atoll(v) : 4096;
+      uint64_t keep = (uint64_t)(mb < 0 ? 0 : mb) << 20;
+      cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
 }
 
 sk_status set_status_from_cuda(cudaError_t e) {

@@ -112,6 +112,9 @@ void count_launch(int n = 1);   // adds to the process-wide kernel-launch counte
 // launch, failing that launch.  Launches still request only what they use.
 cudaError_t allow_dynamic_smem(const void* func);
 sk_status query_info(const sk_query* q, QueryInfo* out);   // validation + canonical numbering
+// Stream-ordered allocation from the library's device pool (update scratch); release with
+// cudaFreeAsync on a stream ordered after the last use.
+cudaError_t pool_malloc_async(void** ptr, size_t bytes, cudaStream_t st);
 // Algorithm 1's draw: d rows of row_len field elements from SplitMix64(seed)
 std::vector<uint64_t> draw_coefficients(uint64_t seed, int d, int row_len);
 // A set used only for estimation: its relations' counters are rel_ctr (owned elsewhere).

@@ -100,6 +100,276 @@ __global__ void __launch_bounds__(256, (A > 0 && V8 && NARROW && POW2) ? 5 : 1) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Partitioned update through the key tables (unit weights, power-of-two m <= 2^16, narrow
+// records of 16 or 32 bytes: the star fact table).  k_update_tab adds each (tuple, row) to
+// the L2-resident int64 sketch with one 64-bit reduction, and the L2 lookup rate bounds it
+// (9 reductions per tuple at d = 9, about half of them forwarded between the two dies' L2
+// halves).  Shared-memory atomics run about ten times faster than L2 reductions on GB300,
+// but a d x m int32 sketch of 9 x 2^16 does not fit in one SM.  So the update runs in two
+// phases over windows of the batch.  Each row's bins are split into S = m / 2^L parts of
+// 2^L bins, L = min(log2 m, 15), so S is 1 or 2.
+//   1. k_tab_items: per tuple the same gathers and bin and sign sums as update_tuple_tab,
+//      written as planes: bins [d][W] uint16 (coalesced stores) and per 32 tuples one word
+//      of sign bits per row.  A tuple with a key outside its declared domain is skipped and
+//      reported, as in every other path: it is written as bin 0 with sign +1 and, for each
+//      row, -1 is added at once to that row's counter 0, so phase 2 needs no validity test.
+//      Stores carry an L2 evict-first hint, so the planes do not push the key tables'
+//      records out of L2.
+//   2. k_part_accum: a CTA owns part h of one row as 2^L int32 counters in shared memory
+//      (at most 128 KB), reads its row's plane over a range of tuples, adds the sign of every
+//      tuple whose bin lies in its part with a shared-memory atomic, and adds each counter
+//      into the int64 sketch with one 64-bit reduction.
+// Every counter receives the same sum as in k_update_tab (integer addition in any order);
+// a CTA's int32 counter holds at most its range's tuple count in magnitude, kept below 2^31.
+// ---------------------------------------------------------------------------
+struct PartArgs {
+  uint16_t* bins;     // [d][W]
+  uint32_t* sgn;      // [d][W / 32]: bit t % 32 of word t / 32 set when tuple t's sign is -1
+  int64_t W;          // window capacity, a multiple of 256
+  int64_t i0;         // first tuple of the window
+  int64_t cnt;        // tuples in the window, <= W
+};
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void st_u16_hint(uint16_t* ptr, uint16_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void st_u32_hint(uint32_t* ptr, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+
+// RV: record length in 16-byte vectors, 2 (d <= 14: bins in words 0..6, signs in word 7) or
+// 1 (d <= 6: bins in words 0..2, signs in word 3).  Persistent: each thread walks the window
+// with the grid's stride, loading the keys of its next tuple before it gathers the records
+// of the current one, so the key stream's latency overlaps the gathers.  Lanes of a warp
+// take consecutive tuples and iterate together (the ballots need the whole warp).
+// Bin sums: only each sum mod 2^16 is needed (m divides 2^16).  Per record word holding the
+// bins of rows 2j and 2j + 1, lo[j] adds the low halves (below 5 * 2^16: no overflow) and
+// all[j] the whole words mod 2^32, so row 2j's sum is lo[j] mod 2^16 and row 2j + 1's is
+// ((all[j] - lo[j]) >> 16) mod 2^16 (all - lo is the sum of the high halves times 2^16).
+template <int A, int RV>
+__global__ void __launch_bounds__(256, 5) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
+  constexpr int NB = RV == 2 ? 7 : 3;   // words of bins per record
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gend = (q.cnt + 31) & ~(int64_t)31;
+  const uint32_t mask = (uint32_t)p.m - 1u;
+  const bool lead = (threadIdx.x & 31) == 0;
+  const uint64_t pol = policy_evict_first();
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // keys of the thread's next tuple, checked against their domains as they arrive: the
+  // in-domain keys (< 2^31) as 32-bit values, bit u of okm set when key u is in its domain
+  uint32_t kx[A], okm = 0;
+#pragma unroll
+  for (int u = 0; u < A; u++) {
+    const int64_t k = g < q.cnt ? ld_key_stream(p.cols + (int64_t)u * p.stride + q.i0 + g) : -1;
+    const bool kin = k >= 0 && k < p.dom[u];
+    okm |= (uint32_t)kin << u;
+    kx[u] = kin ? (uint32_t)k : 0u;
+  }
+  for (; g < gend; g += step) {
+    const bool in = g < q.cnt;
+    const bool ok = in && okm == (1u << A) - 1u;
+    const uint4* rec[A];
+#pragma unroll
+    for (int u = 0; u < A; u++) rec[u] = (const uint4*)t.tbl + (t.base[u] + kx[u]) * RV;
+    if (in && !ok) {   // written as bin 0, sign +1 below: cancel it in every row's counter 0
+      record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
+      for (int j = 0; j < p.d; j++) red_add_global(p.ctr + (int64_t)j * p.m, ~0ull);
+    }
+    const int64_t gn = g + step;
+    okm = 0;
+#pragma unroll
+    for (int u = 0; u < A; u++) {
+      const int64_t k = gn < q.cnt ? ld_key_stream(p.cols + (int64_t)u * p.stride + q.i0 + gn) : -1;
+      const bool kin = k >= 0 && k < p.dom[u];
+      okm |= (uint32_t)kin << u;
+      kx[u] = kin ? (uint32_t)k : 0u;
+    }
+    uint32_t lo[NB], all[NB], sg = 0;
+#pragma unroll
+    for (int j = 0; j < NB; j++) lo[j] = all[j] = 0;
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < A; u++) {
+        uint32_t w[8];
+        if (RV == 2) {
+          ld_record32(rec[u], w);
+        } else {
+          const uint4 v = __ldg(rec[u]);
+          w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        }
+        sg ^= w[4 * RV - 1];   // the record's last word: the sign bits
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+          lo[j] += w[j] & 0xffffu;
+          all[j] += w[j];
+        }
+      }
+    }
+    const int64_t word = g >> 5;
+#pragma unroll
+    for (int j = 0; j < 2 * NB; j++) {
+      if (j >= p.d) break;
+      const uint32_t sum = (j & 1) ? (all[j >> 1] - lo[j >> 1]) >> 16 : lo[j >> 1];
+      if (in) st_u16_hint(q.bins + (int64_t)j * q.W + g, (uint16_t)(sum & mask), pol);
+      const uint32_t sb = __ballot_sync(0xffffffffu, (sg >> j) & 1u);
+      if (lead) st_u32_hint(q.sgn + (int64_t)j * (q.W >> 5) + word, sb, pol);
+    }
+  }
+}
+
+// blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row`, tuple range c of
+// nrange (ranges of seg tuples, a multiple of 256, taken with stride nrange * seg).  A
+// thread takes two units of 8 tuples per iteration (each: one 16-byte load of bins, 8 bits
+// of the sign and validity words), all loads issued before the atomics.
+// vw: bit k set when tuple k of the unit is in the window (all but the window's last unit: 0xff).
+__device__ __forceinline__ void part_unit(int* cnt, uint4 v, uint32_t sw, uint32_t vw, uint32_t base, uint32_t span) {
+  const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const uint32_t rel = ((e[k >> 1] >> (16 * (k & 1))) & 0xffffu) - base;   // outside the part: >= span
+    if (rel < span && ((vw >> k) & 1u)) atomicAdd(cnt + rel, 1 - (int)(((sw >> k) & 1u) << 1));
+  }
+}
+
+__device__ __forceinline__ uint32_t unit_mask(int64_t u, int64_t cnt) {
+  const int64_t r = cnt - (u << 3);
+  return r >= 8 ? 0xffu : ((1u << r) - 1u);
+}
+
+__global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long long* ctr, int64_t m, int d,
+                                                     int logL, int64_t seg, int nrange) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* cnt = (int*)smem_raw;
+  const int S = (int)(m >> logL);
+  const int h = (int)(blockIdx.x % (unsigned)S);
+  const int rest = (int)(blockIdx.x / (unsigned)S);
+  const int row = rest % d;
+  const int c = rest / d;
+  const int L = 1 << logL;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  const uint16_t* bins = q.bins + (int64_t)row * q.W;
+  const uint32_t* sgn = q.sgn + (int64_t)row * (q.W >> 5);
+  const uint32_t base = (uint32_t)h << logL, span = (uint32_t)L;
+  const int64_t bd = blockDim.x;
+  for (int64_t a = (int64_t)c * seg; a < q.cnt; a += (int64_t)nrange * seg) {
+    const int64_t ue = ((a + seg < q.cnt ? a + seg : q.cnt) + 7) >> 3;   // units [a / 8, ue)
+    int64_t u = (a >> 3) + threadIdx.x;
+    for (; u + bd < ue; u += 2 * bd) {
+      const int64_t u2 = u + bd;
+      const uint4 v1 = *(const uint4*)(bins + (u << 3));
+      const uint4 v2 = *(const uint4*)(bins + (u2 << 3));
+      const uint32_t s1 = __ldg(sgn + (u >> 2)), s2 = __ldg(sgn + (u2 >> 2));
+      const int sh1 = (int)(u & 3) << 3, sh2 = (int)(u2 & 3) << 3;
+      part_unit(cnt, v1, s1 >> sh1, unit_mask(u, q.cnt), base, span);
+      part_unit(cnt, v2, s2 >> sh2, unit_mask(u2, q.cnt), base, span);
+    }
+    if (u < ue) {
+      const int sh = (int)(u & 3) << 3;
+      part_unit(cnt, *(const uint4*)(bins + (u << 3)), __ldg(sgn + (u >> 2)) >> sh, unit_mask(u, q.cnt), base, span);
+    }
+  }
+  __syncthreads();
+  unsigned long long* out = ctr + (int64_t)row * m + ((int64_t)h << logL);
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const int v = cnt[k];
+    if (v != 0) red_add_global(out + k, (unsigned long long)(int64_t)v);
+  }
+}
+
+// Persistent grid: as many CTAs as fit on the GPU (at most one tuple per thread).
+template <int A>
+cudaError_t launch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int sms, cudaStream_t st) {
+  auto kern = t.rvec == 2 ? k_tab_items<A, 2> : k_tab_items<A, 1>;
+  // no shared memory: leave the whole unified array to L1, which caches the hot records
+  cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((q.cnt + 255) / 256, (int64_t)sms * std::max(1, per_sm)));
+  kern<<<grid, 256, 0, st>>>(a, t, q);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// SK_PART_UPDATE=0 keeps the single-phase k_update_tab for batches the partitioned update
+// could take; SK_PART_WINDOW caps the tuples per window (default and largest: 2^30, which
+// keeps every shared-memory counter of k_part_accum below 2^31 in magnitude).
+int part_update_mode() {
+  const char* v = std::getenv("SK_PART_UPDATE");
+  return (v && v[0] == '0') ? 0 : 1;
+}
+
+int64_t part_window_max() {
+  const char* v = std::getenv("SK_PART_WINDOW");
+  const long long x = v ? std::atoll(v) : 0;
+  return (x > 0 && x < (1ll << 30)) ? (int64_t)x : ((int64_t)1 << 30);
+}
+
+// Both phases over every window of the batch (staging allocated from the stream-ordered
+// pool on st and released on st).  *ran false when the staging cannot be allocated.
+cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int sms, cudaStream_t st, bool* ran) {
+  *ran = false;
+  const int64_t n = a.n;
+  const int64_t W = std::min<int64_t>((n + 255) / 256 * 256, (part_window_max() + 255) / 256 * 256);
+  const size_t bin_bytes = (size_t)a.d * W * sizeof(uint16_t);
+  const size_t sgn_bytes = (size_t)a.d * (W / 32) * sizeof(uint32_t);
+  void* buf = nullptr;
+  cudaError_t e = pool_malloc_async(&buf, bin_bytes + sgn_bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  *ran = true;
+  PartArgs q;
+  q.bins = (uint16_t*)buf;
+  q.sgn = (uint32_t*)((char*)buf + bin_bytes);
+  q.W = W;
+  int logm = 0;
+  while (((int64_t)1 << logm) < (int64_t)a.m) logm++;
+  const int logL = std::min(logm, 15);
+  const int S = (int)(a.m >> logL);
+  const size_t smem = (size_t)4 << logL;
+  e = allow_dynamic_smem((const void*)k_part_accum);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part_accum, 1024, smem);
+  const int64_t slots = (int64_t)sms * std::max(1, per_sm);
+  const int64_t units = (int64_t)S * a.d;
+  for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
+    q.i0 = i0;
+    q.cnt = std::min(W, n - i0);
+    switch (a.a) {
+      case 1: e = launch_tab_items<1>(a, t, q, sms, st); break;
+      case 2: e = launch_tab_items<2>(a, t, q, sms, st); break;
+      case 3: e = launch_tab_items<3>(a, t, q, sms, st); break;
+      case 4: e = launch_tab_items<4>(a, t, q, sms, st); break;
+      default: e = launch_tab_items<5>(a, t, q, sms, st); break;
+    }
+    if (e != cudaSuccess) break;
+    // ranges per (row, part): the grid a whole number of waves when that takes 2..64 waves
+    int64_t nr = 0;
+    for (int64_t k = 2; k <= 64 && !nr; k++)
+      if ((k * slots) % units == 0) nr = k * slots / units;
+    if (!nr) nr = (4 * slots + units - 1) / units;
+    nr = std::max<int64_t>(1, std::min<int64_t>(nr, (q.cnt + 255) / 256));
+    const int64_t seg = ((q.cnt + nr - 1) / nr + 255) / 256 * 256;
+    nr = (q.cnt + seg - 1) / seg;
+    k_part_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, logL, seg, (int)nr);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  const cudaError_t ef = cudaFreeAsync(buf, st);
+  return e != cudaSuccess ? e : ef;
+}
+
 // SK_TAB_V8=0 reads 32-byte key-table records as two 16-byte loads instead of one.
 bool tab_v8_enabled() {
   const char* v = std::getenv("SK_TAB_V8");
@@ -498,7 +768,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
                                     (size_t)s->d * (size_t)s->m * sizeof(int64_t) <= ((size_t)32 << 20));
     if (fits && worth && total > 0 && bytes <= key_table_max_bytes()) {
       void* buf = nullptr;
-      e = cudaMallocAsync(&buf, bytes, st);
+      e = pool_malloc_async(&buf, bytes, st);
       if (e != cudaSuccess) {
         cudaGetLastError();   // not enough memory for the table: hash per tuple instead
       } else {
@@ -515,7 +785,12 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
           count_launch();
           e = cudaGetLastError();
         }
-        if (e == cudaSuccess) {
+        bool part_done = false;
+        const bool part_ok = part_update_mode() != 0 && pow2 && t.narrow && t.rvec <= 2 && tab_v8_enabled() &&
+                             weights == nullptr && rp.a >= 1 && rp.a <= 5 && !use_smem && s->m >= 1024 &&
+                             n >= (int64_t)s->m * 16;
+        if (e == cudaSuccess && part_ok) e = run_partitioned(a, t, sms, st, &part_done);
+        if (e == cudaSuccess && !part_done) {
           if (use_smem) {
             const int per_sm = sub_bytes <= 48 * 1024 ? 4 : (sub_bytes <= 100 * 1024 ? 2 : 1);
             const int64_t want = (n + 256 * 16 - 1) / (256 * 16);

@@ -170,3 +170,35 @@ def test_key_table_from_page_locked_host_columns(monkeypatch):
             co = O.draw_coefficients(8, 9, q.n_comp, len(q.edges))
             ref = O.sketch_relation(q, co, 0, cols.numpy(), w.numpy(), 1 << 15, threads=16)
         assert np.array_equal(got, ref), host
+
+
+@pytest.mark.parametrize("a,d,m,n,window", [(5, 9, 1 << 16, 1_200_007, 0), (5, 9, 1 << 16, 1_200_007, 262_144),
+                                             (3, 14, 1 << 15, 600_001, 0), (2, 5, 1 << 14, 300_007, 65_536),
+                                             (1, 13, 1 << 12, 100_003, 0), (4, 2, 1 << 16, 1_048_576, 262_144),
+                                             (2, 7, 1 << 13, 200_003, 0), (3, 6, 1 << 15, 524_288, 0)])
+def test_partitioned_update_bit_exact(a, d, m, n, window, monkeypatch):
+    """Unit-weight batches with declared domains, power-of-two m <= 2^16 and sketches too
+    large for one CTA's shared memory take the two-phase update (per-row bin planes, then
+    shared-memory accumulation per (row, part)); one window or several with a ragged last
+    one; keys at the table's first and last records and outside the domain (skipped and
+    reported).  The launch count shows which path ran: the table build plus two launches
+    per window."""
+    monkeypatch.setenv("SK_KEY_TABLE", "1")
+    if window:
+        monkeypatch.setenv("SK_PART_WINDOW", str(window))
+    rng = np.random.default_rng(a * 7919 + d)
+    doms = [int(x) for x in rng.integers(1000, 200_000, size=a)]
+    cols = np.stack([synth.zipf_keys(n, 1.1, doms[u], 300 + u).numpy() for u in range(a)])
+    cols[0, :5] = [0, doms[0] - 1, -1, doms[0], 3]
+    cols[a - 1, n - 3:] = [doms[a - 1], 0, doms[a - 1] - 1]
+    attrs, edges = _star(a)
+    L0 = pkg.sk_launch_count()
+    got = _run(attrs, edges, m, d, 1234 + a, cols, None, doms)
+    launches = pkg.sk_launch_count() - L0
+    per_window = window if window else n
+    assert launches == 1 + 2 * ((n + per_window - 1) // per_window), launches
+    keep = np.all((cols >= 0) & (cols < np.array(doms)[:, None]), axis=0)
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(1234 + a, d, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols[:, keep], None, m, threads=16)
+    assert np.array_equal(got, ref)
