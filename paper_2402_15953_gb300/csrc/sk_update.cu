@@ -101,34 +101,42 @@ __global__ void __launch_bounds__(256, (A > 0 && V8 && NARROW && POW2) ? 5 : 1) 
 }
 
 // ---------------------------------------------------------------------------
-// Partitioned update through the key tables (unit weights, power-of-two m <= 2^16, narrow
-// records of 16 or 32 bytes: the star fact table).  k_update_tab adds each (tuple, row) to
-// the L2-resident int64 sketch with one 64-bit reduction, and the L2 lookup rate bounds it
+// Partitioned update through the key tables (unit weights, power-of-two 1024 <= m <= 2^16,
+// d <= 14, at most 5 attributes: the star fact table).  k_update_tab adds each (tuple, row)
+// to the L2-resident int64 sketch with one 64-bit reduction, and the L2 lookup rate bounds it
 // (9 reductions per tuple at d = 9, about half of them forwarded between the two dies' L2
 // halves).  Shared-memory atomics run about ten times faster than L2 reductions on GB300,
 // but a d x m int32 sketch of 9 x 2^16 does not fit in one SM.  So the update runs in two
 // phases over windows of the batch.  Each row's bins are split into S = m / 2^L parts of
 // 2^L bins, L = min(log2 m, 15), so S is 1 or 2.
-//   1. k_tab_items: per tuple the same gathers and bin and sign sums as update_tuple_tab,
-//      written as planes: bins [d][W] uint16 (coalesced stores) and per 32 tuples one word
-//      of sign bits per row.  A tuple with a key outside its declared domain is skipped and
-//      reported, as in every other path: it is written as bin 0 with sign +1 and, for each
-//      row, -1 is added at once to that row's counter 0, so phase 2 needs no validity test.
-//      Stores carry an L2 evict-first hint, so the planes do not push the key tables'
+//   1. k_tab_items: per tuple the key-table gathers and each row's bin sum and sign product
+//      (Eqs. 2-3), written tile by tile (32 consecutive tuples, one warp).  Per tile and row:
+//      32 16-bit items, the tuples of part 0 first and then those of part 1 (each item the
+//      bin's offset within its part in bits 0..14 and the sign in bit 15), and one 16-bit
+//      word with the two parts' counts; the tile's rows form one contiguous block.  A tuple
+//      with a key outside its declared domain is left out (and reported, as in every other
+//      path).  Stores carry an L2 evict-first hint, so the items do not push the key tables'
 //      records out of L2.
 //   2. k_part_accum: a CTA owns part h of one row as 2^L int32 counters in shared memory
-//      (at most 128 KB), reads its row's plane over a range of tuples, adds the sign of every
-//      tuple whose bin lies in its part with a shared-memory atomic, and adds each counter
-//      into the int64 sketch with one 64-bit reduction.
+//      (at most 128 KB); over a range of tiles each warp takes one tile row per step, lane k
+//      holding slot k, adds the signs of part h's items with shared-memory atomics, and the
+//      CTA finally adds each counter into the int64 sketch with one 64-bit reduction.
 // Every counter receives the same sum as in k_update_tab (integer addition in any order);
 // a CTA's int32 counter holds at most its range's tuple count in magnitude, kept below 2^31.
+//
+// Records for this path (32 bytes, built by k_key_table_l20 for d <= 9): row r's bin in bits
+// 20 (r mod 3) .. 20 (r mod 3) + 15 of 64-bit word r / 3 (words 0..2), the d sign bits in
+// 32-bit word 7.  Summing the A <= 5 records word by word in 64 bits gives every row's exact
+// bin sum (below A 2^16 < 2^20: no carry between lanes).  For 10 <= d <= 14 the narrow
+// 16-bit records of k_key_table are used (row pairs summed as described at k_tab_items).
 // ---------------------------------------------------------------------------
 struct PartArgs {
-  uint16_t* bins;     // [d][W]
-  uint32_t* sgn;      // [d][W / 32]: bit t % 32 of word t / 32 set when tuple t's sign is -1
-  int64_t W;          // window capacity, a multiple of 256
-  int64_t i0;         // first tuple of the window
-  int64_t cnt;        // tuples in the window, <= W
+  uint16_t* items;               // tile t, row j: [(t d + j) 32 + slot]
+  uint16_t* cnts;                // tile t, row j: [t d + j] = count of part 0 | count of part 1 << 8
+  const int64_t* col[5];         // column u of the window's first tuple
+  int64_t W;                     // window capacity, a multiple of 256
+  int64_t cnt;                   // tuples in the window, <= W
+  int logL;                      // part width 2^L
 };
 
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -145,31 +153,70 @@ __device__ __forceinline__ void st_u32_hint(uint32_t* ptr, uint32_t v, uint64_t 
   asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
 }
 
-// RV: record length in 16-byte vectors, 2 (d <= 14: bins in words 0..6, signs in word 7) or
-// 1 (d <= 6: bins in words 0..2, signs in word 3).  Persistent: each thread walks the window
-// with the grid's stride, loading the keys of its next tuple before it gathers the records
-// of the current one, so the key stream's latency overlaps the gathers.  Lanes of a warp
-// take consecutive tuples and iterate together (the ballots need the whole warp).
-// Bin sums: only each sum mod 2^16 is needed (m divides 2^16).  Per record word holding the
-// bins of rows 2j and 2j + 1, lo[j] adds the low halves (below 5 * 2^16: no overflow) and
-// all[j] the whole words mod 2^32, so row 2j's sum is lo[j] mod 2^16 and row 2j + 1's is
-// ((all[j] - lo[j]) >> 16) mod 2^16 (all - lo is the sum of the high halves times 2^16).
-template <int A, int RV>
-__global__ void __launch_bounds__(256, 5) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
-  constexpr int NB = RV == 2 ? 7 : 3;   // words of bins per record
+__device__ __forceinline__ int64_t ld_key_policy(const int64_t* ptr, uint64_t pol) {
+  int64_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
+// Key-table records in the 20-bit lane format above (d <= 9, one thread per domain key).
+template <bool DEG1>
+__global__ void __launch_bounds__(256) k_key_table_l20(UpdArgs p, TabArgs t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* s_coef = (uint64_t*)smem_raw;
+  const int ncoef = p.d * p.row_len;
+  for (int i = threadIdx.x; i < ncoef; i += blockDim.x) s_coef[i] = p.coef[i];
+  __syncthreads();
+  const int64_t total = t.base[p.a];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    int u = 0;
+    while (u + 1 < p.a && g >= t.base[u + 1]) u++;
+    const uint32_t x = (uint32_t)(g - t.base[u]);
+    const uint64_t* cr = s_coef + t.off[u];
+    uint64_t lane[3] = {0, 0, 0};
+    uint32_t mask = 0;
+#pragma unroll
+    for (int r = 0; r < 9; r++) {
+      if (r >= p.d) break;
+      uint32_t par;
+      const uint32_t b = key_row_hash<true, DEG1>(p, cr + (int64_t)r * p.row_len, p.deg[u], x, &par);
+      lane[r / 3] |= (uint64_t)b << (20 * (r % 3));
+      mask |= par << r;
+    }
+    uint4* out = (uint4*)(t.tbl + g * 8);
+    out[0] = make_uint4((uint32_t)lane[0], (uint32_t)(lane[0] >> 32), (uint32_t)lane[1], (uint32_t)(lane[1] >> 32));
+    out[1] = make_uint4((uint32_t)lane[2], (uint32_t)(lane[2] >> 32), 0u, mask);
+  }
+}
+
+// FMT 0: 20-bit lane records (d <= 9); FMT 1: narrow 16-bit records of 32 bytes (d <= 14):
+// per record word holding the bins of rows 2j and 2j + 1, lo[j] adds the low halves (below
+// 5 * 2^16: no overflow) and all[j] the whole words mod 2^32, so row 2j's sum is lo[j] mod
+// 2^16 and row 2j + 1's is ((all[j] - lo[j]) >> 16) mod 2^16 (m divides 2^16).
+// Persistent: each thread walks the window with the grid's stride, loading the keys of its
+// next tuple before it gathers the records of the current one, so the key stream's latency
+// overlaps the gathers.  Lanes of a warp take consecutive tuples (one tile) and iterate
+// together (the ballots need the whole warp).
+template <int A, int FMT>
+__global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t gend = (q.cnt + 31) & ~(int64_t)31;
   const uint32_t mask = (uint32_t)p.m - 1u;
-  const bool lead = (threadIdx.x & 31) == 0;
+  const uint32_t low = (1u << q.logL) - 1u;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int d = p.d;
   const uint64_t pol = policy_evict_first();
+  const uint4* tbl = (const uint4*)t.tbl;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // keys of the thread's next tuple, checked against their domains as they arrive: the
   // in-domain keys (< 2^31) as 32-bit values, bit u of okm set when key u is in its domain
   uint32_t kx[A], okm = 0;
 #pragma unroll
   for (int u = 0; u < A; u++) {
-    const int64_t k = g < q.cnt ? ld_key_stream(p.cols + (int64_t)u * p.stride + q.i0 + g) : -1;
-    const bool kin = k >= 0 && k < p.dom[u];
+    const int64_t k = g < q.cnt ? ld_key_policy(q.col[u] + g, pol) : -1;
+    const bool kin = (uint64_t)k < (uint64_t)p.dom[u];
     okm |= (uint32_t)kin << u;
     kx[u] = kin ? (uint32_t)k : 0u;
   }
@@ -178,72 +225,88 @@ __global__ void __launch_bounds__(256, 5) k_tab_items(UpdArgs p, TabArgs t, Part
     const bool ok = in && okm == (1u << A) - 1u;
     const uint4* rec[A];
 #pragma unroll
-    for (int u = 0; u < A; u++) rec[u] = (const uint4*)t.tbl + (t.base[u] + kx[u]) * RV;
-    if (in && !ok) {   // written as bin 0, sign +1 below: cancel it in every row's counter 0
-      record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
-      for (int j = 0; j < p.d; j++) red_add_global(p.ctr + (int64_t)j * p.m, ~0ull);
-    }
+    for (int u = 0; u < A; u++) rec[u] = tbl + ((uint64_t)t.base[u] + kx[u]) * 2;
+    if (in && !ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);   // left out of the tile below
     const int64_t gn = g + step;
     okm = 0;
 #pragma unroll
     for (int u = 0; u < A; u++) {
-      const int64_t k = gn < q.cnt ? ld_key_stream(p.cols + (int64_t)u * p.stride + q.i0 + gn) : -1;
-      const bool kin = k >= 0 && k < p.dom[u];
+      const int64_t k = gn < q.cnt ? ld_key_policy(q.col[u] + gn, pol) : -1;
+      const bool kin = (uint64_t)k < (uint64_t)p.dom[u];
       okm |= (uint32_t)kin << u;
       kx[u] = kin ? (uint32_t)k : 0u;
     }
-    uint32_t lo[NB], all[NB], sg = 0;
+    const uint32_t vb = __ballot_sync(0xffffffffu, ok);
+    uint16_t* ip = q.items + ((g >> 5) * d << 5);   // this tile's row 0
+    uint16_t* cp = q.cnts + (g >> 5) * d;
+    // one row: compact the tile's valid tuples by part (part 0 first) and store the counts
+    auto put = [&](int j, uint32_t bin, uint32_t neg) {
+      const bool hi = (bin >> q.logL) != 0;
+      const uint32_t hb = __ballot_sync(0xffffffffu, ok && hi);
+      const uint32_t lb = vb & ~hb;
+      const uint32_t c0 = __popc(lb);
+      const uint32_t pos = hi ? c0 + __popc(hb & lt) : __popc(lb & lt);
+      if (ok) st_u16_hint(ip + 32 * j + pos, (uint16_t)((bin & low) | (neg << 15)), pol);
+      if (lane == 0) st_u16_hint(cp + j, (uint16_t)(c0 | ((uint32_t)__popc(hb) << 8)), pol);
+    };
+    uint32_t sg = 0;
+    if (FMT == 0) {
+      uint64_t acc0 = 0, acc1 = 0, acc2 = 0;
+      if (ok) {
 #pragma unroll
-    for (int j = 0; j < NB; j++) lo[j] = all[j] = 0;
-    if (ok) {
-#pragma unroll
-      for (int u = 0; u < A; u++) {
-        uint32_t w[8];
-        if (RV == 2) {
+        for (int u = 0; u < A; u++) {
+          uint32_t w[8];
           ld_record32(rec[u], w);
-        } else {
-          const uint4 v = __ldg(rec[u]);
-          w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-        }
-        sg ^= w[4 * RV - 1];   // the record's last word: the sign bits
-#pragma unroll
-        for (int j = 0; j < NB; j++) {
-          lo[j] += w[j] & 0xffffu;
-          all[j] += w[j];
+          acc0 += ((uint64_t)w[1] << 32) | w[0];
+          acc1 += ((uint64_t)w[3] << 32) | w[2];
+          acc2 += ((uint64_t)w[5] << 32) | w[4];
+          sg ^= w[7];
         }
       }
-    }
-    const int64_t word = g >> 5;
 #pragma unroll
-    for (int j = 0; j < 2 * NB; j++) {
-      if (j >= p.d) break;
-      const uint32_t sum = (j & 1) ? (all[j >> 1] - lo[j >> 1]) >> 16 : lo[j >> 1];
-      if (in) st_u16_hint(q.bins + (int64_t)j * q.W + g, (uint16_t)(sum & mask), pol);
-      const uint32_t sb = __ballot_sync(0xffffffffu, (sg >> j) & 1u);
-      if (lead) st_u32_hint(q.sgn + (int64_t)j * (q.W >> 5) + word, sb, pol);
+      for (int j = 0; j < 9; j++) {
+        if (j >= d) break;
+        const uint64_t acc = j < 3 ? acc0 : (j < 6 ? acc1 : acc2);
+        put(j, (uint32_t)(acc >> (20 * (j % 3))) & mask, (sg >> j) & 1u);
+      }
+    } else {
+      uint32_t lo[7], all[7];
+#pragma unroll
+      for (int j = 0; j < 7; j++) lo[j] = all[j] = 0;
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < A; u++) {
+          uint32_t w[8];
+          ld_record32(rec[u], w);
+          sg ^= w[7];
+#pragma unroll
+          for (int j = 0; j < 7; j++) {
+            lo[j] += w[j] & 0xffffu;
+            all[j] += w[j];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 14; j++) {
+        if (j >= d) break;
+        const uint32_t sum = (j & 1) ? (all[j >> 1] - lo[j >> 1]) >> 16 : lo[j >> 1];
+        put(j, sum & mask, (sg >> j) & 1u);
+      }
     }
   }
 }
 
-// blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row`, tuple range c of
-// nrange (ranges of seg tuples, a multiple of 256, taken with stride nrange * seg).  A
-// thread takes two units of 8 tuples per iteration (each: one 16-byte load of bins, 8 bits
-// of the sign and validity words), all loads issued before the atomics.
-// vw: bit k set when tuple k of the unit is in the window (all but the window's last unit: 0xff).
-__device__ __forceinline__ void part_unit(int* cnt, uint4 v, uint32_t sw, uint32_t vw, uint32_t base, uint32_t span) {
-  const uint32_t e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const uint32_t rel = ((e[k >> 1] >> (16 * (k & 1))) & 0xffffu) - base;   // outside the part: >= span
-    if (rel < span && ((vw >> k) & 1u)) atomicAdd(cnt + rel, 1 - (int)(((sw >> k) & 1u) << 1));
-  }
+// counter[idx] += v in shared memory when p is set: one predicated reduction, no branch
+__device__ __forceinline__ void red_shared_if(uint32_t saddr, int v, bool p) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}"
+               ::"r"(saddr), "r"(v), "r"((uint32_t)p) : "memory");
 }
 
-__device__ __forceinline__ uint32_t unit_mask(int64_t u, int64_t cnt) {
-  const int64_t r = cnt - (u << 3);
-  return r >= 8 ? 0xffu : ((1u << r) - 1u);
-}
-
+// blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row`, tile range c of nrange
+// (ranges of seg tuples, a multiple of 256, taken with stride nrange * seg).  A thread takes
+// 8 slots of one tile row (one 16-byte load and the tile row's count word) per unit; with
+// 1024 threads, unit u + 1024 is 256 tiles further at the same slot offset, so the thread's
+// pointers advance by a constant stride.  Two units per iteration, loads first.
 __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long long* ctr, int64_t m, int d,
                                                      int logL, int64_t seg, int nrange) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,26 +319,38 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
   const int L = 1 << logL;
   for (int k = threadIdx.x; k < L; k += blockDim.x) cnt[k] = 0;
   __syncthreads();
-  const uint16_t* bins = q.bins + (int64_t)row * q.W;
-  const uint32_t* sgn = q.sgn + (int64_t)row * (q.W >> 5);
-  const uint32_t base = (uint32_t)h << logL, span = (uint32_t)L;
-  const int64_t bd = blockDim.x;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(cnt);
+  const uint32_t off = (threadIdx.x & 3u) << 3;        // this thread's slots of a tile row: [off, off + 8)
+  const int64_t tstep = blockDim.x >> 2;                 // tiles between a thread's consecutive units
+  const int64_t istride = tstep * ((int64_t)d << 5);     // the same in items
+  const int64_t cstride = tstep * d;                     // and in count words
+  // slots [off, off + 8) of one tile row: add the signs of part h's items
+  auto unit = [&](uint4 v, uint32_t cw) {
+    const uint32_t lo = h ? (cw & 0xffu) : 0u;
+    const uint32_t n = h ? (cw >> 8) : (cw & 0xffu);
+    const uint32_t b = off - lo;                         // slot off + k is in part h when b + k < n
+    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
+      int neg;   // 0 or -1 from the item's sign bit
+      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
+      red_shared_if(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k < n);
+    }
+  };
   for (int64_t a = (int64_t)c * seg; a < q.cnt; a += (int64_t)nrange * seg) {
-    const int64_t ue = ((a + seg < q.cnt ? a + seg : q.cnt) + 7) >> 3;   // units [a / 8, ue)
-    int64_t u = (a >> 3) + threadIdx.x;
-    for (; u + bd < ue; u += 2 * bd) {
-      const int64_t u2 = u + bd;
-      const uint4 v1 = *(const uint4*)(bins + (u << 3));
-      const uint4 v2 = *(const uint4*)(bins + (u2 << 3));
-      const uint32_t s1 = __ldg(sgn + (u >> 2)), s2 = __ldg(sgn + (u2 >> 2));
-      const int sh1 = (int)(u & 3) << 3, sh2 = (int)(u2 & 3) << 3;
-      part_unit(cnt, v1, s1 >> sh1, unit_mask(u, q.cnt), base, span);
-      part_unit(cnt, v2, s2 >> sh2, unit_mask(u2, q.cnt), base, span);
+    const int64_t te = (a + seg < q.cnt ? a + seg : q.cnt) + 31 >> 5;   // tiles [a / 32, te)
+    int64_t t = (a >> 5) + (threadIdx.x >> 2);
+    const uint16_t* ip = q.items + (t * d + row) * 32 + off;
+    const uint16_t* cp = q.cnts + t * d + row;
+    for (; t + tstep < te; t += 2 * tstep, ip += 2 * istride, cp += 2 * cstride) {
+      const uint4 v1 = *(const uint4*)ip;
+      const uint4 v2 = *(const uint4*)(ip + istride);
+      const uint32_t c1 = __ldg(cp), c2 = __ldg(cp + cstride);
+      unit(v1, c1);
+      unit(v2, c2);
     }
-    if (u < ue) {
-      const int sh = (int)(u & 3) << 3;
-      part_unit(cnt, *(const uint4*)(bins + (u << 3)), __ldg(sgn + (u >> 2)) >> sh, unit_mask(u, q.cnt), base, span);
-    }
+    if (t < te) unit(*(const uint4*)ip, __ldg(cp));
   }
   __syncthreads();
   unsigned long long* out = ctr + (int64_t)row * m + ((int64_t)h << logL);
@@ -286,9 +361,9 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
 }
 
 // Persistent grid: as many CTAs as fit on the GPU (at most one tuple per thread).
-template <int A>
+template <int A, int FMT>
 cudaError_t launch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int sms, cudaStream_t st) {
-  auto kern = t.rvec == 2 ? k_tab_items<A, 2> : k_tab_items<A, 1>;
+  auto kern = k_tab_items<A, FMT>;
   // no shared memory: leave the whole unified array to L1, which caches the hot records
   cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   int per_sm = 0;
@@ -300,6 +375,17 @@ cudaError_t launch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs&
   return cudaGetLastError();
 }
 
+template <int FMT>
+cudaError_t dispatch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int sms, cudaStream_t st) {
+  switch (a.a) {
+    case 1: return launch_tab_items<1, FMT>(a, t, q, sms, st);
+    case 2: return launch_tab_items<2, FMT>(a, t, q, sms, st);
+    case 3: return launch_tab_items<3, FMT>(a, t, q, sms, st);
+    case 4: return launch_tab_items<4, FMT>(a, t, q, sms, st);
+    default: return launch_tab_items<5, FMT>(a, t, q, sms, st);
+  }
+}
+
 // SK_PART_UPDATE=0 keeps the single-phase k_update_tab for batches the partitioned update
 // could take; SK_PART_WINDOW caps the tuples per window (default and largest: 2^30, which
 // keeps every shared-memory counter of k_part_accum below 2^31 in magnitude).
@@ -308,51 +394,40 @@ int part_update_mode() {
   return (v && v[0] == '0') ? 0 : 1;
 }
 
-int64_t part_window_max() {
+int64_t part_window(int64_t n) {
   const char* v = std::getenv("SK_PART_WINDOW");
   const long long x = v ? std::atoll(v) : 0;
-  return (x > 0 && x < (1ll << 30)) ? (int64_t)x : ((int64_t)1 << 30);
+  const int64_t cap = (x > 0 && x < (1ll << 30)) ? (int64_t)x : ((int64_t)1 << 30);
+  return std::min<int64_t>((n + 255) / 256 * 256, (cap + 255) / 256 * 256);
 }
 
-// Both phases over every window of the batch (staging allocated from the stream-ordered
-// pool on st and released on st).  *ran false when the staging cannot be allocated.
-cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int sms, cudaStream_t st, bool* ran) {
-  *ran = false;
+size_t part_staging_bytes(int d, int64_t W) {
+  return (size_t)d * W * sizeof(uint16_t) + (size_t)d * (W / 32) * sizeof(uint16_t);
+}
+
+// Both phases over every window of the batch; staging (part_staging_bytes) is caller-owned.
+cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* staging, int sms, cudaStream_t st) {
   const int64_t n = a.n;
-  const int64_t W = std::min<int64_t>((n + 255) / 256 * 256, (part_window_max() + 255) / 256 * 256);
-  const size_t bin_bytes = (size_t)a.d * W * sizeof(uint16_t);
-  const size_t sgn_bytes = (size_t)a.d * (W / 32) * sizeof(uint32_t);
-  void* buf = nullptr;
-  cudaError_t e = pool_malloc_async(&buf, bin_bytes + sgn_bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cudaSuccess;
-  }
-  *ran = true;
+  const int64_t W = part_window(n);
   PartArgs q;
-  q.bins = (uint16_t*)buf;
-  q.sgn = (uint32_t*)((char*)buf + bin_bytes);
+  q.items = (uint16_t*)staging;
+  q.cnts = (uint16_t*)((char*)staging + (size_t)a.d * W * sizeof(uint16_t));
   q.W = W;
   int logm = 0;
   while (((int64_t)1 << logm) < (int64_t)a.m) logm++;
   const int logL = std::min(logm, 15);
+  q.logL = logL;
   const int S = (int)(a.m >> logL);
   const size_t smem = (size_t)4 << logL;
-  e = allow_dynamic_smem((const void*)k_part_accum);
+  cudaError_t e = allow_dynamic_smem((const void*)k_part_accum);
   int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part_accum, 1024, smem);
   const int64_t slots = (int64_t)sms * std::max(1, per_sm);
   const int64_t units = (int64_t)S * a.d;
   for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
-    q.i0 = i0;
     q.cnt = std::min(W, n - i0);
-    switch (a.a) {
-      case 1: e = launch_tab_items<1>(a, t, q, sms, st); break;
-      case 2: e = launch_tab_items<2>(a, t, q, sms, st); break;
-      case 3: e = launch_tab_items<3>(a, t, q, sms, st); break;
-      case 4: e = launch_tab_items<4>(a, t, q, sms, st); break;
-      default: e = launch_tab_items<5>(a, t, q, sms, st); break;
-    }
+    for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
+    e = fmt == 0 ? dispatch_tab_items<0>(a, t, q, sms, st) : dispatch_tab_items<1>(a, t, q, sms, st);
     if (e != cudaSuccess) break;
     // ranges per (row, part): the grid a whole number of waves when that takes 2..64 waves
     int64_t nr = 0;
@@ -366,8 +441,7 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int sms, cudaStr
     count_launch();
     e = cudaGetLastError();
   }
-  const cudaError_t ef = cudaFreeAsync(buf, st);
-  return e != cudaSuccess ? e : ef;
+  return e;
 }
 
 // SK_TAB_V8=0 reads 32-byte key-table records as two 16-byte loads instead of one.
@@ -759,24 +833,43 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
     t.base[rp.a] = total;
     t.narrow = s->m <= 65536 && s->d <= 32;
     t.rvec = key_record_vectors(s->d, t.narrow);
-    const size_t bytes = (size_t)total * (size_t)t.rvec * 16;
+    // The two-phase partitioned update (unit weights, power-of-two 1024 <= m <= 2^16, d <= 14,
+    // at most 5 attributes, sketch too large for one CTA's shared memory, at least 16 tuples
+    // per counter of a row) takes 32-byte records: the 20-bit lane format for d <= 9, the
+    // narrow format otherwise.
+    bool part = part_update_mode() != 0 && pow2 && weights == nullptr && rp.a <= 5 && !use_smem && s->m >= 1024 &&
+                s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16;
+    const int part_fmt = s->d <= 9 ? 0 : 1;
     // Automatic choice: the tables replace per-tuple hashing by gathers, which pays when
     // the domains are small against the batch and the counter updates hit L2 (for a sketch
     // much larger than L2 the update is bound by its atomics either way and the gathers
     // only add traffic: 27.7 vs 24.7 ms for 8 x 1e7 rows into 128 MB sketches).
     const bool worth = ktm == 1 || (total * 4 <= n * (int64_t)rp.a &&
                                     (size_t)s->d * (size_t)s->m * sizeof(int64_t) <= ((size_t)32 << 20));
+    void* staging = nullptr;
+    if (fits && worth && total > 0 && part) {
+      e = pool_malloc_async(&staging, part_staging_bytes(s->d, part_window(n)), st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();   // no room for the planes: single-phase update
+        staging = nullptr;
+        part = false;
+      }
+    }
+    if (part) t.rvec = 2;
+    const size_t bytes = (size_t)total * (size_t)t.rvec * 16;
     if (fits && worth && total > 0 && bytes <= key_table_max_bytes()) {
       void* buf = nullptr;
       e = pool_malloc_async(&buf, bytes, st);
       if (e != cudaSuccess) {
         cudaGetLastError();   // not enough memory for the table: hash per tuple instead
+        if (staging) cudaFreeAsync(staging, st);
       } else {
         t.tbl = (uint32_t*)buf;
         a.smem_wmax = 0;
         const bool d1 = all_deg1(a);
-        auto kb = pow2 ? (d1 ? k_key_table<true, true> : k_key_table<true, false>)
-                       : (d1 ? k_key_table<false, true> : k_key_table<false, false>);
+        auto kb = (part && part_fmt == 0) ? (d1 ? k_key_table_l20<true> : k_key_table_l20<false>)
+                  : pow2 ? (d1 ? k_key_table<true, true> : k_key_table<true, false>)
+                         : (d1 ? k_key_table<false, true> : k_key_table<false, false>);
         e = cudaSuccess;
         if (coef_bytes > 48 * 1024) e = allow_dynamic_smem((const void*)kb);
         if (e == cudaSuccess) {
@@ -785,12 +878,9 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
           count_launch();
           e = cudaGetLastError();
         }
-        bool part_done = false;
-        const bool part_ok = part_update_mode() != 0 && pow2 && t.narrow && t.rvec <= 2 && tab_v8_enabled() &&
-                             weights == nullptr && rp.a >= 1 && rp.a <= 5 && !use_smem && s->m >= 1024 &&
-                             n >= (int64_t)s->m * 16;
-        if (e == cudaSuccess && part_ok) e = run_partitioned(a, t, sms, st, &part_done);
-        if (e == cudaSuccess && !part_done) {
+        if (e == cudaSuccess && part) {
+          e = run_partitioned(a, t, part_fmt, staging, sms, st);
+        } else if (e == cudaSuccess) {
           if (use_smem) {
             const int per_sm = sub_bytes <= 48 * 1024 ? 4 : (sub_bytes <= 100 * 1024 ? 2 : 1);
             const int64_t want = (n + 256 * 16 - 1) / (256 * 16);
@@ -804,9 +894,15 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
             e = pow2 ? dispatch_tab<true, false>(a, t, grid, 0, st) : dispatch_tab<false, false>(a, t, grid, 0, st);
           }
         }
-        const cudaError_t ef = cudaFreeAsync(buf, st);
+        cudaError_t ef = cudaFreeAsync(buf, st);
+        if (staging) {
+          const cudaError_t es = cudaFreeAsync(staging, st);
+          if (ef == cudaSuccess) ef = es;
+        }
         return set_status_from_cuda(e != cudaSuccess ? e : ef);
       }
+    } else if (staging) {
+      cudaFreeAsync(staging, st);
     }
   }
   const bool cache_ok = !use_smem && pow2 && s->d <= 32 && rp.a >= 1 && rp.a <= 5 && s->m <= (1ll << 30) &&
