@@ -64,6 +64,9 @@ def parse_args():
                     help="exact estimator arithmetic of the star step (identical rows from each)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not overlap step i's estimate with step i+1's update")
+    ap.add_argument("--workloads", default="chain3,batched,chain8,serving,subqueries",
+                    help="configs run after the star step (one GPU only) and reported under 'workloads'")
+    ap.add_argument("--no-workloads", action="store_true", help="report the star step only")
     return ap.parse_args()
 
 
@@ -260,6 +263,14 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def gpu_id(local=0) -> str:
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return str(local)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -298,12 +309,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
 
-    gpu_uuid = "0"
-    try:
-        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_uuid = str(local)
-    clk = ClockSampler(gpu_uuid)
+    clk = ClockSampler(gpu_id(local))
     clk.start()
     time.sleep(0.25)
     launches0 = pkg.sk_launch_count()
@@ -399,30 +405,31 @@ def run_ours(args, world, rank, local):
     fact_s = fact_ms / 1e3
     tables = not args.no_domains
     if tables:
-        # The fact-table update call is two launches, timed together: k_key_table hashes the
-        # 5 x 1e6 declared domain keys once (d rows each) and k_update_tab runs the 1e8 tuples
-        # (5 key loads, 5 gathers of 32-byte records, 9 counter atomics each).
-        # HBM roofline (algorithmic bytes = the 40 key bytes per tuple; tables and sketch are
-        # meant to stay in L2).  traffic = DRAM bytes of one ncu capture of k_update_tab at
-        # 2e7 rows (1.448 GB, record misses included) scaled to this row count, plus the
-        # table write (5e6 records x 32 B).
-        # L2 roofline, the bound that binds: L2 tag lookups per tuple from the same capture
-        # (16.35 = 9 atomics + key and record reads + lookups forwarded between the two dies'
-        # L2 halves) against 188 slices x 1 lookup per cycle x 2.016 GHz.
-        traffic = 1.448e9 * args.fact_rows / 2e7 / 1e9 + 5 * 1_000_000 * 32 / 1e9
-        kernel = "k_key_table + k_update_tab<5,pow2,global,narrow,v8> (fact table F)"
-        l2_req_per_tuple = 16.35
+        # The fact-table update call is three launches, timed together: k_key_table_l20 hashes
+        # the 5 x 1e6 declared domain keys once (9 rows each, 32-byte records), k_tab_items
+        # gathers the five records of each of the 1e8 tuples and writes every row's bin into
+        # per-tile item planes (phase 1), k_part_accum adds them into half-row int32 sketches
+        # in shared memory and flushes each counter once (phase 2).
+        # HBM roofline: algorithmic bytes = the 40 key bytes per tuple.  traffic = DRAM bytes
+        # of one ncu capture of both phases at 2e7 rows (k_tab_items 1.4365 GB read + 0.3483 GB
+        # written, k_part_accum 0.3760 + 0.0040 GB: key stream, record misses and the item
+        # planes' round trip) scaled to this row count, plus the table write (5e6 x 32 B).
+        # L2 roofline beside it: L2 requests per tuple from the same capture (4.91: 3.87 in
+        # phase 1, 1.04 in phase 2; 16.35 with one 64-bit reduction per counter update).
+        traffic = (1.4365 + 0.3483 + 0.3760 + 0.0040) * args.fact_rows / 2e7 + 5 * 1_000_000 * 32 / 1e9
+        kernel = "k_key_table_l20 + k_tab_items<5,L20> + k_part_accum (fact table F, two-phase)"
+        l2_req_per_tuple = 4.91
         l2_peak = 188 * 2.016e9
         l2_rate = l2_req_per_tuple * args.fact_rows / fact_s
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kernel,
                     "work": "40 key bytes per fact tuple (5 int64 columns)",
-                    "traffic_unit": "GB per launch (ncu, 2e7-row launch scaled, + table write)",
+                    "traffic_unit": "GB per launch (ncu, 2e7-row launches scaled, + table write)",
                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}
-        extra = {"roofline_l2": {"bound": "l2_tag_lookups", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
-                                 "unit": "G lookups/s", "frac": l2_rate / l2_peak,
+        extra = {"roofline_l2": {"bound": "l2_requests", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
+                                 "unit": "G requests/s", "frac": l2_rate / l2_peak,
                                  "per_tuple": l2_req_per_tuple, "kernel": kernel,
-                                 "source": "ncu lts__t_tag_requests of k_update_tab (2e7 rows): 82.5 % of peak"}}
+                                 "source": "ncu lts__t_requests of k_tab_items + k_part_accum (2e7 rows)"}}
     else:
         # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
         # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the
@@ -442,7 +449,10 @@ def run_ours(args, world, rank, local):
                                   "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"}}
     # counter updates of the fact table (one per row and tuple), as a rate over the same call
     extra["counter_updates"] = {"per_tuple": wl.d, "achieved": wl.d * args.fact_rows / fact_s / 1e9,
-                                "unit": "G updates/s", "kind": "red.global.add.u64 into the L2-resident sketch"}
+                                "unit": "G updates/s",
+                                "kind": ("shared-memory reductions into half-row int32 sketches, one 64-bit flush per "
+                                         "counter and CTA" if tables else
+                                         "red.global.add.u64 into the L2-resident sketch")}
 
     serial = {"ms_per_step": ms_per_step, "value": value, "gpu_launches": launches}
     if pipe is not None and pipe["value"] > value:
@@ -490,6 +500,18 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline_1core"] = {"value": total / sec1, "unit": "tuples/s", "cores": 1, "kind": "oracle",
                                       "sample": desc1}
     s.close()
+    if not args.no_workloads and world == 1:
+        # every other configuration of the workload set, each with its own timed region,
+        # clock samples and parity checks, after the star's inputs are released
+        del rels, wl
+        torch.cuda.empty_cache()
+        line["workloads"] = {}
+        for name in [x for x in args.workloads.split(",") if x]:
+            try:
+                line["workloads"][name] = run_workload(args, world, rank, name)
+            except Exception as ex:   # one failing configuration must not hide the others
+                line["workloads"][name] = {"error": repr(ex)}
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -553,8 +575,10 @@ def run_batched(args, world, rank):
     +-1 weights with 10% deletions): one step resets the 256 sketches and applies every
     relation's batch, (a) one sk_sketch_reset and one sk_sketch_update_batch launch per
     relation, (b) one sk_update_plan_zero and one persistent sk_update_plan_run (autotuned),
-    (c) the same captured in a CUDA graph.  The sketches of (a) and (b) are compared after
-    timing."""
+    (c) the same captured in a CUDA graph.  Parity: the sketches of (a) and (b) are equal,
+    and the three smallest relations' sketches equal the CPU oracle's; the 256 estimates are
+    identical from one FP64 call per set, one fused call per set and one sk_estimate_many."""
+    import numpy as np
     import torch
 
     import paper_2402_15953_gb300 as pkg
@@ -595,6 +619,9 @@ def run_batched(args, world, rank):
         torch.cuda.synchronize()
         return max_over_ranks(world, e0.elapsed_time(e1) / steps)
 
+    clk = ClockSampler(gpu_id())
+    clk.start()
+    time.sleep(0.2)
     ms_a = timeit(step_a, args.steps)
     ms_b = timeit(step_b, args.steps)
     g = torch.cuda.CUDAGraph()
@@ -605,10 +632,22 @@ def run_batched(args, world, rank):
     with torch.cuda.graph(g, stream=side):
         step_b()
     ms_c = timeit(g.replay, args.steps)
+    clocks = clk.stop()
     step_a()
     step_b()
     torch.cuda.synchronize()
     same = all(torch.equal(x.counters, y.counters) for x, y in zip(sa, sb))
+    # the oracle on the three smallest relations (all d rows of relation 0)
+    import oracle as O
+    O.build()
+    oracle_ok = True
+    for i in sorted(range(len(wl)), key=lambda j: wl[j].relation.n)[:3]:
+        b = wl[i]
+        q = O.canonical_query(b.num_join_attrs, b.edges)
+        co = O.draw_coefficients(b.hash_seed, b.d, q.n_comp, len(q.edges))
+        want = O.sketch_relation(q, co, 0, b.relation.cols.cpu().numpy(), b.relation.weights.cpu().numpy(), b.m,
+                                 threads=os.cpu_count() or 1)
+        oracle_ok = oracle_ok and bool(np.array_equal(sb[i].counters[0].cpu().numpy(), want))
 
     # estimating all 256 sets: one sk_estimate_join per set (FP64, then fused) against one
     # sk_estimate_many call (fused sets grouped by width).  Each dimension relation first gets
@@ -616,6 +655,7 @@ def run_batched(args, world, rank):
     for s, b in zip(sb, wl):
         for k in range(1, len(b.num_join_attrs)):
             s.update(k, b.relation.cols[k - 1:k, :20_000].contiguous())
+
     def est_seq():
         return [x.estimate() for x in sb]
 
@@ -632,13 +672,13 @@ def run_batched(args, world, rank):
         return (time.perf_counter() - t0) * 1e3 / reps, out
 
     reps = max(1, args.steps // 5)
+    for x in sb:
+        x.set_estimator("fft64")
     seq_fft_ms, rows_fft = host_time(est_seq, reps)
     for x in sb:
         x.set_estimator("fused")
     seq_fu_ms, rows_fu = host_time(est_seq, reps)
     many_ms, rows_many = host_time(est_many, reps)
-    for x in sb:
-        x.set_estimator("fft64")
     est_same = [e["rows"] for e in rows_fft] == [e["rows"] for e in rows_many] == [e["rows"] for e in rows_fu]
     estimates = {"sets": len(sb), "one_call_per_set_fft64_ms": seq_fft_ms, "one_call_per_set_fused_ms": seq_fu_ms,
                  "estimate_many_fused_ms": many_ms, "estimates_per_s_many": len(sb) / (many_ms / 1e3),
@@ -651,13 +691,14 @@ def run_batched(args, world, rank):
                                    "columns (s in [0.8, 1.4], domains 1e4..1e7), m = 2^10..2^18, d = 7, +-1 weights "
                                    "with 10% deletions", "tuples_per_step": total},
             "per_relation_launches_ms": ms_a, "persistent_plan_ms": ms_b, "persistent_plan_graph_ms": ms_c,
-            "speedup_vs_per_relation": ms_a / ms_c, "identical_sketches": same, "autotuned": best,
-            "estimates": estimates}
+            "speedup_vs_per_relation": ms_a / ms_c, "autotuned": best, "estimates": estimates, "clocks": clocks,
+            "parity": {"plan_equals_per_relation": same, "smallest_3_relations_equal_oracle": oracle_ok,
+                       "estimates_identical_fft64_fused_many": est_same,
+                       "ok": bool(same and oracle_ok and est_same)}}
     plan.close()
     for s in sa + sb:
         s.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serving(args, world, rank):
@@ -665,7 +706,8 @@ def run_serving(args, world, rank):
     log-uniform 1e3..1e6 tuples (Zipf 1.1 keys over 1e6, 5% of rows deleted) and estimate
     requests, 10:1, Poisson arrivals; HBM budget 32 GB.  First every request is submitted
     at once (saturated throughput), then arrivals at 50% and 90% of that rate; latency =
-    arrival to result on the host."""
+    arrival to result on the host.  Parity: every estimate of the saturated run equals the
+    same request run one by one, and the oracle's for two sets."""
     import numpy as np
     import torch
 
@@ -738,10 +780,11 @@ def run_serving(args, world, rank):
         est = sorted(r.latency * 1e3 for r in reqs if r.kind == "estimate")
         tuples = sum(r.cols.shape[1] for r in reqs if r.kind == "update")
         errors = sum(1 for r in reqs if r.error)
+        rows = {j: r.result["rows"] for j, r in enumerate(reqs) if r.kind == "estimate" and r.result is not None}
         return {"requests": len(reqs), "wall_s": wall, "requests_per_s": len(reqs) / wall,
                 "tuples_per_s": tuples / wall, "p50_ms": lat[len(lat) // 2], "p99_ms": percentile(lat, 99.0),
                 "estimate_p50_ms": est[len(est) // 2] if est else None,
-                "estimate_p99_ms": percentile(est, 99.0) if est else None, "errors": errors}
+                "estimate_p99_ms": percentile(est, 99.0) if est else None, "errors": errors}, rows
 
     def sequential(trace):
         """Baseline: the same requests one at a time, each update a copy plus its own launch,
@@ -753,18 +796,19 @@ def run_serving(args, world, rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tuples = 0
-        for r in trace:
+        rows = {}
+        for j, r in enumerate(trace):
             if r[0] == "update":
                 live[r[1]].update(r[2], r[3].cuda(non_blocking=True), r[4].cuda(non_blocking=True))
                 torch.cuda.synchronize()
                 tuples += r[3].shape[1]
             else:
-                live[r[1]].estimate()
+                rows[j] = live[r[1]].estimate()["rows"]
         wall = time.perf_counter() - t0
         for x in live:
             x.close()
         return {"requests": len(trace), "wall_s": wall, "requests_per_s": len(trace) / wall,
-                "tuples_per_s": tuples / wall}
+                "tuples_per_s": tuples / wall}, rows
 
     def capacity(trace):
         """The server's own throughput: every request queued on a held server, then
@@ -785,12 +829,49 @@ def run_serving(args, world, rank):
         return {"requests": len(reqs), "wall_s": wall, "requests_per_s": len(reqs) / wall,
                 "tuples_per_s": tuples / wall, "errors": sum(1 for r in reqs if r.error)}
 
+    def oracle_check(trace, rows):
+        """The CPU oracle's Algorithm 3 for the last estimate of up to two two-relation sets
+        (whose estimate is one inner product per row), over that set's updates before it."""
+        import oracle as O
+        O.build()
+        cands = []
+        for sid, (a, e, m, d, sd) in enumerate(sets):
+            if len(a) != 2:
+                continue
+            last = max((j for j, r in enumerate(trace) if r[0] == "estimate" and r[1] == sid), default=None)
+            if last is None:
+                continue
+            n = sum(r[3].shape[1] for r in trace[:last] if r[0] == "update" and r[1] == sid)
+            cands.append((n, sid, last))
+        checked, ok = [], True
+        for n, sid, last in sorted(cands)[:2]:
+            a, e, m, d, sd = sets[sid]
+            q = O.canonical_query(a, e)
+            co = O.draw_coefficients(sd, d, q.n_comp, len(q.edges))
+            acc = [np.zeros((d, m), dtype=np.int64) for _ in a]
+            for r in trace[:last]:
+                if r[0] == "update" and r[1] == sid:
+                    acc[r[2]] += O.sketch_relation(q, co, r[2], r[3].numpy(), r[4].numpy(), m,
+                                                   threads=os.cpu_count() or 1)
+            ref = O.estimate(q, acc)
+            ok = ok and rows.get(last) == ref.rows
+            checked.append({"set": sid, "request": last, "tuples": n})
+        return ok, checked
+
     trace = make_trace(args.requests, 1)
     run(make_trace(200, 2), None)           # warm-up (scratch allocation, kernel attributes)
-    sat = run(trace, None)
-    points = {"saturated": sat, "server_capacity": capacity(trace), "sequential_one_by_one": sequential(trace)}
+    clk = ClockSampler(gpu_id())
+    clk.start()
+    time.sleep(0.2)
+    sat, sat_rows = run(trace, None)
+    cap = capacity(trace)
+    seq, seq_rows = sequential(trace)
+    points = {"saturated": sat, "server_capacity": cap, "sequential_one_by_one": seq}
     for frac in (0.5, 0.9):
-        points[f"rate_{int(frac * 100)}pct"] = run(trace, frac * sat["requests_per_s"])
+        points[f"rate_{int(frac * 100)}pct"], _ = run(trace, frac * sat["requests_per_s"])
+    clocks = clk.stop()
+    mixed_equal = set(sat_rows) == set(seq_rows) and all(sat_rows[j] == seq_rows[j] for j in seq_rows)
+    oracle_ok, checked = oracle_check(trace, seq_rows)
     line = {"metric": "serving: p50/p99 request latency and throughput", "value": sat["tuples_per_s"],
             "unit": "tuples/s", "n_gpus": world, "steps": args.requests, "warmup": 200,
             "ms_per_step": 1e3 / sat["requests_per_s"], "higher_is_better": True, "scaling": "weak",
@@ -799,9 +880,12 @@ def run_serving(args, world, rank):
             "config": {"workload": "64 live sets (chains of 2-6 relations, m = 2^14..2^18, d = 9); update batches "
                                    "log-uniform 1e3..1e6 tuples, Zipf 1.1 keys over 1e6, 5% deletions; 10 updates : "
                                    "1 estimate; Poisson arrivals; HBM budget 32 GB"},
-            "points": points}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "points": points, "capacity_vs_one_by_one": cap["requests_per_s"] / seq["requests_per_s"],
+            "clocks": clocks,
+            "parity": {"mixed_equals_one_by_one": mixed_equal, "estimates_compared": len(seq_rows),
+                       "oracle_last_estimate_of": checked, "oracle_equal": oracle_ok,
+                       "ok": bool(mixed_equal and oracle_ok and sat["errors"] == 0)}}
+    return line
 
 
 def run_e2e_direct(args, s, wl, stream, world):
@@ -896,13 +980,19 @@ def run_e2e_direct_pipelined(args, wl, world):
 def run_small_config(args, world, rank, which):
     """chain3: R1(A) - R2(A,B) - R3(B), 1e4 rows each, m = 256, d = 5 (launch-latency bound);
     chain8: 8-relation chain, 1e7 Zipf(1.2) rows each, m = 2^20, d = 16 (estimator at scale).
-    Times the update of all relations and the estimate separately with CUDA events."""
+    Times the update of all relations and the estimate separately with CUDA events.
+    Parity: chain3 in full against the CPU oracle (every sketch, every row, the median);
+    chain8 by identical rows from the three exact arithmetics and one sampled sketch row
+    of a two-column relation against the oracle."""
+    import numpy as np
     import torch
 
+    import oracle as O
     import paper_2402_15953_gb300 as pkg
     import synth
     from paper_2402_15953_gb300 import build as pkg_build
     pkg_build.build()
+    O.build()
     wl = synth.chain3(device="cuda") if which == "chain3" else synth.chain(device="cuda")
     s = pkg.SketchSet(wl.num_join_attrs, wl.edges, wl.m, wl.d, wl.hash_seed)
     s.set_estimator(args.estimator)
@@ -920,6 +1010,9 @@ def run_small_config(args, world, rank, which):
         est = s.estimate()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     up, es = [], []
+    clk = ClockSampler(gpu_id())
+    clk.start()
+    time.sleep(0.2)
     for _ in range(reps):
         e[0].record(stream)
         upd()
@@ -929,6 +1022,38 @@ def run_small_config(args, world, rank, which):
         torch.cuda.synchronize()
         up.append(e[0].elapsed_time(e[1]))
         es.append(e[1].elapsed_time(e[2]))
+    clocks = clk.stop()
+    by_arith, arith_ms = {}, {}
+    for arith in ("fft64", "ntt", "fused"):
+        s.set_estimator(arith)
+        s.estimate()                      # scratch and twiddles for this arithmetic
+        e[0].record(stream)
+        by_arith[arith] = s.estimate()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        arith_ms[arith] = e[0].elapsed_time(e[1])
+    s.set_estimator(args.estimator)
+    same = all(x["rows"] == est["rows"] for x in by_arith.values())
+    q = O.canonical_query(wl.num_join_attrs, wl.edges)
+    co = O.draw_coefficients(wl.hash_seed, wl.d, q.n_comp, len(q.edges))
+    threads = os.cpu_count() or 1
+    if which == "chain3":
+        rels = [(r.cols.cpu().numpy(), None) for r in wl.relations]
+        sk = O.sketch_all(q, co, rels, wl.m, threads=threads)
+        got = s.counters.cpu().numpy()
+        ref = O.estimate(q, sk)
+        sk_ok = all(np.array_equal(got[k], sk[k]) for k in range(len(sk)))
+        parity = {"sketches_equal_oracle": sk_ok, "rows_equal_oracle": est["rows"] == ref.rows,
+                  "median_equal_oracle": est["median"] == ref.median, "arithmetics_identical": same,
+                  "exact_join_size": str(O.exact_join_size(q, rels)),
+                  "ok": bool(sk_ok and est["rows"] == ref.rows and est["median"] == ref.median and same)}
+    else:
+        k, row = 3, 5   # a two-column inner relation, one of its 16 rows
+        ref = O.sketch_relation(q, co[[row]], k, wl.relations[k].cols.cpu().numpy(), None, wl.m, threads=threads)
+        row_ok = bool(np.array_equal(s.counters[k][row].cpu().numpy(), ref[0]))
+        parity = {"arithmetics_identical": same, "sampled_sketch_row_equals_oracle": {"relation": k, "row": row,
+                                                                                      "equal": row_ok},
+                  "ok": bool(same and row_ok)}
     tot = sum(r.n for r in wl.relations)
     ms = statistics.mean(up) + statistics.mean(es)
     line = {"metric": f"{which}: update and estimate time", "value": tot / (ms / 1e3), "unit": "tuples/s",
@@ -938,11 +1063,10 @@ def run_small_config(args, world, rank, which):
             "config": {"workload": which, "tuples_per_step": tot, "m": wl.m, "d": wl.d},
             "update_us": 1e3 * statistics.mean(up), "estimate_us": 1e3 * statistics.mean(es),
             "estimate_p99_us": 1e3 * percentile(es, 99.0), "estimates_per_s": 1e3 / statistics.mean(es),
-            "median": str(est["median"]), "max_residual": est["max_residual"], "max_limbs": est["max_limbs"],
-            "limb_bits": est["limb_bits"]}
+            "estimate_ms_by_arithmetic": arith_ms, "median": str(est["median"]), "max_limbs": est["max_limbs"],
+            "clocks": clocks, "parity": parity}
     s.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_subqueries(args, world, rank):
@@ -952,7 +1076,8 @@ def run_subqueries(args, world, rank):
     every relation and estimates every sub-query.  Family: one sk_family (one pass per relation,
     19 shared view sketches, sub-queries estimated on worker streams).  Against: one
     SketchSet per sub-query (47 relation sketches, each relation updated once per sub-query it
-    is in, estimates one after another)."""
+    is in, estimates one after another).  Parity: the full sub-query's rows equal a plain set's,
+    and the sub-query of join 0 equals the CPU oracle on two rows."""
     import itertools
 
     import torch
@@ -1007,6 +1132,9 @@ def run_subqueries(args, world, rank):
         return (time.perf_counter() - t0) * 1e3 / reps, out
 
     reps = max(3, args.steps // 3)
+    clk = ClockSampler(gpu_id())
+    clk.start()
+    time.sleep(0.2)
     launches0 = pkg.sk_launch_count()
     fam_ms, fam_out = timed(fam_step, reps)
     launches = (pkg.sk_launch_count() - launches0) // (reps + max(1, args.warmup))
@@ -1021,8 +1149,21 @@ def run_subqueries(args, world, rank):
     torch.cuda.synchronize()
     fam_upd_ms = e0.elapsed_time(e1) / reps
     naive_ms, naive_out = timed(naive_step, reps)
+    clocks = clk.stop()
     info = fam.info()
     same_full = fam_out[-1]["rows"] == naive_out[-1]["rows"]
+    # the oracle for sub-query {join 0} (F's first column with D1; an inner product per row),
+    # rows 0 and 1, with the functions Section 3.4's reuse assigns it
+    import oracle as O
+    O.build()
+    q = O.canonical_query(wl.num_join_attrs, wl.edges)
+    co = O.draw_coefficients(wl.hash_seed, wl.d, q.n_comp, len(q.edges))
+    sq = O.subquery(wl.num_join_attrs, wl.edges, co, subs[0])
+    rels = [(r.cols.cpu().numpy(), None) for r in wl.relations]
+    sub_rels = O.subquery_relations(sq, rels)
+    sk = O.sketch_all(sq.query, sq.coeffs[[0, 1]], sub_rels, wl.m, threads=os.cpu_count() or 1)
+    ref = O.estimate(sq.query, sk)
+    oracle_ok = fam_out[0]["rows"][:2] == ref.rows
     line = {"metric": "sub-query family: estimates/s of all connected sub-queries with their updates",
             "value": world * len(subs) / (fam_ms / 1e3), "unit": "sub-query estimates/s", "n_gpus": world,
             "steps": reps, "warmup": args.warmup, "ms_per_step": fam_ms, "higher_is_better": True,
@@ -1035,13 +1176,13 @@ def run_subqueries(args, world, rank):
                        "views": info["views"], "counter_bytes": info["counter_bytes"],
                        "gpu_launches_per_step": launches},
             "one_set_per_subquery": {"ms_per_step": naive_ms, "relation_sketches": sum(len(c) for _, c in naive)},
-            "speedup": naive_ms / fam_ms,
-            "full_query_rows_equal_plain_set": same_full}
+            "speedup": naive_ms / fam_ms, "clocks": clocks,
+            "parity": {"full_query_rows_equal_plain_set": same_full,
+                       "subquery_join0_rows_0_1_equal_oracle": oracle_ok, "ok": bool(same_full and oracle_ok)}}
     for sset, _ in naive:
         sset.close()
     fam.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_shapes(args, world, rank):
@@ -1101,19 +1242,25 @@ def run_shapes(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_workload(args, world, rank, name):
+    if name == "batched":
+        return run_batched(args, world, rank)
+    if name == "serving":
+        return run_serving(args, world, rank)
+    if name in ("chain3", "chain8"):
+        return run_small_config(args, world, rank, name)
+    return run_subqueries(args, world, rank)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.workload == "batched":
-        run_batched(args, world, rank)
-    elif args.workload == "serving":
-        run_serving(args, world, rank)
-    elif args.workload in ("chain3", "chain8"):
-        run_small_config(args, world, rank, args.workload)
-    elif args.workload == "subqueries":
-        run_subqueries(args, world, rank)
+    elif args.workload in ("batched", "serving", "chain3", "chain8", "subqueries"):
+        line = run_workload(args, world, rank, args.workload)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     elif args.workload == "shapes":
         run_shapes(args, world, rank)
     else:

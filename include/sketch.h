@@ -379,8 +379,14 @@ sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t c
  *   do not fit.  Sets must not be updated or estimated outside the server meanwhile.
  * sk_server_submit_update: queues Algorithm 2 for n_rows tuples of `relation` from
  *   host memory (int64 attribute-major columns with col_stride >= n_rows, optional
- *   int64 weights; page-locked memory lets the copy overlap).  The host buffers must
- *   stay valid until the request has finished.  *request_id names the request.
+ *   int64 weights; page-locked memory lets the copy overlap; domain_hint: NULL or the
+ *   relation's |Omega| exclusive key bounds, copied at submission, as for
+ *   sk_sketch_update_batch).  The host buffers must stay valid until the request has
+ *   finished.  *request_id names the request.  The updates admitted in one scheduling
+ *   pass are coalesced: one staging buffer and one persistent multi-item launch for those
+ *   without declared domains (up to 64 per batch, at most update_slots batches in
+ *   flight), one sk_sketch_update_batch call each for those with declared domains (so a
+ *   large batch can take the key tables); results are the same as one launch per update.
  *   A request that could never fit (more memory than the budget leaves beside the
  *   registered sets' counters) finishes at once with status SK_ERR_OVER_BUDGET, and an
  *   update of zero rows finishes at once with SK_OK.
@@ -394,6 +400,7 @@ sk_status sk_set_coefficients(sk_set* set, const uint64_t* host_coeffs, size_t c
  *   them at once.  sk_server_drain on a held server with queued requests does not return.
  * sk_server_pending: the number of submitted requests not yet finished.
  * sk_server_drain: blocks until every submitted request has finished.
+ * sk_server_stats: update batches launched so far and the update requests they held.
  * sk_server_destroy: drains, stops the threads and releases the server (not the sets).
  * Errors: SK_ERR_INVALID_ARG (null, unknown set or request, bad relation or sizes),
  * SK_ERR_OVER_BUDGET, SK_ERR_CUDA, SK_ERR_NO_MEMORY; a request's own status carries
@@ -404,13 +411,14 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
 sk_status sk_server_register_set(sk_server* server, int32_t set_id, sk_set* set);
 sk_status sk_server_submit_update(sk_server* server, int32_t set_id, int32_t relation, int64_t n_rows,
                                   const int64_t* host_cols, int64_t col_stride, const int64_t* host_weights,
-                                  int64_t* request_id);
+                                  const int64_t* domain_hint, int64_t* request_id);
 sk_status sk_server_submit_estimate(sk_server* server, int32_t set_id, int64_t* request_id);
 sk_status sk_server_result(sk_server* server, int64_t request_id, int32_t wait, int32_t* finished,
                            sk_status* status, sk_estimate* est, double* arrival_s, double* done_s);
 sk_status sk_server_hold(sk_server* server, int32_t on);
 sk_status sk_server_pending(sk_server* server, int64_t* n);
 sk_status sk_server_drain(sk_server* server);
+sk_status sk_server_stats(sk_server* server, int64_t* batches, int64_t* batched_updates);
 sk_status sk_server_destroy(sk_server* server);
 
 /* sk_launch_count: number of CUDA kernels this library has launched in this process

@@ -86,7 +86,8 @@ EXPORTS = ["sk_sketch_bytes", "sk_sketch_create", "sk_sketch_update_batch", "sk_
            "sk_get_coefficients", "sk_set_coefficients", "sk_sketch_reset", "sk_launch_count",
            "sk_estimate_join_noalloc", "sk_sketch_set_estimator", "sk_update_plan_create", "sk_update_plan_run", "sk_update_plan_zero", "sk_update_plan_get_config",
            "sk_server_create", "sk_server_register_set", "sk_server_submit_update", "sk_server_submit_estimate",
-           "sk_server_result", "sk_server_hold", "sk_server_pending", "sk_server_drain", "sk_server_destroy",
+           "sk_server_result", "sk_server_hold", "sk_server_pending", "sk_server_drain", "sk_server_stats",
+           "sk_server_destroy",
            "sk_update_plan_set_config", "sk_update_plan_autotune", "sk_update_plan_destroy",
            "sk_family_create", "sk_family_update_batch", "sk_family_estimate", "sk_family_set_estimator",
            "sk_family_info", "sk_family_view", "sk_family_copy_sketch", "sk_family_reset", "sk_family_sync",
@@ -128,7 +129,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sk_update_plan_zero.argtypes = [vp, vp]
     L.sk_server_create.argtypes = [i64, i32, i32, i32, ctypes.POINTER(vp)]
     L.sk_server_register_set.argtypes = [vp, i32, vp]
-    L.sk_server_submit_update.argtypes = [vp, i32, i32, i64, vp, i64, vp, ctypes.POINTER(i64)]
+    L.sk_server_submit_update.argtypes = [vp, i32, i32, i64, vp, i64, vp, vp, ctypes.POINTER(i64)]
+    L.sk_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.sk_server_submit_estimate.argtypes = [vp, i32, ctypes.POINTER(i64)]
     L.sk_server_result.argtypes = [vp, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(sk_estimate),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]

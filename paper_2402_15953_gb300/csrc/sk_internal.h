@@ -96,6 +96,18 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
                         const int64_t* weights, const int64_t* domain, cudaStream_t st);
 sk_status launch_merge(int64_t* dst, const int64_t* src, int64_t count, cudaStream_t st);
 
+// sk_multi.cu: the persistent multi-item update behind sk_update_plan_* and the serving loop.
+size_t multi_item_size();   // bytes of one device descriptor
+// Fills n descriptors (n * multi_item_size() bytes of host memory at desc) for items whose
+// n_rows are all > 0, under cfg; the launch's chunk count, coefficient words and dynamic
+// shared memory come back.  SK_ERR_INVALID_ARG when the shared memory would exceed 200 KB.
+sk_status multi_describe(const sk_update_item* items, int n, const sk_update_plan_config& cfg, void* desc,
+                         int64_t* total_chunks, int* coef_words, size_t* smem_bytes);
+// One persistent launch over n descriptors already in device memory (d_queue: an 8-byte
+// work counter, zeroed here on st).
+sk_status multi_launch(const void* d_desc, int n, int64_t total_chunks, const sk_update_plan_config& cfg,
+                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st);
+
 // sk_estimate.cu
 sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st);
 sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st);

@@ -164,32 +164,17 @@ int sms() {
 }
 
 }  // namespace
-}  // namespace sk
 
-using namespace sk;
+size_t multi_item_size() { return sizeof(MultiItem); }
 
-struct sk_update_plan {
-  std::vector<sk_update_item> items;
-  std::vector<MultiItem> host;
-  sk_update_plan_config cfg{};
-  MultiItem* d_items = nullptr;
-  unsigned long long* d_queue = nullptr;
-  int n_active = 0;
-  int64_t total_chunks = 0;
-  int coef_words = 0;
-  size_t smem_bytes = 0;
-};
-
-namespace {
-
-sk_status plan_build(sk_update_plan* pl) {
-  pl->host.clear();
+sk_status multi_describe(const sk_update_item* items, int n, const sk_update_plan_config& cfg, void* desc,
+                         int64_t* total_chunks, int* coef_words_out, size_t* smem_bytes) {
+  MultiItem* out = (MultiItem*)desc;
   int64_t chunk0 = 0;
   int coef_words = 0;
   int64_t sub_words = 0;
-  const sk_update_plan_config& cfg = pl->cfg;
-  for (const sk_update_item& it : pl->items) {
-    if (it.n_rows == 0) continue;
+  for (int i = 0; i < n; i++) {
+    const sk_update_item& it = items[i];
     sk_set* s = it.set;
     const RelPlan& rp = s->rel[it.relation];
     MultiItem mi;
@@ -228,13 +213,56 @@ sk_status plan_build(sk_update_plan* pl) {
     chunk0 += (it.n_rows + cfg.chunk_tuples - 1) / cfg.chunk_tuples;
     coef_words = std::max(coef_words, s->d * rp.coef_row_len);
     if (mi.use_smem) sub_words = std::max(sub_words, mi.use_smem == 1 ? dm : (dm + 1) / 2);
-    pl->host.push_back(mi);
+    out[i] = mi;
   }
-  pl->n_active = (int)pl->host.size();
-  pl->total_chunks = chunk0;
-  pl->coef_words = (coef_words + 1) & ~1;
-  pl->smem_bytes = (size_t)pl->coef_words * 8 + (size_t)sub_words * 4;
-  if (pl->smem_bytes > 200 * 1024) return SK_ERR_INVALID_ARG;
+  *total_chunks = chunk0;
+  *coef_words_out = (coef_words + 1) & ~1;
+  *smem_bytes = (size_t)(*coef_words_out) * 8 + (size_t)sub_words * 4;
+  return *smem_bytes > 200 * 1024 ? SK_ERR_INVALID_ARG : SK_OK;
+}
+
+sk_status multi_launch(const void* d_desc, int n, int64_t total_chunks, const sk_update_plan_config& cfg,
+                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st) {
+  if (total_chunks == 0) return SK_OK;
+  cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  e = allow_dynamic_smem((const void*)k_update_multi);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(total_chunks, (int64_t)sms() * cfg.ctas_per_sm));
+  k_update_multi<<<grid, cfg.threads, smem_bytes, st>>>((const MultiItem*)d_desc, n, total_chunks, cfg.chunk_tuples,
+                                                        coef_words, d_queue);
+  count_launch();
+  return set_status_from_cuda(cudaGetLastError());
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+struct sk_update_plan {
+  std::vector<sk_update_item> items;
+  std::vector<MultiItem> host;
+  sk_update_plan_config cfg{};
+  MultiItem* d_items = nullptr;
+  unsigned long long* d_queue = nullptr;
+  int n_active = 0;
+  int64_t total_chunks = 0;
+  int coef_words = 0;
+  size_t smem_bytes = 0;
+};
+
+namespace {
+
+sk_status plan_build(sk_update_plan* pl) {
+  pl->host.clear();
+  std::vector<sk_update_item> active;
+  for (const sk_update_item& it : pl->items)
+    if (it.n_rows > 0) active.push_back(it);
+  pl->host.resize(active.size());
+  sk_status st = multi_describe(active.data(), (int)active.size(), pl->cfg, pl->host.data(), &pl->total_chunks,
+                                &pl->coef_words, &pl->smem_bytes);
+  if (st != SK_OK) return st;
+  pl->n_active = (int)active.size();
   if (pl->d_items) {
     cudaFree(pl->d_items);
     pl->d_items = nullptr;
@@ -284,18 +312,8 @@ sk_status sk_update_plan_create(const sk_update_item* items, int32_t n_items, sk
 
 sk_status sk_update_plan_run(sk_update_plan* pl, void* cuda_stream) {
   if (!pl) return SK_ERR_INVALID_ARG;
-  if (pl->total_chunks == 0) return SK_OK;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  cudaError_t e = cudaMemsetAsync(pl->d_queue, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return set_status_from_cuda(e);
-  e = allow_dynamic_smem((const void*)k_update_multi);
-  if (e != cudaSuccess) return set_status_from_cuda(e);
-  const int64_t want = pl->total_chunks;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms() * pl->cfg.ctas_per_sm));
-  k_update_multi<<<grid, pl->cfg.threads, pl->smem_bytes, st>>>(pl->d_items, pl->n_active, pl->total_chunks,
-                                                                pl->cfg.chunk_tuples, pl->coef_words, pl->d_queue);
-  count_launch();
-  return set_status_from_cuda(cudaGetLastError());
+  return multi_launch(pl->d_items, pl->n_active, pl->total_chunks, pl->cfg, pl->coef_words, pl->smem_bytes,
+                      pl->d_queue, (cudaStream_t)cuda_stream);
 }
 
 sk_status sk_update_plan_zero(sk_update_plan* pl, void* cuda_stream) {

@@ -11,14 +11,20 @@
 //    each set, oldest first, as soon as an update slot (a bounded number of in-flight
 //    update batches) or an estimate worker is free and its device memory fits the HBM
 //    budget, so newly arrived work joins the work already running on the device.
-//  - Updates: the host columns are copied into a stream-ordered staging buffer on the
-//    copy stream; the update runs on the update stream after that copy; an event marks
-//    its end and the set's last admitted update.  Estimates: one worker thread per
-//    estimate stream takes up to kEstBatch admitted estimates at a time (of distinct
+//  - Updates are coalesced: every update admitted in one scheduling pass (across sets, and
+//    consecutive updates of one set) forms one batch.  Its host columns are copied into one
+//    stream-ordered staging buffer on the copy stream, then ONE persistent multi-item
+//    launch on the update stream applies all of the batch's plain updates (sketches are
+//    linear, Section 2.2: the counters receive the same sums in any order or grouping);
+//    updates that declare key domains run as their own sk_sketch_update_batch calls, so a
+//    large one can take the key tables.  An event marks the batch's end and each touched
+//    set's last admitted update; a pass that meets an estimate launches its batch first.
+//  - Estimates: one worker thread per estimate stream takes up to kEstBatch admitted
+//    estimates at a time (of distinct
 //    sets: a set has one admitted estimate at most), its stream waits for each set's
 //    last update, and one many-set estimate runs them (fused sets of one width share
 //    their transforms).
-//  - A retire thread waits on the oldest in-flight update's event (updates complete in
+//  - A retire thread waits on the oldest in-flight batch's event (batches complete in
 //    launch order on the single update stream) and releases its slot and memory; the
 //    scheduler sleeps on a condition variable until a submission, a retired update or a
 //    finished estimate changes what can be admitted.  No thread polls.
@@ -43,7 +49,8 @@ using sk::set_status_from_cuda;
 
 namespace {
 
-constexpr int kEstBatch = 8;   // estimates a worker runs together
+constexpr int kEstBatch = 8;    // estimates a worker runs together
+constexpr int kUpdBatch = 64;   // updates coalesced into one batch at most
 struct SvRequest {
   int64_t id = 0;
   bool is_estimate = false;
@@ -53,12 +60,21 @@ struct SvRequest {
   const int64_t* cols = nullptr;   // host, attribute-major, stride `stride`
   int64_t stride = 0;
   const int64_t* w = nullptr;      // host or null
+  std::vector<int64_t> domain;     // declared key domains (empty: none)
   size_t bytes = 0;                // memory charged while admitted
   double arrival = 0.0, done = 0.0;
   bool finished = false;
   sk_status status = SK_OK;
   sk_estimate est;
-  cudaEvent_t ev = nullptr;        // update: end of the update on the update stream
+};
+
+// Updates admitted together: one staging buffer, one multi-item launch (plus one call per
+// update with declared domains), one completion event.
+struct SvBatch {
+  std::vector<SvRequest*> reqs;
+  size_t bytes = 0;                // charged against the budget (sum of the requests')
+  cudaEvent_t ev = nullptr;
+  int slot = -1;                   // pinned descriptor slot
 };
 
 struct SvSet {
@@ -91,7 +107,11 @@ struct sk_server {
   std::condition_variable est_cv;    // estimate workers
   std::map<int32_t, SvSet> sets;
   std::map<int64_t, std::unique_ptr<SvRequest>> reqs;
-  std::deque<SvRequest*> inflight;   // launched updates, launch order
+  std::deque<SvBatch*> inflight;     // launched update batches, launch order
+  char* desc_host = nullptr;         // pinned descriptors: `slots` blocks of kUpdBatch descriptors
+  std::vector<int> free_desc;        // free descriptor blocks
+  sk_update_plan_config cfg{};       // launch configuration of the batches
+  uint64_t batches = 0, batched_updates = 0;
   std::deque<SvRequest*> est_queue;  // admitted estimates
   int64_t next_id = 1;
   int64_t unfinished = 0;
@@ -108,34 +128,7 @@ size_t update_bytes(const sk_set* s, int relation, int64_t n, bool weights) {
   return (size_t)n * 8 * ((size_t)s->num_join_attrs[relation] + (weights ? 1 : 0));
 }
 
-// Launches one admitted update (called with the lock held).
-sk_status launch_update(sk_server* sv, SvSet& ss, SvRequest* q) {
-  sk_set* s = ss.set;
-  const int a = s->num_join_attrs[q->relation];
-  const size_t col_bytes = (size_t)q->n * 8 * a;
-  void* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, q->bytes, sv->copy_stream);
-  if (e != cudaSuccess) return set_status_from_cuda(e);
-  int64_t* dc = (int64_t*)buf;
-  int64_t* dw = q->w ? (int64_t*)((char*)buf + col_bytes) : nullptr;
-  e = cudaMemcpy2DAsync(dc, (size_t)q->n * 8, q->cols, (size_t)q->stride * 8, (size_t)q->n * 8, (size_t)a,
-                        cudaMemcpyHostToDevice, sv->copy_stream);
-  if (e == cudaSuccess && dw) e = cudaMemcpyAsync(dw, q->w, (size_t)q->n * 8, cudaMemcpyHostToDevice, sv->copy_stream);
-  cudaEvent_t copied = nullptr;
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(copied, sv->copy_stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->update_stream, copied, 0);
-  if (copied) cudaEventDestroy(copied);
-  sk_status st = set_status_from_cuda(e);
-  if (st == SK_OK) st = sk_sketch_update_batch(s, q->relation, q->n, dc, q->n, dw, nullptr, sv->update_stream);
-  e = cudaFreeAsync(buf, sv->update_stream);
-  if (st == SK_OK) st = set_status_from_cuda(e);
-  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
-  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(q->ev, sv->update_stream));
-  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(ss.last_update, sv->update_stream));
-  if (st == SK_OK) ss.has_update = true;
-  return st;
-}
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 void finish(sk_server* sv, SvRequest* q, sk_status st) {
   q->status = st;
@@ -145,31 +138,115 @@ void finish(sk_server* sv, SvRequest* q, sk_status st) {
   sv->changed = true;
 }
 
+// Launches one batch of admitted updates (called with the lock held).  Layout of its staging
+// buffer: work counter (256 B) | descriptors | per request: columns, weights (256-aligned).
+sk_status launch_batch(sk_server* sv, SvBatch* b) {
+  const size_t dsz = sk::multi_item_size();
+  size_t total = 256 + align256(dsz * b->reqs.size());
+  for (SvRequest* q : b->reqs) total += align256(q->bytes);
+  char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&buf, total, sv->copy_stream);
+  if (e != cudaSuccess) return set_status_from_cuda(e);
+  std::vector<sk_update_item> items;
+  std::vector<std::pair<SvRequest*, std::pair<int64_t*, int64_t*>>> direct;   // requests with domains
+  size_t off = 256 + align256(dsz * b->reqs.size());
+  for (SvRequest* q : b->reqs) {
+    sk_set* s = sv->sets[q->set_id].set;
+    const int a = s->num_join_attrs[q->relation];
+    int64_t* dc = (int64_t*)(buf + off);
+    int64_t* dw = q->w ? dc + (size_t)q->n * a : nullptr;
+    off += align256(q->bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dc, (size_t)q->n * 8, q->cols, (size_t)q->stride * 8, (size_t)q->n * 8, (size_t)a,
+                            cudaMemcpyHostToDevice, sv->copy_stream);
+    if (e == cudaSuccess && dw) e = cudaMemcpyAsync(dw, q->w, (size_t)q->n * 8, cudaMemcpyHostToDevice, sv->copy_stream);
+    if (!q->domain.empty() || a > 5) direct.push_back({q, {dc, dw}});
+    else items.push_back(sk_update_item{s, q->relation, q->n, dc, q->n, dw});
+  }
+  int64_t chunks = 0;
+  int coef_words = 0;
+  size_t smem = 0;
+  char* desc = sv->desc_host + (size_t)b->slot * kUpdBatch * dsz;
+  sk_status st = set_status_from_cuda(e);
+  if (st == SK_OK && !items.empty()) {
+    st = sk::multi_describe(items.data(), (int)items.size(), sv->cfg, desc, &chunks, &coef_words, &smem);
+    if (st == SK_OK)
+      st = set_status_from_cuda(cudaMemcpyAsync(buf + 256, desc, dsz * items.size(), cudaMemcpyHostToDevice,
+                                                sv->copy_stream));
+  }
+  cudaEvent_t copied = nullptr;
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(copied, sv->copy_stream));
+  if (st == SK_OK) st = set_status_from_cuda(cudaStreamWaitEvent(sv->update_stream, copied, 0));
+  if (copied) cudaEventDestroy(copied);
+  if (st == SK_OK && !items.empty())
+    st = sk::multi_launch(buf + 256, (int)items.size(), chunks, sv->cfg, coef_words, smem,
+                          (unsigned long long*)buf, sv->update_stream);
+  for (auto& dq : direct) {
+    if (st != SK_OK) break;
+    SvRequest* q = dq.first;
+    st = sk_sketch_update_batch(sv->sets[q->set_id].set, q->relation, q->n, dq.second.first, q->n,
+                                dq.second.second, q->domain.empty() ? nullptr : q->domain.data(), sv->update_stream);
+  }
+  const cudaError_t ef = cudaFreeAsync(buf, sv->update_stream);
+  if (st == SK_OK) st = set_status_from_cuda(ef);
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+  if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(b->ev, sv->update_stream));
+  for (SvRequest* q : b->reqs) {
+    SvSet& ss = sv->sets[q->set_id];
+    if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(ss.last_update, sv->update_stream));
+    if (st == SK_OK) ss.has_update = true;
+  }
+  sv->batches++;
+  sv->batched_updates += b->reqs.size();
+  return st;
+}
+
+// Launches the pass's batch, if any (lock held); on failure its requests finish with the error.
+void flush_batch(sk_server* sv, SvBatch*& b) {
+  if (!b) return;
+  const sk_status st = launch_batch(sv, b);
+  if (st != SK_OK) {
+    if (b->ev) cudaEventDestroy(b->ev);
+    sv->used -= b->bytes;
+    for (SvRequest* q : b->reqs) finish(sv, q, st);
+    sv->free_desc.push_back(b->slot);
+    delete b;
+  } else {
+    sv->inflight.push_back(b);
+  }
+  b = nullptr;
+}
+
 // One scheduling pass (lock held): heads of the sets' queues in global arrival order.
 void admit(sk_server* sv) {
   std::vector<std::pair<int64_t, int32_t>> heads;
   for (auto& kv : sv->sets)
     if (!kv.second.queue.empty() && !kv.second.estimating) heads.push_back({kv.second.queue.front()->id, kv.first});
   std::sort(heads.begin(), heads.end());
+  SvBatch* b = nullptr;
   for (const auto& h : heads) {
     SvSet& ss = sv->sets[h.second];
     while (!ss.queue.empty() && !ss.estimating) {
       SvRequest* q = ss.queue.front();
       if (!q->is_estimate) {
-        if ((int)sv->inflight.size() >= sv->slots || sv->used + q->bytes > sv->budget) break;
+        if (!b && sv->free_desc.empty()) break;                      // every update slot in flight
+        if (b && (int)b->reqs.size() >= kUpdBatch) break;
+        if (sv->used + q->bytes > sv->budget) break;
+        if (!b) {
+          b = new (std::nothrow) SvBatch();
+          if (!b) return;
+          b->slot = sv->free_desc.back();
+          sv->free_desc.pop_back();
+        }
         ss.queue.pop_front();
         sv->used += q->bytes;
-        const sk_status st = launch_update(sv, ss, q);
-        if (st != SK_OK) {
-          if (q->ev) cudaEventDestroy(q->ev);
-          q->ev = nullptr;
-          sv->used -= q->bytes;
-          finish(sv, q, st);
-          continue;
-        }
-        sv->inflight.push_back(q);
+        b->bytes += q->bytes;
+        b->reqs.push_back(q);
       } else {
         if (sv->est_free == 0 || sv->used + ss.est_bytes > sv->budget) break;
+        // the estimate waits for this set's last update event: launch the pending batch first
+        flush_batch(sv, b);
         ss.queue.pop_front();
         q->bytes = ss.est_bytes;
         sv->used += q->bytes;
@@ -181,6 +258,7 @@ void admit(sk_server* sv) {
       }
     }
   }
+  flush_batch(sv, b);
 }
 
 void scheduler(sk_server* sv) {
@@ -201,15 +279,16 @@ void retirer(sk_server* sv) {
   for (;;) {
     sv->cv.wait(lk, [&] { return !sv->inflight.empty() || sv->stop; });
     if (sv->inflight.empty()) return;   // stop with nothing in flight
-    SvRequest* q = sv->inflight.front();
+    SvBatch* b = sv->inflight.front();
     lk.unlock();
-    const cudaError_t e = cudaEventSynchronize(q->ev);
+    const cudaError_t e = cudaEventSynchronize(b->ev);
     lk.lock();
     sv->inflight.pop_front();
-    cudaEventDestroy(q->ev);
-    q->ev = nullptr;
-    sv->used -= q->bytes;
-    finish(sv, q, set_status_from_cuda(e));
+    cudaEventDestroy(b->ev);
+    sv->used -= b->bytes;
+    for (SvRequest* q : b->reqs) finish(sv, q, set_status_from_cuda(e));
+    sv->free_desc.push_back(b->slot);
+    delete b;
     sv->cv.notify_all();
   }
 }
@@ -279,6 +358,16 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->update_stream, cudaStreamNonBlocking);
+  // pinned descriptor blocks, one per update slot (a batch's descriptors are copied from
+  // its block asynchronously, so the block stays reserved until the batch retires)
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&sv->desc_host, (size_t)update_slots * kUpdBatch * sk::multi_item_size(),
+                      cudaHostAllocDefault);
+  for (int i = 0; i < update_slots; i++) sv->free_desc.push_back(update_slots - 1 - i);
+  // batches: chunks of 16384 tuples, 6 CTAs per SM, int32 shared sub-sketches up to 16384
+  // counters (the plan defaults of sk_update_plan_create but with smaller chunks: serving
+  // batches are 1e3..1e6 tuples)
+  sv->cfg = sk_update_plan_config{16384, 256, 6, 16384, 0};
   for (int i = 0; i < estimate_workers && e == cudaSuccess; i++) {
     cudaStream_t s = nullptr;
     e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, estimate_priority ? hi : lo);
@@ -288,6 +377,7 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
     for (cudaStream_t s : sv->est_streams) cudaStreamDestroy(s);
     if (sv->copy_stream) cudaStreamDestroy(sv->copy_stream);
     if (sv->update_stream) cudaStreamDestroy(sv->update_stream);
+    if (sv->desc_host) cudaFreeHost(sv->desc_host);
     delete sv;
     return set_status_from_cuda(e);
   }
@@ -321,7 +411,7 @@ sk_status sk_server_register_set(sk_server* sv, int32_t set_id, sk_set* set) {
 
 sk_status sk_server_submit_update(sk_server* sv, int32_t set_id, int32_t relation, int64_t n_rows,
                                   const int64_t* host_cols, int64_t col_stride, const int64_t* host_weights,
-                                  int64_t* request_id) {
+                                  const int64_t* domain_hint, int64_t* request_id) {
   if (!sv || !request_id || n_rows < 0) return SK_ERR_INVALID_ARG;
   std::unique_ptr<SvRequest> q(new (std::nothrow) SvRequest());
   if (!q) return SK_ERR_NO_MEMORY;
@@ -338,6 +428,7 @@ sk_status sk_server_submit_update(sk_server* sv, int32_t set_id, int32_t relatio
   q->cols = host_cols;
   q->stride = col_stride;
   q->w = host_weights;
+  if (domain_hint) q->domain.assign(domain_hint, domain_hint + s->num_join_attrs[relation]);
   q->bytes = update_bytes(s, relation, n_rows, host_weights != nullptr);
   q->arrival = now_s(sv->t0);
   *request_id = q->id;
@@ -452,7 +543,16 @@ sk_status sk_server_destroy(sk_server* sv) {
   cudaStreamDestroy(sv->update_stream);
   for (auto& kv : sv->sets)
     if (kv.second.last_update) cudaEventDestroy(kv.second.last_update);
+  cudaFreeHost(sv->desc_host);
   delete sv;
+  return SK_OK;
+}
+
+sk_status sk_server_stats(sk_server* sv, int64_t* batches, int64_t* batched_updates) {
+  if (!sv) return SK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (batches) *batches = (int64_t)sv->batches;
+  if (batched_updates) *batched_updates = (int64_t)sv->batched_updates;
   return SK_OK;
 }
 

@@ -85,7 +85,9 @@ class SketchServer:
 
     # ---- submission -----------------------------------------------------------------
     def submit_update(self, set_id: int, relation: int, cols: torch.Tensor,
-                      weights: Optional[torch.Tensor] = None) -> Request:
+                      weights: Optional[torch.Tensor] = None, domain=None) -> Request:
+        """Queues an update; domain: None or the relation's per-column exclusive key bounds
+        (as SketchSet.update), copied at submission."""
         if cols.is_cuda:
             cols = cols.cpu()
         if cols.dtype != torch.int64 or cols.dim() != 2:
@@ -99,10 +101,13 @@ class SketchServer:
         n = int(cols.shape[1])
         rid = ctypes.c_int64()
         req = Request("update", set_id, relation=relation, cols=cols, weights=weights)
+        dom = None if domain is None else (ctypes.c_int64 * len(domain))(*[int(x) for x in domain])
         with self._lock:
             _ck(self._L.sk_server_submit_update(self.handle, int(set_id), int(relation), n,
                                                 cols.data_ptr() if n else None, int(cols.stride(0)) if n else 0,
-                                                None if weights is None else weights.data_ptr(), ctypes.byref(rid)),
+                                                None if weights is None else weights.data_ptr(),
+                                                None if dom is None else ctypes.cast(dom, ctypes.c_void_p),
+                                                ctypes.byref(rid)),
                 "sk_server_submit_update")
             req.seq = rid.value
             self._open[req.seq] = req
@@ -142,6 +147,12 @@ class SketchServer:
     def hold(self, on: bool = True) -> None:
         """Pauses (on) or resumes admission; submitted requests queue while held."""
         _ck(self._L.sk_server_hold(self.handle, 1 if on else 0), "sk_server_hold")
+
+    def stats(self) -> dict:
+        """Update batches launched so far and the update requests they held."""
+        b, u = ctypes.c_int64(), ctypes.c_int64()
+        _ck(self._L.sk_server_stats(self.handle, ctypes.byref(b), ctypes.byref(u)), "sk_server_stats")
+        return {"batches": int(b.value), "batched_updates": int(u.value)}
 
     def pending(self) -> int:
         n = ctypes.c_int64()

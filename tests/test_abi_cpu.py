@@ -93,7 +93,8 @@ def test_batched_serving_and_many_argument_checks(lib):
     rid, n = ctypes.c_int64(), ctypes.c_int64()
     fin = ctypes.c_int32()
     assert lib.sk_server_register_set(None, 0, None) == inv
-    assert lib.sk_server_submit_update(None, 0, 0, 0, None, 0, None, ctypes.byref(rid)) == inv
+    assert lib.sk_server_submit_update(None, 0, 0, 0, None, 0, None, None, ctypes.byref(rid)) == inv
+    assert lib.sk_server_stats(None, None, None) == inv
     assert lib.sk_server_submit_estimate(None, 0, ctypes.byref(rid)) == inv
     assert lib.sk_server_result(None, 1, 0, ctypes.byref(fin), None, None, None, None) == inv
     assert lib.sk_server_hold(None, 1) == inv

@@ -167,4 +167,31 @@ def test_hold_then_release_equals_alone():
     for j in alone:
         assert handles[j].error is None and handles[j].result["rows"] == alone[j]["rows"] == ref[j].rows
         assert handles[j].result["median"] == ref[j].median
+    st = srv.stats()
+    n_upd = sum(1 for r in reqs if r[0] == "update")
+    assert st["batched_updates"] == n_upd and st["batches"] < n_upd   # released at once: coalesced
+    srv.close()
+
+
+def test_coalesced_updates_with_declared_domains():
+    """Updates that declare key domains (launched as their own calls inside a batch, key
+    tables allowed) mixed with plain ones: every estimate equals the oracle's."""
+    sets, reqs = _trace(7, n_sets=4, n_req=40)
+    srv = SketchServer()
+    for i, (a, e, m, d, s) in enumerate(sets):
+        assert srv.register_set(i, a, e, m, d, s)
+    srv.hold(True)
+    handles = {}
+    for j, r in enumerate(reqs):
+        if r[0] == "update":
+            dom = [1 << 20] * r[3].shape[0] if j % 2 else None
+            srv.submit_update(r[1], r[2], r[3], r[4], domain=dom)
+        else:
+            handles[j] = srv.submit_estimate(r[1])
+    srv.hold(False)
+    srv.serve()
+    ref = _oracle_expected(sets, reqs)
+    for j, h in handles.items():
+        assert h.error is None, h.error
+        assert h.result["rows"] == ref[j].rows and h.result["median"] == ref[j].median
     srv.close()
