@@ -179,7 +179,13 @@ sk_status sk_sketch_update_batch(sk_set* set, int32_t relation, int64_t n_rows, 
  * |Delta| <= 32767 / chunk_tuples go there, so no counter leaves [0, 2^16) within a
  * chunk and the packed adds are exact; the others update global memory; 0 = never).
  * sk_update_plan_autotune times a set of configurations on the plan itself (every
- * timed run updates the counters: reset them afterwards) and keeps the fastest.
+ * timed run updates the counters: reset them afterwards) and keeps the fastest.  The
+ * choice is persisted: keyed by the device's SM count, the plan's item shapes (m, d and
+ * attribute count, with their counts) and the log2 of its tuple count, it is appended to a
+ * JSON-lines file (SK_AUTOTUNE_CACHE, else autotune.json beside libsketch.so;
+ * SK_AUTOTUNE_CACHE=off disables it), and a later autotune of a plan with the same key takes
+ * the stored configuration without timing (or updating the counters); *best_ms is then the
+ * stored time.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA, SK_ERR_NO_MEMORY. */
 typedef struct {
   sk_set* set;

@@ -104,9 +104,10 @@ size_t multi_item_size();   // bytes of one device descriptor
 sk_status multi_describe(const sk_update_item* items, int n, const sk_update_plan_config& cfg, void* desc,
                          int64_t* total_chunks, int* coef_words, size_t* smem_bytes);
 // One persistent launch over n descriptors already in device memory (d_queue: an 8-byte
-// work counter, zeroed here on st).
+// work counter, zeroed here on st when zero_queue, else already zero).
 sk_status multi_launch(const void* d_desc, int n, int64_t total_chunks, const sk_update_plan_config& cfg,
-                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st);
+                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st,
+                       bool zero_queue);
 
 // sk_estimate.cu
 sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st);

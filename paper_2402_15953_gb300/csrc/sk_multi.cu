@@ -5,10 +5,18 @@
 // a small d x m accumulate each chunk in an int32 shared-memory sub-sketch that is
 // flushed into the int64 counters at the end of the chunk; items up to twice as large
 // can use 16-bit counters packed two per word instead (see sk_update_plan_config).
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "sk_hash.cuh"
@@ -222,9 +230,10 @@ sk_status multi_describe(const sk_update_item* items, int n, const sk_update_pla
 }
 
 sk_status multi_launch(const void* d_desc, int n, int64_t total_chunks, const sk_update_plan_config& cfg,
-                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st) {
+                       int coef_words, size_t smem_bytes, unsigned long long* d_queue, cudaStream_t st,
+                       bool zero_queue) {
   if (total_chunks == 0) return SK_OK;
-  cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
+  cudaError_t e = zero_queue ? cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st) : cudaSuccess;
   if (e != cudaSuccess) return set_status_from_cuda(e);
   e = allow_dynamic_smem((const void*)k_update_multi);
   if (e != cudaSuccess) return set_status_from_cuda(e);
@@ -276,6 +285,81 @@ sk_status plan_build(sk_update_plan* pl) {
   return SK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent autotuning choices.  A plan's key is the device's SM count and the sorted
+// shapes of its items ((m, d, attributes) with their counts, and the log2 of its tuple
+// count); sk_update_plan_autotune looks the key up in a JSON-lines file (one object per line:
+// key, chunk_tuples, threads, ctas_per_sm, smem_max_counters, smem16_max_counters, ms) and
+// times its configuration grid only on a miss, appending the winner.  File:
+// SK_AUTOTUNE_CACHE, else autotune.json beside libsketch.so; SK_AUTOTUNE_CACHE=off disables it.
+// ---------------------------------------------------------------------------
+std::string tune_key(const sk_update_plan* pl) {
+  std::map<std::tuple<int64_t, int, int>, int> shapes;
+  int64_t tuples = 0;
+  for (const sk_update_item& it : pl->items) {
+    if (it.n_rows == 0) continue;
+    shapes[std::make_tuple(it.set->m, it.set->d, it.set->rel[it.relation].a)]++;
+    tuples += it.n_rows;
+  }
+  int lg = 0;
+  while (lg < 62 && ((int64_t)1 << (lg + 1)) <= tuples) lg++;
+  std::string k = "sms=" + std::to_string(sms()) + ";tuples=2^" + std::to_string(lg) + ";";
+  for (const auto& kv : shapes)
+    k += "m" + std::to_string(std::get<0>(kv.first)) + ".d" + std::to_string(std::get<1>(kv.first)) + ".a" +
+         std::to_string(std::get<2>(kv.first)) + "x" + std::to_string(kv.second) + ",";
+  return k;
+}
+
+std::string tune_cache_path() {
+  const char* v = std::getenv("SK_AUTOTUNE_CACHE");
+  if (v && std::strcmp(v, "off") == 0) return std::string();
+  if (v && v[0]) return std::string(v);
+  Dl_info info;
+  if (dladdr((const void*)&tune_cache_path, &info) && info.dli_fname) {
+    std::string lib(info.dli_fname);
+    const size_t slash = lib.rfind('/');
+    if (slash != std::string::npos) return lib.substr(0, slash + 1) + "autotune.json";
+  }
+  return std::string();
+}
+
+std::mutex g_tune_mu;
+
+bool tune_cache_find(const std::string& path, const std::string& key, sk_update_plan_config* cfg, double* ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return false;
+  char line[4096];
+  bool found = false;
+  const std::string want = "{\"key\": \"" + key + "\", ";
+  while (std::fgets(line, sizeof(line), f)) {
+    if (std::strncmp(line, want.c_str(), want.size()) != 0) continue;
+    sk_update_plan_config c{};
+    double t = 0.0;
+    if (std::sscanf(line + want.size(),
+                    "\"chunk_tuples\": %d, \"threads\": %d, \"ctas_per_sm\": %d, \"smem_max_counters\": %d, "
+                    "\"smem16_max_counters\": %d, \"ms\": %lf",
+                    &c.chunk_tuples, &c.threads, &c.ctas_per_sm, &c.smem_max_counters, &c.smem16_max_counters, &t) == 6) {
+      *cfg = c;   // the last matching line wins
+      *ms = t;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_cache_store(const std::string& path, const std::string& key, const sk_update_plan_config& c, double ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;   // read-only location: tuning still applies to this plan
+  std::fprintf(f,
+               "{\"key\": \"%s\", \"chunk_tuples\": %d, \"threads\": %d, \"ctas_per_sm\": %d, "
+               "\"smem_max_counters\": %d, \"smem16_max_counters\": %d, \"ms\": %.6f}\n",
+               key.c_str(), c.chunk_tuples, c.threads, c.ctas_per_sm, c.smem_max_counters, c.smem16_max_counters, ms);
+  std::fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
@@ -313,7 +397,7 @@ sk_status sk_update_plan_create(const sk_update_item* items, int32_t n_items, sk
 sk_status sk_update_plan_run(sk_update_plan* pl, void* cuda_stream) {
   if (!pl) return SK_ERR_INVALID_ARG;
   return multi_launch(pl->d_items, pl->n_active, pl->total_chunks, pl->cfg, pl->coef_words, pl->smem_bytes,
-                      pl->d_queue, (cudaStream_t)cuda_stream);
+                      pl->d_queue, (cudaStream_t)cuda_stream, true);
 }
 
 sk_status sk_update_plan_zero(sk_update_plan* pl, void* cuda_stream) {
@@ -349,6 +433,15 @@ sk_status sk_update_plan_set_config(sk_update_plan* pl, const sk_update_plan_con
 sk_status sk_update_plan_autotune(sk_update_plan* pl, void* cuda_stream, sk_update_plan_config* best,
                                   double* best_ms) {
   if (!pl) return SK_ERR_INVALID_ARG;
+  const std::string key = tune_key(pl);
+  const std::string path = tune_cache_path();
+  sk_update_plan_config cached;
+  double cached_ms = 0.0;
+  if (!path.empty() && tune_cache_find(path, key, &cached, &cached_ms) && sk_update_plan_set_config(pl, &cached) == SK_OK) {
+    if (best) *best = cached;
+    if (best_ms) *best_ms = cached_ms;
+    return SK_OK;
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int chunks[] = {8192, 32768, 131072};
   const int ctas[] = {4, 8};
@@ -389,6 +482,7 @@ sk_status sk_update_plan_autotune(sk_update_plan* pl, void* cuda_stream, sk_upda
   sk_status s2 = sk_update_plan_set_config(pl, &bestc);
   if (best) *best = bestc;
   if (best_ms) *best_ms = bestt;
+  if (s2 == SK_OK && !path.empty()) tune_cache_store(path, key, bestc, bestt);
   return s2;
 }
 

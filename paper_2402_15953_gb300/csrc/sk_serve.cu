@@ -108,8 +108,10 @@ struct sk_server {
   std::map<int32_t, SvSet> sets;
   std::map<int64_t, std::unique_ptr<SvRequest>> reqs;
   std::deque<SvBatch*> inflight;     // launched update batches, launch order
-  char* desc_host = nullptr;         // pinned descriptors: `slots` blocks of kUpdBatch descriptors
-  std::vector<int> free_desc;        // free descriptor blocks
+  char* desc_host = nullptr;         // pinned blocks, one per slot: zeroed work counter + descriptors
+  size_t desc_block = 0;             // bytes per block
+  std::vector<cudaEvent_t> ev_copied, ev_done;   // per slot, reused by its batches
+  std::vector<int> free_desc;        // free slots
   sk_update_plan_config cfg{};       // launch configuration of the batches
   uint64_t batches = 0, batched_updates = 0;
   std::deque<SvRequest*> est_queue;  // admitted estimates
@@ -140,16 +142,20 @@ void finish(sk_server* sv, SvRequest* q, sk_status st) {
 
 // Launches one batch of admitted updates (called with the lock held).  Layout of its staging
 // buffer: work counter (256 B) | descriptors | per request: columns, weights (256-aligned).
+// The work counter's zero and the descriptors come from the slot's pinned block in one copy.
+// A batch of one update without declared domains is a plain sk_sketch_update_batch call.
 sk_status launch_batch(sk_server* sv, SvBatch* b) {
   const size_t dsz = sk::multi_item_size();
-  size_t total = 256 + align256(dsz * b->reqs.size());
+  const size_t head = 256 + align256(dsz * b->reqs.size());
+  size_t total = head;
   for (SvRequest* q : b->reqs) total += align256(q->bytes);
   char* buf = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&buf, total, sv->copy_stream);
   if (e != cudaSuccess) return set_status_from_cuda(e);
   std::vector<sk_update_item> items;
-  std::vector<std::pair<SvRequest*, std::pair<int64_t*, int64_t*>>> direct;   // requests with domains
-  size_t off = 256 + align256(dsz * b->reqs.size());
+  std::vector<std::pair<SvRequest*, std::pair<int64_t*, int64_t*>>> direct;   // own calls
+  size_t off = head;
+  const bool single = b->reqs.size() == 1;
   for (SvRequest* q : b->reqs) {
     sk_set* s = sv->sets[q->set_id].set;
     const int a = s->num_join_attrs[q->relation];
@@ -160,28 +166,27 @@ sk_status launch_batch(sk_server* sv, SvBatch* b) {
       e = cudaMemcpy2DAsync(dc, (size_t)q->n * 8, q->cols, (size_t)q->stride * 8, (size_t)q->n * 8, (size_t)a,
                             cudaMemcpyHostToDevice, sv->copy_stream);
     if (e == cudaSuccess && dw) e = cudaMemcpyAsync(dw, q->w, (size_t)q->n * 8, cudaMemcpyHostToDevice, sv->copy_stream);
-    if (!q->domain.empty() || a > 5) direct.push_back({q, {dc, dw}});
+    if (single || !q->domain.empty() || a > 5) direct.push_back({q, {dc, dw}});
     else items.push_back(sk_update_item{s, q->relation, q->n, dc, q->n, dw});
   }
   int64_t chunks = 0;
   int coef_words = 0;
   size_t smem = 0;
-  char* desc = sv->desc_host + (size_t)b->slot * kUpdBatch * dsz;
+  char* blk = sv->desc_host + (size_t)b->slot * sv->desc_block;
   sk_status st = set_status_from_cuda(e);
   if (st == SK_OK && !items.empty()) {
-    st = sk::multi_describe(items.data(), (int)items.size(), sv->cfg, desc, &chunks, &coef_words, &smem);
+    std::memset(blk, 0, 256);
+    st = sk::multi_describe(items.data(), (int)items.size(), sv->cfg, blk + 256, &chunks, &coef_words, &smem);
     if (st == SK_OK)
-      st = set_status_from_cuda(cudaMemcpyAsync(buf + 256, desc, dsz * items.size(), cudaMemcpyHostToDevice,
+      st = set_status_from_cuda(cudaMemcpyAsync(buf, blk, 256 + dsz * items.size(), cudaMemcpyHostToDevice,
                                                 sv->copy_stream));
   }
-  cudaEvent_t copied = nullptr;
-  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+  const cudaEvent_t copied = sv->ev_copied[b->slot];
   if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(copied, sv->copy_stream));
   if (st == SK_OK) st = set_status_from_cuda(cudaStreamWaitEvent(sv->update_stream, copied, 0));
-  if (copied) cudaEventDestroy(copied);
   if (st == SK_OK && !items.empty())
     st = sk::multi_launch(buf + 256, (int)items.size(), chunks, sv->cfg, coef_words, smem,
-                          (unsigned long long*)buf, sv->update_stream);
+                          (unsigned long long*)buf, sv->update_stream, false);
   for (auto& dq : direct) {
     if (st != SK_OK) break;
     SvRequest* q = dq.first;
@@ -190,7 +195,7 @@ sk_status launch_batch(sk_server* sv, SvBatch* b) {
   }
   const cudaError_t ef = cudaFreeAsync(buf, sv->update_stream);
   if (st == SK_OK) st = set_status_from_cuda(ef);
-  if (st == SK_OK) st = set_status_from_cuda(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+  b->ev = sv->ev_done[b->slot];
   if (st == SK_OK) st = set_status_from_cuda(cudaEventRecord(b->ev, sv->update_stream));
   for (SvRequest* q : b->reqs) {
     SvSet& ss = sv->sets[q->set_id];
@@ -207,7 +212,6 @@ void flush_batch(sk_server* sv, SvBatch*& b) {
   if (!b) return;
   const sk_status st = launch_batch(sv, b);
   if (st != SK_OK) {
-    if (b->ev) cudaEventDestroy(b->ev);
     sv->used -= b->bytes;
     for (SvRequest* q : b->reqs) finish(sv, q, st);
     sv->free_desc.push_back(b->slot);
@@ -284,7 +288,6 @@ void retirer(sk_server* sv) {
     const cudaError_t e = cudaEventSynchronize(b->ev);
     lk.lock();
     sv->inflight.pop_front();
-    cudaEventDestroy(b->ev);
     sv->used -= b->bytes;
     for (SvRequest* q : b->reqs) finish(sv, q, set_status_from_cuda(e));
     sv->free_desc.push_back(b->slot);
@@ -360,9 +363,15 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->update_stream, cudaStreamNonBlocking);
   // pinned descriptor blocks, one per update slot (a batch's descriptors are copied from
   // its block asynchronously, so the block stays reserved until the batch retires)
-  if (e == cudaSuccess)
-    e = cudaHostAlloc((void**)&sv->desc_host, (size_t)update_slots * kUpdBatch * sk::multi_item_size(),
-                      cudaHostAllocDefault);
+  sv->desc_block = 256 + align256(kUpdBatch * sk::multi_item_size());
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&sv->desc_host, (size_t)update_slots * sv->desc_block, cudaHostAllocDefault);
+  for (int i = 0; i < update_slots && e == cudaSuccess; i++) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
+    if (a) sv->ev_copied.push_back(a);
+    if (b) sv->ev_done.push_back(b);
+  }
   for (int i = 0; i < update_slots; i++) sv->free_desc.push_back(update_slots - 1 - i);
   // batches: chunks of 16384 tuples, 6 CTAs per SM, int32 shared sub-sketches up to 16384
   // counters (the plan defaults of sk_update_plan_create but with smaller chunks: serving
@@ -378,6 +387,8 @@ sk_status sk_server_create(int64_t hbm_budget_bytes, int32_t update_slots, int32
     if (sv->copy_stream) cudaStreamDestroy(sv->copy_stream);
     if (sv->update_stream) cudaStreamDestroy(sv->update_stream);
     if (sv->desc_host) cudaFreeHost(sv->desc_host);
+    for (cudaEvent_t x : sv->ev_copied) cudaEventDestroy(x);
+    for (cudaEvent_t x : sv->ev_done) cudaEventDestroy(x);
     delete sv;
     return set_status_from_cuda(e);
   }
@@ -544,6 +555,8 @@ sk_status sk_server_destroy(sk_server* sv) {
   for (auto& kv : sv->sets)
     if (kv.second.last_update) cudaEventDestroy(kv.second.last_update);
   cudaFreeHost(sv->desc_host);
+  for (cudaEvent_t x : sv->ev_copied) cudaEventDestroy(x);
+  for (cudaEvent_t x : sv->ev_done) cudaEventDestroy(x);
   delete sv;
   return SK_OK;
 }

@@ -166,3 +166,34 @@ def test_full_size_batched_workload_sampled_against_oracle():
     plan.close()
     for s in sets:
         s.close()
+
+
+def test_autotune_choice_is_persisted(workload, tmp_path, monkeypatch):
+    """The first autotune of a plan shape times the grid and appends its winner to the cache
+    file; a second plan of the same shape takes it from there without timing (its counters
+    stay untouched) and still gives the item-by-item counters."""
+    cache = tmp_path / "autotune.json"
+    monkeypatch.setenv("SK_AUTOTUNE_CACHE", str(cache))
+    sub = workload[:12]
+    a = _sets(sub)
+    plan_a = pkg.UpdatePlan([(s, 0, b.relation.cols, b.relation.weights) for s, b in zip(a, sub)])
+    best_a, ms_a = plan_a.autotune()
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"key": "sms=' in lines[0]
+    b = _sets(sub)
+    plan_b = pkg.UpdatePlan([(s, 0, bb.relation.cols, bb.relation.weights) for s, bb in zip(b, sub)])
+    best_b, ms_b = plan_b.autotune()
+    assert best_b == best_a and ms_b == pytest.approx(ms_a, rel=1e-5)
+    assert len(cache.read_text().splitlines()) == 1
+    assert all(int(torch.count_nonzero(s.counters)) == 0 for s in b)   # not timed: nothing applied
+    plan_b.run()
+    ref = _sets(sub)
+    for s, bb in zip(ref, sub):
+        s.update(0, bb.relation.cols, bb.relation.weights)
+    torch.cuda.synchronize()
+    for x, y in zip(b, ref):
+        assert torch.equal(x.counters, y.counters)
+    for p in (plan_a, plan_b):
+        p.close()
+    for s in a + b + ref:
+        s.close()
