@@ -237,17 +237,19 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
       kx[u] = kin ? (uint32_t)k : 0u;
     }
     const uint32_t vb = __ballot_sync(0xffffffffu, ok);
+    const uint32_t nv = __popc(vb), rv = __popc(vb & lt);   // valid tuples in the tile / before this lane
     uint16_t* ip = q.items + ((g >> 5) * d << 5);   // this tile's row 0
     uint16_t* cp = q.cnts + (g >> 5) * d;
-    // one row: compact the tile's valid tuples by part (part 0 first) and store the counts
+    // one row: compact the tile's valid tuples by part (part 0 first) and store the counts;
+    // with r1 the part-1 tuples before this lane, a part-1 tuple goes to c0 + r1 and a part-0
+    // one to rv - r1
     auto put = [&](int j, uint32_t bin, uint32_t neg) {
       const bool hi = (bin >> q.logL) != 0;
       const uint32_t hb = __ballot_sync(0xffffffffu, ok && hi);
-      const uint32_t lb = vb & ~hb;
-      const uint32_t c0 = __popc(lb);
-      const uint32_t pos = hi ? c0 + __popc(hb & lt) : __popc(lb & lt);
+      const uint32_t n1 = __popc(hb), c0 = nv - n1, r1 = __popc(hb & lt);
+      const uint32_t pos = hi ? c0 + r1 : rv - r1;
       if (ok) st_u16_hint(ip + 32 * j + pos, (uint16_t)((bin & low) | (neg << 15)), pol);
-      if (lane == 0) st_u16_hint(cp + j, (uint16_t)(c0 | ((uint32_t)__popc(hb) << 8)), pol);
+      if (lane == 0) st_u16_hint(cp + j, (uint16_t)(c0 | (n1 << 8)), pol);
     };
     uint32_t sg = 0;
     if (FMT == 0) {
@@ -296,10 +298,10 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
   }
 }
 
-// counter[idx] += v in shared memory when p is set: one predicated reduction, no branch
-__device__ __forceinline__ void red_shared_if(uint32_t saddr, int v, bool p) {
-  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}"
-               ::"r"(saddr), "r"(v), "r"((uint32_t)p) : "memory");
+// shared counter at saddr += v when x < n (unsigned): one compare, one predicated reduction
+__device__ __forceinline__ void red_shared_if_lt(uint32_t saddr, int v, uint32_t x, uint32_t n) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %2, %3;\n\t@q red.shared.add.s32 [%0], %1;\n\t}"
+               ::"r"(saddr), "r"(v), "r"(x), "r"(n) : "memory");
 }
 
 // blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row`, tile range c of nrange
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
       const uint32_t it = e[k >> 1] >> (16 * (k & 1));
       int neg;   // 0 or -1 from the item's sign bit
       asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
-      red_shared_if(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k < n);
+      red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k, n);
     }
   };
   for (int64_t a = (int64_t)c * seg; a < q.cnt; a += (int64_t)nrange * seg) {
