@@ -259,15 +259,15 @@ sk_status sk_estimate_many(sk_set* const* sets, int32_t n, sk_estimate* out, voi
  * cross-correlation (Definition 3.1); all give the identical exact result.
  * Default (sk_sketch_create): SK_ESTIMATOR_FUSED.
  *   SK_ESTIMATOR_FFT64: the paper's transform, FP64 FFTs on signed limbs, outputs
- *     rounded to integers.  The limb width comes from a first-order model of the FFT
- *     rounding error, not from a proven bound, so each step is certified a posteriori
- *     instead: largest distance to an integer <= 1/4, the exact row-sum identity
- *     sum z = (sum a)(sum x) mod 2^64 and, for power-of-two m, Z(w) = A(1/w) X(w)
- *     modulo q = 2^64 - 2^32 + 1 at a random primitive m-th root of unity w; a step
- *     that fails is redone with narrower limbs.  This certificate is probabilistic:
- *     a wrong output that keeps its residual and row sums passes the evaluation check
- *     with probability at most (m - 1) / q per row (for other widths only the residual
- *     and row-sum checks apply).  The other two arithmetics need no certificate;
+ *     rounded to integers.  The limb width B is the widest for which an a priori bound
+ *     on the FFT rounding error -- Percival's bound for FFT convolution (Math. Comp. 72,
+ *     2003), extended to the packing of two limbs per transform and the sums over limb
+ *     pairs, with the twiddle table's measured error -- is at most 1/4, so every rounded
+ *     output is exact by that bound; each step is also checked a posteriori (largest
+ *     distance to an integer <= 1/4, the exact row-sum identity sum z = (sum a)(sum x)
+ *     mod 2^64 and, for power-of-two m, Z(w) = A(1/w) X(w) modulo q = 2^64 - 2^32 + 1
+ *     at a random primitive m-th root of unity w) and redone with narrower limbs if a
+ *     check fails.  The other two arithmetics need no certificate;
  *   SK_ESTIMATOR_NTT: number-theoretic transforms over GF(2^64 - 2^32 + 1) on signed
  *     limbs narrow enough that every output lies below q/2 in magnitude, exact by
  *     construction (GB300's integer pipes are much faster than its FP64 pipe);
@@ -295,10 +295,11 @@ sk_status sk_sketch_set_estimator(sk_set* set, int32_t estimator);
  * e.g. code running in a host callback or driver hook that must not enter the CUDA
  * allocator, a process whose device memory is fully held by another pool, or a
  * latency-critical path that forbids allocation.  No counterpart in the paper.
- * It always uses FP64 FFTs (whatever the set's estimator) with the certificate
- * described for SK_ESTIMATOR_FFT64 -- residual, exact per-row sums and the evaluation
- * at a random root of unity, each step redone up to three times with narrower limbs
- * -- so rows, median, fits_i64, median_i64, median_f64 and mid_mean_f64 equal those of
+ * It always uses FP64 FFTs (whatever the set's estimator) with the limb width and
+ * checks described for SK_ESTIMATOR_FFT64 -- the a priori bound, then the residual,
+ * exact per-row sums and the evaluation at a random root of unity, each step redone up
+ * to three times with narrower limbs -- so rows, median, fits_i64, median_i64,
+ * median_f64 and mid_mean_f64 equal those of
  * sk_estimate_join; the diagnostics (max_residual, max_limbs, limb_bits, retries)
  * describe this call's own arithmetic.  Only power-of-two m (2 <= m <= 2^22) is
  * accepted; other widths return SK_ERR_UNSUPPORTED_WIDTH.  The set's device must be

@@ -14,12 +14,14 @@
 // packed per complex transform), forms for every limb-sum s the spectrum
 // sum_{l + l' = s} conj(A_l) X_l', inverts it, rounds every output to the
 // nearest integer and recombines z = sum_s 2^(B s) round(y_s) exactly.  B is
-// picked from a worst-case rounding-error model so the FFT error stays far below
-// 1/2; each step is then certified a posteriori: the largest distance of an
-// output to its nearest integer must be <= 1/4, per row the exact identity
-// sum_j z_j = (sum_j a_j)(sum_j x_j) must hold mod 2^64 and, for power-of-two m,
-// Z(w) = A(1/w) X(w) mod 2^64 - 2^32 + 1 at a random primitive m-th root of unity w.
-// A failed certificate redoes the step with narrower limbs.
+// the widest limb for which Percival's a priori bound on the FFT's rounding error
+// (with the twiddle table's measured error, see fp64_step_bound) stays at or below
+// 1/4, so every rounding is exact by that bound; each step is also checked a
+// posteriori: the largest distance of an output to its nearest integer must be
+// <= 1/4, per row the exact identity sum_j z_j = (sum_j a_j)(sum_j x_j) must hold
+// mod 2^64 and, for power-of-two m, Z(w) = A(1/w) X(w) mod 2^64 - 2^32 + 1 at a
+// random primitive m-th root of unity w.  A failed check redoes the step with
+// narrower limbs.
 //
 // FFTs: radix-2 decimation-in-time in shared memory; widths up to 2^12 in one
 // pass, wider ones (up to 2^22) as a four-step transform m = R x C (column FFTs
@@ -32,6 +34,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <vector>
 
 #include "sk_internal.h"
 
@@ -939,17 +942,79 @@ int ilog2(int64_t v) {
   return r;
 }
 
-// Largest limb width B such that, with every limb at its largest magnitude 2^(B-1),
-// the modelled FFT rounding error 3 eps log2(m) npairs m 2^(2B-2) stays below 1/8
-// and each rounded output npairs m 2^(2B-2) stays below 2^51.
-int limb_bits_for(int64_t m, int npairs) {
-  const double logm = std::log2((double)m);
+// ---------------------------------------------------------------------------
+// A priori error bound of one FP64 correlation step, after Percival (Math. Comp. 72 (2003),
+// Theorem 5.1): a cyclic convolution of length N = 2^n computed with radix-2 FFTs in floating
+// point (unit roundoff eps), with precomputed roots of unity off by at most beta, errs in every
+// output by at most |x|_2 |y|_2 ((1 + eps)^(3n) (1 + eps sqrt5)^(3n+1) (1 + beta)^(3n) - 1).
+// The step here differs from that computation in ways that each add a bounded factor:
+//   - every transform has S = n stages, plus one more above 2^12 (the four-step split multiplies
+//     by the inter-pass twiddle from the same table): S replaces n;
+//   - two real limb vectors share one complex forward transform; the separation after it (one
+//     complex addition, an exact halving) maps the packed spectrum's error onto the two limbs'
+//     spectra without growing its l2 norm, and the packed input has |w|_2^2 = |u|_2^2 + |v|_2^2;
+//   - the npairs limb products of one limb sum are added (npairs - 1 additions) and two limb sums
+//     share one inverse transform (one addition), whose output error is bounded by the packed
+//     input's norm: at most twice a single sum's;
+//   - for widths that are not powers of two the circular output adds two linear outputs.
+// Every addition stage contributes a factor (1 + eps).  A limb vector has at most m non-zero
+// signed B-bit digits, so a packed forward vector has |w|_2 <= sqrt(2 m) 2^(B-1), and
+//   error <= fold * 2 * npairs * 2 m 2^(2B-2) * E,
+//   E = (1 + eps)^(3S + 2 + npairs) (1 + eps sqrt5)^(3S + 1) (1 + beta)^(3S) - 1.
+// The limb width is the largest B with that bound at most 1/4 (rounding to the nearest integer
+// is then exact, with margin) and every output below 2^51 in magnitude.  beta is measured on
+// the twiddle table itself (twiddle_error), so the bound holds for the roots actually used.
+// ---------------------------------------------------------------------------
+double fp64_step_bound(int64_t m, int64_t M, int npairs, int B, double beta) {
+  int n = 0;
+  while (((int64_t)1 << n) < M) n++;
+  const int S = n + (M > 4096 ? 1 : 0);
+  const double eps = std::ldexp(1.0, -53);
+  const double lg = (3.0 * S + 2 + npairs) * std::log1p(eps) + (3.0 * S + 1) * std::log1p(std::sqrt(5.0) * eps) +
+                    3.0 * S * std::log1p(beta);
+  const double E = std::expm1(lg) * (1.0 + 1e-9);   // margin for the rounding of this evaluation
+  const double fold = M != m ? 2.0 : 1.0;
+  return fold * 2.0 * npairs * 2.0 * (double)m * std::ldexp(1.0, 2 * B - 2) * E;
+}
+
+int limb_bits_for(int64_t m, int64_t M, int npairs, double beta) {
+  const double fold = M != m ? 2.0 : 1.0;
   for (int B = 24; B >= 2; B--) {
-    const double mag = (double)npairs * (double)m * std::ldexp(1.0, 2 * B - 2);
-    const double err = 3.0 * std::ldexp(1.0, -53) * logm * mag;
-    if (err <= 0.125 && mag < std::ldexp(1.0, 51)) return B;
+    const double mag = fold * (double)npairs * (double)m * std::ldexp(1.0, 2 * B - 2);
+    if (fp64_step_bound(m, M, npairs, B, beta) <= 0.25 && mag < std::ldexp(1.0, 51)) return B;
   }
   return 2;
+}
+
+// Largest deviation |w' - w| of the length-M twiddle table (M / 2 entries W_M^t =
+// exp(-2 pi i t / M) in device memory) from the exact roots, computed on the host in long
+// double (the reference's own error, far below 1e-17, is covered by the added 1e-17).  The
+// table for a length comes from one deterministic kernel, so the value is cached per length.
+double twiddle_error(int64_t M, const double2* d_tw, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<int64_t, double> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(M);
+    if (it != cache.end()) return it->second;
+  }
+  std::vector<double2> h((size_t)(M / 2));
+  if (M >= 2) {
+    if (cudaMemcpyAsync(h.data(), d_tw, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return 1.0;   // unknown: a bound that admits no limb width, so the step reports inexact
+  }
+  const long double pi = acosl(-1.0L);
+  double worst = 0.0;
+  for (int64_t t = 0; t < M / 2; t++) {
+    const long double a = 2.0L * pi * (long double)t / (long double)M;
+    const long double dc = (long double)h[(size_t)t].x - cosl(a), ds = (long double)h[(size_t)t].y + sinl(a);
+    worst = std::max(worst, (double)sqrtl(dc * dc + ds * ds));
+  }
+  const double beta = worst + 1e-17;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[M] = beta;
+  return beta;
 }
 
 // Grows a scratch buffer with the stream-ordered allocator: the old buffer is only
@@ -1919,6 +1984,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
     SK_CK(cudaGetLastError());
   }
   const double2* tw = (const double2*)s->d_twiddle;
+  const double beta = s->estimator == SK_ESTIMATOR_FFT64 ? twiddle_error(M, tw, st) : 0.0;
   char* base = (char*)s->scratch.ptr;
   I256* d_rows = (I256*)(base + small_off);
   I256* d_sorted = d_rows + SK_MAX_ROWS;
@@ -2005,12 +2071,12 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
           corr++;
           continue;
         }
-        int B = std::min(limb_bits_for(M, 1), bmax[corr]);
+        int B = std::min(limb_bits_for(m, M, 1, beta), bmax[corr]);
         int La = 0, Lx = 0;
         for (;;) {
           La = (bits_a + 2 + B - 1) / B;
           Lx = (bits_x + 2 + B - 1) / B;
-          const int nb = std::min(limb_bits_for(M, std::min(La, Lx)), bmax[corr]);
+          const int nb = std::min(limb_bits_for(m, M, std::min(La, Lx), beta), bmax[corr]);
           if (nb >= B) break;
           B = nb;
         }
@@ -2103,7 +2169,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
     }
     // a step failed its certificate: redo everything with narrower limbs there
     retries++;
-    bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(M, 1)) - 3);
+    bmax[failed] = std::max(2, (step_B[failed] ? step_B[failed] : limb_bits_for(m, M, 1, beta)) - 3);
   }
   return SK_ERR_INEXACT;
 }
@@ -2487,6 +2553,7 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
   k_twiddle<<<grid_for(m / 2), 256, 0, st>>>(tw, m);
   count_launch();
   SK_CK(cudaGetLastError());
+  const double beta = twiddle_error(m, tw, st);
 
   double max_resid = 0.0;
   int max_limbs = 0, last_B = 0, retries = 0;
@@ -2526,14 +2593,14 @@ sk_status run_estimate_noalloc(sk_set* s, sk_estimate* out, cudaStream_t st) {
         continue;
       }
       if (hb[0] + hb[1] + logm + 1 > 255) return SK_ERR_OVERFLOW;
-      int B = limb_bits_for(m, 1);
+      int B = limb_bits_for(m, m, 1, beta);
       bool done = false;
       for (int attempt = 0; attempt < 4 && !done; attempt++) {
         int La = 0, Lx = 0;
         for (;;) {
           La = (hb[0] + 2 + B - 1) / B;
           Lx = (hb[1] + 2 + B - 1) / B;
-          const int nb = limb_bits_for(m, std::min(La, Lx));
+          const int nb = limb_bits_for(m, m, std::min(La, Lx), beta);
           if (nb >= B) break;
           B = nb;
         }
