@@ -1470,15 +1470,47 @@ __global__ void k_fu_final(const uint32_t* part, int d, int nchunk, uint32_t min
 // host: Montgomery form of v (< p)
 uint32_t fu_to_mont(uint64_t v, uint32_t p) { return (uint32_t)(((unsigned __int128)v << 32) % p); }
 
+// Per-width constants of prime i, computed once per width M (modular exponentiations are
+// host work that every estimate would otherwise repeat): w, a root of unity of order exactly
+// M, its inverse, and in Montgomery form w, w^-1, w^(M/4), w^(-M/4), M^-1 and 1.
+struct FuWidth {
+  uint64_t w = 1, winv = 1;
+  uint32_t w_m = 0, winv_m = 0, r4 = 0, r4i = 0, minv = 0, one = 0;
+};
+
+const FuWidth& fu_width(int i, int64_t M) {
+  static std::mutex mu;
+  static std::map<int64_t, std::vector<FuWidth>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(M);
+  if (it == cache.end()) {
+    const std::vector<FuPrime>& pr = fu_primes();
+    std::vector<FuWidth> v(kFuMaxPrimes);
+    for (int k = 0; k < kFuMaxPrimes && k < (int)pr.size(); k++) {
+      const uint64_t p = pr[k].p;
+      FuWidth& f = v[k];
+      f.w = fu_powmod(pr[k].g, (p - 1) / (uint64_t)M, p);
+      f.winv = fu_powmod(f.w, p - 2, p);
+      f.one = fu_to_mont(1, pr[k].p);
+      f.w_m = fu_to_mont(f.w, pr[k].p);
+      f.winv_m = fu_to_mont(f.winv, pr[k].p);
+      f.r4 = M >= 4 ? fu_to_mont(fu_powmod(f.w, (uint64_t)M / 4, p), pr[k].p) : f.one;
+      f.r4i = M >= 4 ? fu_to_mont(fu_powmod(f.winv, (uint64_t)M / 4, p), pr[k].p) : f.one;
+      f.minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), pr[k].p);
+    }
+    it = cache.emplace(M, std::move(v)).first;
+  }
+  return it->second[i];
+}
+
 // One prime's pass (twiddles already in place): load, forward transform, product-sum.
 template <int PI>
 sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, uint32_t* W, uint32_t* part,
                         int nchunk, uint32_t* res, int np, unsigned long long negmask, cudaStream_t st) {
   const int r = s->r, d = s->d;
   uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
-  const uint64_t p = fp.p;
-  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
-  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
+  const FuWidth& fw = fu_width(PI, M);
+  const uint32_t r4 = fw.r4;
   k_fu_load<PI><<<dim3((unsigned)std::max(1, grid_for((int64_t)r * d * M) / r), (unsigned)r), 256, 0, st>>>(
       s->d_fu_rel, r, d, M, fp.r2, fp.r3, V);
   count_launch();
@@ -1486,37 +1518,171 @@ sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, ui
   sk_status fs = xform<MontOps<PI>>(V, W, (int64_t)r * d, M, tw, false, r4, st);
   if (fs != SK_OK) return fs;
   k_fu_reduce<PI><<<d * nchunk, 256, 0, st>>>(W, r, d, M, negmask, nchunk, part);
-  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
-  k_fu_final<PI><<<(d + 63) / 64, 64, 0, st>>>(part, d, nchunk, minv, res, np);
+  k_fu_final<PI><<<(d + 63) / 64, 64, 0, st>>>(part, d, nchunk, fw.minv, res, np);
   count_launch(2);
   return set_status_from_cuda(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Small widths (m <= 4096, every relation's row in one CTA's shared memory): the whole
+// pairwise fused estimate in three launches and one host synchronisation.  k_fu_small_bound
+// turns the norm partials into each row's bound and the number of primes (as fu_row_bits
+// and fu_setup do on the host), k_fu_small gives CTA (row, prime) the row's r counter vectors
+// mod that prime, transforms them in shared memory, forms sum_nu prod_k C_k(s_k nu) and
+// writes the row's residue; CTAs of primes beyond the count return at once.
+// ---------------------------------------------------------------------------
+struct FuSmallArgs {
+  const int64_t* const* rel;     // r relation counter blocks [d][m]
+  const uint32_t* tw;            // twiddle tables [prime][m] (w^t | w^-t, Montgomery form)
+  uint32_t r2[kFuMaxPrimes], r3[kFuMaxPrimes], r4[kFuMaxPrimes], minv[kFuMaxPrimes];
+  double log2p[kFuMaxPrimes];
+  int r, d, logm, nch;
+  unsigned long long negmask;
+  const double* part;            // norm partials [r d][nch][2]
+  int* np;                       // primes used (0: more than kFuMaxPrimes would be needed)
+  uint32_t* res;                 // [d][kFuMaxPrimes]
+};
+
+// One CTA: row bounds (one thread per row, fu_row_bits's arithmetic) and their maximum.
+__global__ void k_fu_small_bound(FuSmallArgs a) {
+  __shared__ double worst;   // largest row bound in bits; rows with a zero relation vector are 0
+  if (threadIdx.x == 0) worst = 0.0;
+  __syncthreads();
+  for (int row = threadIdx.x; row < a.d; row += blockDim.x) {
+    double b = 0.0, best1 = 0.0, best2 = 0.0;
+    bool zero = false;
+    for (int k = 0; k < a.r && !zero; k++) {
+      const int64_t v = (int64_t)k * a.d + row;
+      double v1 = 0.0, sq = 0.0;
+      for (int c = 0; c < a.nch; c++) {
+        v1 += a.part[2 * (v * a.nch + c)];
+        sq += a.part[2 * (v * a.nch + c) + 1];
+      }
+      const double v2 = sqrt(sq);
+      if (v1 <= 0.0) {
+        zero = true;
+        break;
+      }
+      b += log2(v1 * (1.0 + 1e-9));
+      const double save = log2(v1 * (1.0 + 1e-9)) - log2(v2 * (1.0 + 1e-9));
+      if (save > best1) {
+        best2 = best1;
+        best1 = save;
+      } else if (save > best2) {
+        best2 = save;
+      }
+    }
+    if (zero) continue;
+    const double bits = a.r >= 2 ? b - best1 - best2 : b;
+    unsigned long long* w = (unsigned long long*)&worst;   // non-negative doubles order as integers
+    atomicMax(w, (unsigned long long)__double_as_longlong(bits < 0.0 ? 0.0 : bits));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double bits = worst;
+    int np = 0;
+    double cover = 0.0;
+    while (np < kFuMaxPrimes && cover < bits + 3.0) cover += a.log2p[np++];
+    *a.np = cover < bits + 3.0 ? 0 : np;
+  }
+}
+
+template <int PI>
+__device__ __forceinline__ void fu_small_body(const FuSmallArgs& a, int row, uint32_t* V, uint32_t* red) {
+  using O = MontOps<PI>;
+  const int m = 1 << a.logm;
+  const uint32_t p = c_fu_p[PI];
+  for (int idx = threadIdx.x; idx < a.r * m; idx += blockDim.x) {
+    const int k = idx >> a.logm, j = idx & (m - 1);
+    const int64_t c = a.rel[k][(int64_t)row * m + j];
+    const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
+    uint32_t h = (uint32_t)(mag >> 32);
+    if (h >= p) h -= p;
+    const uint32_t v = O::add(O::mul(h, a.r3[PI]), O::mul((uint32_t)mag, a.r2[PI]));
+    V[k * m + bitrev(j, a.logm)] = c < 0 ? O::neg(v) : v;
+  }
+  __syncthreads();
+  smem_xform<O>(V, a.r, a.logm, a.tw + (int64_t)PI * m, 1, false, a.r4[PI]);
+  uint32_t sum = 0;
+  for (int nu = threadIdx.x; nu < m; nu += blockDim.x) {
+    const int neg_nu = (m - nu) & (m - 1);
+    uint32_t prod = V[(a.negmask & 1ull) ? neg_nu : nu];
+    for (int k = 1; k < a.r; k++) prod = O::mul(prod, V[k * m + (((a.negmask >> k) & 1ull) ? neg_nu : nu)]);
+    sum = O::add(sum, prod);
+  }
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] = O::add(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.res[row * kFuMaxPrimes + PI] = O::mul(O::mul(red[0], a.minv[PI]), 1u);
+}
+
+// grid (d, kFuMaxPrimes), 256 threads, r m 4 bytes of dynamic shared memory
+__global__ void __launch_bounds__(256) k_fu_small(FuSmallArgs a) {
+  extern __shared__ __align__(16) unsigned char fs_smem[];
+  __shared__ uint32_t red[256];
+  const int row = blockIdx.x, pi = blockIdx.y;
+  if (pi >= *a.np) return;   // uniform across the CTA
+  uint32_t* V = (uint32_t*)fs_smem;
+  switch (pi) {
+    case 0: fu_small_body<0>(a, row, V, red); break;
+    case 1: fu_small_body<1>(a, row, V, red); break;
+    case 2: fu_small_body<2>(a, row, V, red); break;
+    case 3: fu_small_body<3>(a, row, V, red); break;
+    case 4: fu_small_body<4>(a, row, V, red); break;
+    case 5: fu_small_body<5>(a, row, V, red); break;
+    case 6: fu_small_body<6>(a, row, V, red); break;
+    case 7: fu_small_body<7>(a, row, V, red); break;
+    default: fu_small_body<8>(a, row, V, red); break;
+  }
+}
+
 // Garner's mixed-radix reconstruction of the integer with the given residues, taken in
 // [-P/2, P/2) with P the product of the primes; false when it needs more than 255 bits.
+// Garner's coefficients: c_i = (p_0 p_1 ... p_{i-1})^-1 mod p_i, computed once.
+const std::vector<uint64_t>& fu_garner() {
+  static const std::vector<uint64_t> c = [] {
+    const std::vector<FuPrime>& pr = fu_primes();
+    std::vector<uint64_t> v(pr.size(), 1);
+    for (size_t i = 0; i < pr.size(); i++) {
+      const uint64_t p = pr[i].p;
+      uint64_t q = 1;
+      for (size_t k = 0; k < i; k++) q = q * (pr[k].p % p) % p;   // all below 2^31: products fit 64 bits
+      v[i] = fu_powmod(q, p - 2, p);
+    }
+    return v;
+  }();
+  return c;
+}
+
 bool fu_crt(const uint32_t* res, int np, const std::vector<FuPrime>& pr, I256* out) {
   constexpr int W = 6;   // 384-bit accumulators
-  uint64_t X[W] = {0}, Q[W] = {1, 0, 0, 0, 0, 0};
-  auto mod_small = [](const uint64_t* a, uint64_t p) {
-    unsigned __int128 r = 0;
-    for (int i = W - 1; i >= 0; i--) r = ((r << 64) | a[i]) % p;
-    return (uint64_t)r;
-  };
-  auto mul_add = [](uint64_t* acc, const uint64_t* a, uint64_t t) {   // acc += a * t
+  const std::vector<uint64_t>& cg = fu_garner();
+  // mixed-radix digits: X = t_0 + t_1 p_0 + t_2 p_0 p_1 + ..., 0 <= t_i < p_i, with
+  // t_i = (res_i - (t_0 + t_1 p_0 + ... + t_{i-1} p_0 ... p_{i-2})) c_i mod p_i, the bracket
+  // evaluated mod p_i by Horner (every operand below 2^31)
+  uint64_t t[kFuMaxPrimes];
+  for (int i = 0; i < np; i++) {
+    const uint64_t p = pr[i].p;
+    uint64_t acc = 0;
+    for (int j = i - 1; j >= 0; j--) acc = (acc * (pr[j].p % p) + t[j]) % p;
+    t[i] = ((uint64_t)res[i] % p + p - acc) % p * cg[i] % p;
+  }
+  auto mul_add = [](uint64_t* acc, const uint64_t* a, uint64_t f) {   // acc += a * f
     unsigned __int128 carry = 0;
     for (int i = 0; i < W; i++) {
-      const unsigned __int128 v = (unsigned __int128)a[i] * t + acc[i] + carry;
+      const unsigned __int128 v = (unsigned __int128)a[i] * f + acc[i] + carry;
       acc[i] = (uint64_t)v;
       carry = v >> 64;
     }
   };
+  uint64_t X[W] = {0}, Q[W] = {1, 0, 0, 0, 0, 0};
   for (int i = 0; i < np; i++) {
-    const uint64_t p = pr[i].p;
-    const uint64_t xm = mod_small(X, p), qm = mod_small(Q, p);
-    const uint64_t t = (uint64_t)((unsigned __int128)((res[i] + p - xm) % p) * fu_powmod(qm, p - 2, p) % p);
-    mul_add(X, Q, t);
+    mul_add(X, Q, t[i]);
     uint64_t Qn[W] = {0};
-    mul_add(Qn, Q, p);
+    mul_add(Qn, Q, pr[i].p);
     std::memcpy(Q, Qn, sizeof(Q));
   }
   // negative when 2X >= Q
@@ -1684,12 +1850,10 @@ sk_status fu_finish(sk_set* s, const FuSetup& f, sk_estimate* out, cudaStream_t 
 template <int PI>
 sk_status fu_twiddles(sk_set* s, const FuPrime& fp, int64_t M, cudaStream_t st) {
   if (s->fu_np > PI) return SK_OK;
-  const uint64_t p = fp.p;
-  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);   // order exactly M
-  const uint64_t winv = fu_powmod(w, p - 2, p);
+  const FuWidth& fw = fu_width(PI, M);
+  (void)fp;
   uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
-  k_fu_twiddle<PI><<<grid_for(M / 2), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p), fu_to_mont(winv, fp.p),
-                                                      fu_to_mont(1, fp.p));
+  k_fu_twiddle<PI><<<grid_for(M / 2), 256, 0, st>>>(tw, tw + M / 2, M, fw.w_m, fw.winv_m, fw.one);
   count_launch();
   return set_status_from_cuda(cudaGetLastError());
 }
@@ -1697,11 +1861,103 @@ sk_status fu_twiddles(sk_set* s, const FuPrime& fp, int64_t M, cudaStream_t st) 
 // The fused estimate for queries whose components all join two attributes and a
 // power-of-two width: one product of spectra per prime.  *done false when it does not
 // apply.
+// The small-width form (see k_fu_small): twiddles for every prime once per set, then norms,
+// bound and per-(row, prime) residues in three launches, one read-back.  *done false when
+// the bound needs more than kFuMaxPrimes primes (the caller then takes the general path).
+sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long long negmask, cudaStream_t st,
+                                      bool* done) {
+  *done = false;
+  const int64_t m = s->m;
+  const int r = s->r, d = s->d;
+  const std::vector<FuPrime>& pr = fu_primes();
+  if (!s->d_fu_rel) {
+    SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
+    SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
+  }
+  if (s->fu_m != m || !s->d_fu_tw) {
+    if (s->d_fu_tw) cudaFree(s->d_fu_tw);
+    s->d_fu_tw = nullptr;
+    s->fu_np = 0;
+    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * m * sizeof(uint32_t)));
+    s->fu_m = m;
+  }
+  if (s->fu_np < kFuMaxPrimes) {
+    sk_status ts = SK_OK;
+#define SK_FU_TW(I) if (ts == SK_OK) ts = fu_twiddles<I>(s, pr[I], m, st);
+    SK_FU_TW(0) SK_FU_TW(1) SK_FU_TW(2) SK_FU_TW(3) SK_FU_TW(4) SK_FU_TW(5) SK_FU_TW(6) SK_FU_TW(7) SK_FU_TW(8)
+#undef SK_FU_TW
+    if (ts != SK_OK) return ts;
+    s->fu_np = kFuMaxPrimes;
+  }
+  // scratch: norm partials | residues [d][kFuMaxPrimes] | prime count
+  const int nch = fu_l1_chunks((int64_t)r * d, m);
+  const size_t l1_bytes = ((size_t)r * d * nch * 16 + 255) & ~(size_t)255;
+  const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
+  SK_CK(ensure(s->scratch, l1_bytes + res_bytes + 256, st));
+  FuSmallArgs a;
+  a.rel = s->d_fu_rel;
+  a.tw = s->d_fu_tw;
+  int logm = 0;
+  while (((int64_t)1 << logm) < m) logm++;
+  for (int i = 0; i < kFuMaxPrimes; i++) {
+    const FuWidth& fw = fu_width(i, m);
+    a.r2[i] = pr[i].r2;
+    a.r3[i] = pr[i].r3;
+    a.r4[i] = fw.r4;
+    a.minv[i] = fw.minv;
+    a.log2p[i] = pr[i].log2p;
+  }
+  a.r = r;
+  a.d = d;
+  a.logm = logm;
+  a.nch = nch;
+  a.negmask = negmask;
+  a.part = (double*)s->scratch.ptr;
+  a.res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
+  a.np = (int*)((char*)s->scratch.ptr + l1_bytes + res_bytes);
+  k_fu_norms<<<(unsigned)((int64_t)r * d * nch), 256, 0, st>>>(s->d_fu_rel, d, m, nch, (double*)s->scratch.ptr);
+  k_fu_small_bound<<<1, 256, 0, st>>>(a);
+  const size_t smem = (size_t)r * m * sizeof(uint32_t);
+  if (smem > 48 * 1024) SK_CK(allow_dynamic_smem((const void*)k_fu_small));
+  k_fu_small<<<dim3((unsigned)d, kFuMaxPrimes), 256, smem, st>>>(a);
+  count_launch(3);
+  SK_CK(cudaGetLastError());
+  std::vector<uint32_t> res((size_t)d * kFuMaxPrimes);
+  int np = 0;
+  SK_CK(cudaMemcpyAsync(res.data(), a.res, res.size() * 4, cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaMemcpyAsync(&np, a.np, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK_CK(cudaStreamSynchronize(st));
+  if (np == 0) return SK_OK;   // beyond nine primes
+  I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
+  for (int row = 0; row < d; row++)
+    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, np, pr, &rows[row])) return SK_ERR_OVERFLOW;
+  std::memcpy(sorted, rows, sizeof(I256) * d);
+  std::sort(sorted, sorted + d, [](const I256& x, const I256& y) { return i256_lt(x, y); });
+  fill_estimate(out, rows, sorted, d);
+  out->max_residual = 0.0;
+  out->max_limbs = np;   // CRT primes
+  out->limb_bits = 0;
+  out->corr_steps = s->corr_steps;
+  out->retries = 0;
+  *done = true;
+  return SK_OK;
+}
+
+// SK_FUSED_SMALL=0 keeps small widths on the general fused path.
+bool fused_small_enabled() {
+  const char* v = std::getenv("SK_FUSED_SMALL");
+  return !(v && v[0] == '0');
+}
+
 sk_status run_estimate_pairwise(sk_set* s, sk_estimate* out, cudaStream_t st, bool* done) {
   *done = false;
   const int64_t m = s->m;
   unsigned long long negmask = 0;
   if ((m & (m - 1)) != 0 || m < 2 || m > (1ll << 22) || !fu_eligible(s, &negmask)) return SK_OK;
+  if (m <= 4096 && (int64_t)s->r * m * 4 <= 96 * 1024 && fused_small_enabled()) {
+    SK_CK_ST(run_estimate_pairwise_small(s, out, negmask, st, done));
+    if (*done) return SK_OK;
+  }
   FuSetup f;
   SK_CK_ST(fu_setup(s, m, true, st, &f));
   if (!f.np) return SK_OK;   // beyond nine primes: the GF(q) steps handle it
@@ -1820,13 +2076,8 @@ sk_status crt_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* slot
   using O = MontOps<PI>;
   const int d = s->d;
   const int64_t m = s->m, dM = (int64_t)d * M;
-  const uint64_t p = fp.p;
-  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);
-  const uint64_t winv = fu_powmod(w, p - 2, p);
-  const uint32_t one = fu_to_mont(1, fp.p);
-  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : one;
-  const uint32_t r4i = M >= 4 ? fu_to_mont(fu_powmod(winv, (uint64_t)M / 4, p), fp.p) : one;
-  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
+  const FuWidth& fw = fu_width(PI, M);
+  const uint32_t one = fw.one, r4 = fw.r4, r4i = fw.r4i, minv = fw.minv;
   const uint32_t* tw = s->d_fu_tw + (size_t)PI * M;
   auto slot = [&](int i) { return slots + (size_t)i * dM; };
   const int eg = grid_for(dM);
@@ -2234,20 +2485,16 @@ template <int PI>
 sk_status fu_group_pass(const FuPrime& fp, int64_t M, const int64_t* const* d_rows, int64_t nvec, const FuOut* d_outs,
                         int nout, uint32_t* tw, uint32_t* V, uint32_t* W, uint32_t* part, int nchunk, uint32_t* res,
                         cudaStream_t st) {
-  const uint64_t p = fp.p;
-  const uint64_t w = fu_powmod(fp.g, (p - 1) / (uint64_t)M, p);
-  const uint64_t winv = fu_powmod(w, p - 2, p);
-  k_fu_twiddle<PI><<<grid_for(std::max<int64_t>(1, M / 2)), 256, 0, st>>>(tw, tw + M / 2, M, fu_to_mont(w, fp.p),
-                                                                           fu_to_mont(winv, fp.p), fu_to_mont(1, fp.p));
+  const FuWidth& fw = fu_width(PI, M);
+  k_fu_twiddle<PI><<<grid_for(std::max<int64_t>(1, M / 2)), 256, 0, st>>>(tw, tw + M / 2, M, fw.w_m, fw.winv_m,
+                                                                           fw.one);
   k_fu_load_rows<PI><<<grid_for(nvec * M), 256, 0, st>>>(d_rows, nvec, ilog2(M), fp.r2, fp.r3, V);
   count_launch(2);
   SK_CK(cudaGetLastError());
-  const uint32_t r4 = M >= 4 ? fu_to_mont(fu_powmod(w, (uint64_t)M / 4, p), fp.p) : fu_to_mont(1, fp.p);
-  sk_status fs = xform<MontOps<PI>>(V, W, nvec, M, tw, false, r4, st);
+  sk_status fs = xform<MontOps<PI>>(V, W, nvec, M, tw, false, fw.r4, st);
   if (fs != SK_OK) return fs;
   k_fu_reduce_many<PI><<<nout * nchunk, 256, 0, st>>>(W, d_outs, M, nchunk, part);
-  const uint32_t minv = fu_to_mont(fu_powmod((uint64_t)M % p, p - 2, p), fp.p);
-  k_fu_final<PI><<<(nout + 63) / 64, 64, 0, st>>>(part, nout, nchunk, minv, res, kFuMaxPrimes);
+  k_fu_final<PI><<<(nout + 63) / 64, 64, 0, st>>>(part, nout, nchunk, fw.minv, res, kFuMaxPrimes);
   count_launch(2);
   return set_status_from_cuda(cudaGetLastError());
 }
