@@ -405,20 +405,23 @@ def run_ours(args, world, rank, local):
     fact_s = fact_ms / 1e3
     tables = not args.no_domains
     if tables:
-        # The fact-table update call is three launches, timed together: k_key_table_l20 hashes
-        # the 5 x 1e6 declared domain keys once (9 rows each, 32-byte records), k_tab_items
+        # The fact-table update call is three launches, timed together: k_key_table_l24 hashes
+        # the 5 x 1e6 declared domain keys once (9 rows each, 24-byte records), k_tab_items
         # gathers the five records of each of the 1e8 tuples and writes every row's bin into
         # per-tile item planes (phase 1), k_part_accum adds them into half-row int32 sketches
         # in shared memory and flushes each counter once (phase 2).
         # HBM roofline: algorithmic bytes = the 40 key bytes per tuple.  traffic = DRAM bytes
-        # of one ncu capture of both phases at 2e7 rows (k_tab_items 1.4365 GB read + 0.3483 GB
-        # written, k_part_accum 0.3760 + 0.0040 GB: key stream, record misses and the item
-        # planes' round trip) scaled to this row count, plus the table write (5e6 x 32 B).
-        # L2 roofline beside it: L2 requests per tuple from the same capture (4.91: 3.87 in
-        # phase 1, 1.04 in phase 2; 16.35 with one 64-bit reduction per counter update).
-        traffic = (1.4365 + 0.3483 + 0.3760 + 0.0040) * args.fact_rows / 2e7 + 5 * 1_000_000 * 32 / 1e9
-        kernel = "k_key_table_l20 + k_tab_items<5,L20> + k_part_accum (fact table F, two-phase)"
-        l2_req_per_tuple = 4.91
+        # of one ncu capture of both phases at 2e7 rows (k_tab_items 1.3479 GB read + 0.3459 GB
+        # written, k_part_accum 0.3760 + 0.0030 GB: key stream, record misses and the item
+        # planes' round trip) scaled to this row count, plus the table write (5e6 x 24 B).
+        # L2 roofline beside it: L2 requests per tuple from the same capture (5.53: 4.49 in
+        # phase 1, 1.05 in phase 2; 16.35 with one 64-bit reduction per counter update).
+        # The bound phase 1 actually meets is the L1 data pipe: 5.84 wavefronts per tuple (one
+        # per record gather and lane, plus the key loads and item stores), 94.3 % of its peak
+        # of one wavefront per clock and SM in that capture.
+        traffic = (1.3479 + 0.3459 + 0.3760 + 0.0030) * args.fact_rows / 2e7 + 5 * 1_000_000 * 24 / 1e9
+        kernel = "k_key_table_l24 + k_tab_items<5,24B> + k_part_accum (fact table F, two-phase)"
+        l2_req_per_tuple = 5.53
         l2_peak = 188 * 2.016e9
         l2_rate = l2_req_per_tuple * args.fact_rows / fact_s
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -429,7 +432,10 @@ def run_ours(args, world, rank, local):
         extra = {"roofline_l2": {"bound": "l2_requests", "achieved": l2_rate / 1e9, "peak": l2_peak / 1e9,
                                  "unit": "G requests/s", "frac": l2_rate / l2_peak,
                                  "per_tuple": l2_req_per_tuple, "kernel": kernel,
-                                 "source": "ncu lts__t_requests of k_tab_items + k_part_accum (2e7 rows)"}}
+                                 "source": "ncu lts__t_requests of k_tab_items + k_part_accum (2e7 rows)"},
+                 "roofline_l1_phase1": {"bound": "l1_data_pipe_wavefronts", "per_tuple": 5.84,
+                                        "frac_ncu": 0.943, "kernel": "k_tab_items<5,24B>",
+                                        "source": "ncu l1tex__data_pipe_lsu_wavefronts (2e7 rows)"}}
     else:
         # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
         # GF(2^61-1) Horner multiply-add steps (1 per bin hash, 3 per sign hash), peak = the

@@ -190,7 +190,60 @@ __global__ void __launch_bounds__(256) k_key_table_l20(UpdArgs p, TabArgs t) {
   }
 }
 
-// FMT 0: 20-bit lane records (d <= 9); FMT 1: narrow 16-bit records of 32 bytes (d <= 14):
+// Key-table records of 24 bytes (d <= 9, one thread per domain key): rows 3w .. 3w + 2 in
+// 64-bit word w (w = 0, 1, 2), row r's lane at bit 22 (r mod 3): its bin (below 2^16) in the
+// lane's bits 0..15 and its sign bit at lane bit 19.  Summing A <= 5 records word by word in
+// 64 bits: the bins add up to below 5 2^16 < 2^19 in lane bits 0..18, so they never reach
+// bit 19, and lane bit 19 of the sum is the parity of the signs (their sum, at most 5, fills
+// lane bits 19..21; for the top lane, bits 63 and beyond, the carries leave the word).  So a
+// row's bin sum mod m is (word >> 22 (r mod 3)) & (m - 1) and its sign product the bit above
+// it at 19.  Five tables over 10^6 keys take 120 MB against 160 MB for 32-byte records, which
+// keeps more of the Zipf tail in L2.  Record k (global index, 8-byte aligned) starts at 24 k:
+// for even k its words 0 and 1 form the 16-byte-aligned pair and word 2 follows; for odd k
+// the first 8 bytes hold word 2 and the aligned pair after it words 0 and 1, so a reader
+// always takes words 0 and 1 with one 16-byte load and word 2 with one 8-byte load.
+template <bool DEG1>
+__global__ void __launch_bounds__(256) k_key_table_l24(UpdArgs p, TabArgs t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* s_coef = (uint64_t*)smem_raw;
+  const int ncoef = p.d * p.row_len;
+  for (int i = threadIdx.x; i < ncoef; i += blockDim.x) s_coef[i] = p.coef[i];
+  __syncthreads();
+  const int64_t total = t.base[p.a];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  uint64_t* tbl = (uint64_t*)t.tbl;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    int u = 0;
+    while (u + 1 < p.a && g >= t.base[u + 1]) u++;
+    const uint32_t x = (uint32_t)(g - t.base[u]);
+    const uint64_t* cr = s_coef + t.off[u];
+    uint64_t lane[3] = {0, 0, 0};
+#pragma unroll
+    for (int r = 0; r < 9; r++) {
+      if (r >= p.d) break;
+      uint32_t par;
+      const uint32_t b = key_row_hash<true, DEG1>(p, cr + (int64_t)r * p.row_len, p.deg[u], x, &par);
+      lane[r / 3] |= ((uint64_t)b | ((uint64_t)par << 19)) << (22 * (r % 3));
+    }
+    const bool odd = (g & 1) != 0;
+    uint64_t* out = tbl + 3 * g;
+    out[odd ? 1 : 0] = lane[0];
+    out[odd ? 2 : 1] = lane[1];
+    out[odd ? 0 : 2] = lane[2];
+  }
+}
+
+// Words 0, 1 and 2 of 24-byte record k (layout above): one 16-byte and one 8-byte load.
+__device__ __forceinline__ void ld_record24(const uint64_t* tbl, uint64_t k, uint64_t& w0, uint64_t& w1,
+                                            uint64_t& w2) {
+  const uint64_t odd = k & 1u;
+  const uint64_t* r = tbl + 3 * k;
+  asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(r + odd));
+  asm("ld.global.nc.u64 %0, [%1];" : "=l"(w2) : "l"(r + 2 - 2 * odd));
+}
+
+// FMT 0: 20-bit lane records (d <= 9); FMT 2: 24-byte records (d <= 9, k_key_table_l24);
+// FMT 1: narrow 16-bit records of 32 bytes (d <= 14):
 // per record word holding the bins of rows 2j and 2j + 1, lo[j] adds the low halves (below
 // 5 * 2^16: no overflow) and all[j] the whole words mod 2^32, so row 2j's sum is lo[j] mod
 // 2^16 and row 2j + 1's is ((all[j] - lo[j]) >> 16) mod 2^16 (m divides 2^16).
@@ -199,7 +252,7 @@ __global__ void __launch_bounds__(256) k_key_table_l20(UpdArgs p, TabArgs t) {
 // overlaps the gathers.  Lanes of a warp take consecutive tuples (one tile) and iterate
 // together (the ballots need the whole warp).
 template <int A, int FMT>
-__global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
+__global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t gend = (q.cnt + 31) & ~(int64_t)31;
   const uint32_t mask = (uint32_t)p.m - 1u;
@@ -223,9 +276,9 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
   for (; g < gend; g += step) {
     const bool in = g < q.cnt;
     const bool ok = in && okm == (1u << A) - 1u;
-    const uint4* rec[A];
+    uint64_t kg[A];   // global record indices
 #pragma unroll
-    for (int u = 0; u < A; u++) rec[u] = tbl + ((uint64_t)t.base[u] + kx[u]) * 2;
+    for (int u = 0; u < A; u++) kg[u] = (uint64_t)t.base[u] + kx[u];
     if (in && !ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);   // left out of the tile below
     const int64_t gn = g + step;
     okm = 0;
@@ -240,16 +293,17 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
     const uint32_t nv = __popc(vb), rv = __popc(vb & lt);   // valid tuples in the tile / before this lane
     uint16_t* ip = q.items + ((g >> 5) * d << 5);   // this tile's row 0
     uint16_t* cp = q.cnts + (g >> 5) * d;
-    // one row: compact the tile's valid tuples by part (part 0 first) and store the counts;
-    // with r1 the part-1 tuples before this lane, a part-1 tuple goes to c0 + r1 and a part-0
-    // one to rv - r1
+    // one row: compact the tile's valid tuples by part (part 0 first); with r1 the part-1
+    // tuples before this lane, a part-1 tuple goes to c0 + r1 and a part-0 one to rv - r1.
+    // Lane j keeps row j's count word; the tile's d count words go out in one store below.
+    uint32_t cword = 0;
     auto put = [&](int j, uint32_t bin, uint32_t neg) {
       const bool hi = (bin >> q.logL) != 0;
       const uint32_t hb = __ballot_sync(0xffffffffu, ok && hi);
       const uint32_t n1 = __popc(hb), c0 = nv - n1, r1 = __popc(hb & lt);
       const uint32_t pos = hi ? c0 + r1 : rv - r1;
       if (ok) st_u16_hint(ip + 32 * j + pos, (uint16_t)((bin & low) | (neg << 15)), pol);
-      if (lane == 0) st_u16_hint(cp + j, (uint16_t)(c0 | (n1 << 8)), pol);
+      if (lane == (unsigned)j) cword = c0 | (n1 << 8);
     };
     uint32_t sg = 0;
     if (FMT == 0) {
@@ -258,7 +312,7 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
 #pragma unroll
         for (int u = 0; u < A; u++) {
           uint32_t w[8];
-          ld_record32(rec[u], w);
+          ld_record32(tbl + kg[u] * 2, w);
           acc0 += ((uint64_t)w[1] << 32) | w[0];
           acc1 += ((uint64_t)w[3] << 32) | w[2];
           acc2 += ((uint64_t)w[5] << 32) | w[4];
@@ -271,6 +325,25 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
         const uint64_t acc = j < 3 ? acc0 : (j < 6 ? acc1 : acc2);
         put(j, (uint32_t)(acc >> (20 * (j % 3))) & mask, (sg >> j) & 1u);
       }
+    } else if (FMT == 2) {
+      uint64_t acc0 = 0, acc1 = 0, acc2 = 0;
+      if (ok) {
+#pragma unroll
+        for (int u = 0; u < A; u++) {
+          uint64_t w0, w1, w2;
+          ld_record24((const uint64_t*)t.tbl, kg[u], w0, w1, w2);
+          acc0 += w0;
+          acc1 += w1;
+          acc2 += w2;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 9; j++) {
+        if (j >= d) break;
+        const uint64_t acc = j < 3 ? acc0 : (j < 6 ? acc1 : acc2);
+        const int sh = 22 * (j % 3);
+        put(j, (uint32_t)(acc >> sh) & mask, (uint32_t)(acc >> (sh + 19)) & 1u);
+      }
     } else {
       uint32_t lo[7], all[7];
 #pragma unroll
@@ -279,7 +352,7 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
 #pragma unroll
         for (int u = 0; u < A; u++) {
           uint32_t w[8];
-          ld_record32(rec[u], w);
+          ld_record32(tbl + kg[u] * 2, w);
           sg ^= w[7];
 #pragma unroll
           for (int j = 0; j < 7; j++) {
@@ -295,6 +368,7 @@ __global__ void __launch_bounds__(256, FMT == 0 ? 5 : 4) k_tab_items(UpdArgs p, 
         put(j, sum & mask, (sg >> j) & 1u);
       }
     }
+    if (lane < (unsigned)d) st_u16_hint(cp + lane, (uint16_t)cword, pol);
   }
 }
 
@@ -396,6 +470,12 @@ int part_update_mode() {
   return (v && v[0] == '0') ? 0 : 1;
 }
 
+// SK_PART_RECORD=32 takes the 32-byte 20-bit lane records instead of the 24-byte ones for d <= 9.
+int part_record_bytes() {
+  const char* v = std::getenv("SK_PART_RECORD");
+  return (v && std::atoi(v) == 32) ? 32 : 24;
+}
+
 int64_t part_window(int64_t n) {
   const char* v = std::getenv("SK_PART_WINDOW");
   const long long x = v ? std::atoll(v) : 0;
@@ -429,7 +509,9 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
   for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
     q.cnt = std::min(W, n - i0);
     for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
-    e = fmt == 0 ? dispatch_tab_items<0>(a, t, q, sms, st) : dispatch_tab_items<1>(a, t, q, sms, st);
+    e = fmt == 0   ? dispatch_tab_items<0>(a, t, q, sms, st)
+        : fmt == 2 ? dispatch_tab_items<2>(a, t, q, sms, st)
+                   : dispatch_tab_items<1>(a, t, q, sms, st);
     if (e != cudaSuccess) break;
     // ranges per (row, part): the grid a whole number of waves when that takes 2..64 waves
     int64_t nr = 0;
@@ -837,11 +919,11 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
     t.rvec = key_record_vectors(s->d, t.narrow);
     // The two-phase partitioned update (unit weights, power-of-two 1024 <= m <= 2^16, d <= 14,
     // at most 5 attributes, sketch too large for one CTA's shared memory, at least 16 tuples
-    // per counter of a row) takes 32-byte records: the 20-bit lane format for d <= 9, the
-    // narrow format otherwise.
+    // per counter of a row) takes 24-byte records for d <= 9 (the 32-byte 20-bit lane ones
+    // with SK_PART_RECORD=32) and the narrow 32-byte format otherwise.
     bool part = part_update_mode() != 0 && pow2 && weights == nullptr && rp.a <= 5 && !use_smem && s->m >= 1024 &&
                 s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16;
-    const int part_fmt = s->d <= 9 ? 0 : 1;
+    const int part_fmt = s->d <= 9 ? (part_record_bytes() == 32 ? 0 : 2) : 1;
     // Automatic choice: the tables replace per-tuple hashing by gathers, which pays when
     // the domains are small against the batch and the counter updates hit L2 (for a sketch
     // much larger than L2 the update is bound by its atomics either way and the gathers
@@ -858,7 +940,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
       }
     }
     if (part) t.rvec = 2;
-    const size_t bytes = (size_t)total * (size_t)t.rvec * 16;
+    const size_t bytes = (size_t)total * (part && part_fmt == 2 ? 24 : (size_t)t.rvec * 16);
     if (fits && worth && total > 0 && bytes <= key_table_max_bytes()) {
       void* buf = nullptr;
       e = pool_malloc_async(&buf, bytes, st);
@@ -869,7 +951,8 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
         t.tbl = (uint32_t*)buf;
         a.smem_wmax = 0;
         const bool d1 = all_deg1(a);
-        auto kb = (part && part_fmt == 0) ? (d1 ? k_key_table_l20<true> : k_key_table_l20<false>)
+        auto kb = (part && part_fmt == 2)   ? (d1 ? k_key_table_l24<true> : k_key_table_l24<false>)
+                  : (part && part_fmt == 0) ? (d1 ? k_key_table_l20<true> : k_key_table_l20<false>)
                   : pow2 ? (d1 ? k_key_table<true, true> : k_key_table<true, false>)
                          : (d1 ? k_key_table<false, true> : k_key_table<false, false>);
         e = cudaSuccess;

@@ -172,18 +172,20 @@ def test_key_table_from_page_locked_host_columns(monkeypatch):
         assert np.array_equal(got, ref), host
 
 
+@pytest.mark.parametrize("record", ["24", "32"])
 @pytest.mark.parametrize("a,d,m,n,window", [(5, 9, 1 << 16, 1_200_007, 0), (5, 9, 1 << 16, 1_200_007, 262_144),
                                              (3, 14, 1 << 15, 600_001, 0), (2, 5, 1 << 14, 300_007, 65_536),
                                              (1, 13, 1 << 12, 100_003, 0), (4, 2, 1 << 16, 1_048_576, 262_144),
                                              (2, 7, 1 << 13, 200_003, 0), (3, 6, 1 << 15, 524_288, 0)])
-def test_partitioned_update_bit_exact(a, d, m, n, window, monkeypatch):
+def test_partitioned_update_bit_exact(a, d, m, n, window, record, monkeypatch):
     """Unit-weight batches with declared domains, power-of-two m <= 2^16 and sketches too
     large for one CTA's shared memory take the two-phase update (per-row bin planes, then
-    shared-memory accumulation per (row, part)); one window or several with a ragged last
-    one; keys at the table's first and last records and outside the domain (skipped and
-    reported).  The launch count shows which path ran: the table build plus two launches
-    per window."""
+    shared-memory accumulation per (row, part)), with 24- and 32-byte key-table records for
+    d <= 9; one window or several with a ragged last one; keys at the table's first and last
+    records and outside the domain (skipped and reported).  The launch count shows which path
+    ran: the table build plus two launches per window."""
     monkeypatch.setenv("SK_KEY_TABLE", "1")
+    monkeypatch.setenv("SK_PART_RECORD", record)
     if window:
         monkeypatch.setenv("SK_PART_WINDOW", str(window))
     rng = np.random.default_rng(a * 7919 + d)
@@ -233,3 +235,30 @@ def test_partitioned_update_edges(monkeypatch):
         co = O.draw_coefficients(4321 + d, d, q.n_comp, len(q.edges))
         ref = O.sketch_relation(q, co, 0, cols[:, keep], None, m, threads=16)
         assert np.array_equal(got, ref), (a, d, m)
+
+
+@pytest.mark.parametrize("m,d", [(1 << 12, 13), (1 << 16, 3)])
+def test_partitioned_update_heavy_bins(m, d, monkeypatch):
+    """Two heavy bins per row: 3e6 tuples of which 45 % carry one key pair and 45 % another,
+    so that every CTA's range adds about 9000 same-sign items to one shared counter of every
+    row while the rest spread over the row.  Bit-exact against the oracle (counters past 10^6
+    in magnitude), at one part per row (m = 2^12, d = 13: too large for one CTA's shared
+    memory) and two (m = 2^16)."""
+    monkeypatch.setenv("SK_KEY_TABLE", "1")
+    n, a = 3_000_000, 2
+    doms = [5000, 7000]
+    cols = np.stack([synth.zipf_keys(n, 1.1, doms[u], 700 + u).numpy() for u in range(a)])
+    rng = np.random.default_rng(5)
+    pick = rng.random(n)
+    cols[0, pick < 0.45], cols[1, pick < 0.45] = 0, 0
+    heavy2 = (pick >= 0.45) & (pick < 0.9)
+    cols[0, heavy2], cols[1, heavy2] = 17, 4242
+    attrs, edges = _star(a)
+    L0 = pkg.sk_launch_count()
+    got = _run(attrs, edges, m, d, 99, cols, None, doms)
+    assert pkg.sk_launch_count() - L0 == 3   # table build, phase 1, phase 2
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(99, d, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols, None, m, threads=16)
+    assert np.abs(ref).max() > 1_000_000
+    assert np.array_equal(got, ref)
