@@ -145,9 +145,16 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
  * so when the domains are small against the batch (sum of bounds * 4 <=
  * n_rows * |Omega|) and the relation's d * m * 8-byte sketch is at most 32 MiB
  * (environment: SK_KEY_TABLE=0 never, =1 whenever the bounds allow).  The table
- * (sum of bounds * 16 or 32 bytes when m <= 2^16 and d <= 14) comes from the device's
- * stream-ordered pool and is released on cuda_stream at the end of the call; if
- * it cannot be allocated the call hashes per tuple.  Results are identical.
+ * (sum of bounds * 16 or 32 bytes when m <= 2^16 and d <= 14; 24 bytes for the
+ * two-phase update below when d <= 9) comes from the device's stream-ordered pool
+ * and is released on cuda_stream at the end of the call; if it cannot be
+ * allocated the call hashes per tuple.  Unit-weight batches (dev_weights NULL)
+ * into a power-of-two 1024 <= m <= 2^16 with d <= 14, at most 5 attributes, at
+ * least 16 m rows and a d * m int32 sketch too large for one CTA's shared memory
+ * update in two phases through the table: per-tuple bins written as 16-bit items
+ * (2 d bytes per row of staging from the same pool), then added per half row in
+ * shared memory (SK_PART_UPDATE=0 keeps the one-phase table update).  Results
+ * are identical on every path.
  * Asynchronous on cuda_stream; the columns and weights must stay valid until it
  * completes.  n_rows == 0 is a no-op.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
