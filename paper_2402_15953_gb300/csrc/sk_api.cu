@@ -32,6 +32,14 @@ cudaError_t allow_dynamic_smem(const void* func) {
   return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+cudaError_t fit_dynamic_smem(const void* func, size_t dynamic_bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  if (fa.sharedSizeBytes + dynamic_bytes <= (size_t)48 * 1024) return cudaSuccess;   // the default limit
+  return allow_dynamic_smem(func);
+}
+
 // Stream-ordered device memory pool of this library (one per device, created on first use)
 // for update scratch: key tables and the partitioned update's planes.  Up to
 // SK_POOL_KEEP_MB (default 4096) MiB stay reserved between calls, so a batch's scratch of a

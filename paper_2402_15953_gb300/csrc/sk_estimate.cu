@@ -1918,7 +1918,7 @@ sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long
   k_fu_norms<<<(unsigned)((int64_t)r * d * nch), 256, 0, st>>>(s->d_fu_rel, d, m, nch, (double*)s->scratch.ptr);
   k_fu_small_bound<<<1, 256, 0, st>>>(a);
   const size_t smem = (size_t)r * m * sizeof(uint32_t);
-  if (smem > 48 * 1024) SK_CK(allow_dynamic_smem((const void*)k_fu_small));
+  SK_CK(fit_dynamic_smem((const void*)k_fu_small, smem));
   k_fu_small<<<dim3((unsigned)d, kFuMaxPrimes), 256, smem, st>>>(a);
   count_launch(3);
   SK_CK(cudaGetLastError());

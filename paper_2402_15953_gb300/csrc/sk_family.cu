@@ -134,10 +134,8 @@ __global__ void __launch_bounds__(256) k_update_views(UpdArgs p, ViewArgs v) {
 template <int A, bool POW2>
 cudaError_t launch_views(const UpdArgs& a, const ViewArgs& v, size_t smem, cudaStream_t st) {
   auto kern = k_update_views<A, POW2>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = allow_dynamic_smem((const void*)kern);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = fit_dynamic_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>((a.n + 255) / 256, 0x7fffffff);
   kern<<<(int)grid, 256, smem, st>>>(a, v);
   count_launch();

@@ -124,6 +124,9 @@ void count_launch(int n = 1);   // adds to the process-wide kernel-launch counte
 // concurrent caller (estimate worker threads) lower it between another thread's set and
 // launch, failing that launch.  Launches still request only what they use.
 cudaError_t allow_dynamic_smem(const void* func);
+// Raises func's dynamic shared-memory limit when its static shared memory plus
+// dynamic_bytes exceed the default 48 KB.
+cudaError_t fit_dynamic_smem(const void* func, size_t dynamic_bytes);
 sk_status query_info(const sk_query* q, QueryInfo* out);   // validation + canonical numbering
 // Stream-ordered allocation from the library's device pool (update scratch); release with
 // cudaFreeAsync on a stream ordered after the last use.

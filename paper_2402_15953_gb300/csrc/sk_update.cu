@@ -539,10 +539,8 @@ cudaError_t launch_tab(const UpdArgs& a, const TabArgs& t, int grid, size_t smem
   const bool v8 = t.rvec == 2 && tab_v8_enabled();
   auto kern = t.narrow ? (v8 ? k_update_tab<A, POW2, SMEM, true, true> : k_update_tab<A, POW2, SMEM, true, false>)
                        : (v8 ? k_update_tab<A, POW2, SMEM, false, true> : k_update_tab<A, POW2, SMEM, false, false>);
-  if (smem > 48 * 1024) {
-    cudaError_t e = allow_dynamic_smem((const void*)kern);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = fit_dynamic_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<grid, 256, smem, st>>>(a, t);
   count_launch();
   return cudaGetLastError();
@@ -956,7 +954,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
                   : pow2 ? (d1 ? k_key_table<true, true> : k_key_table<true, false>)
                          : (d1 ? k_key_table<false, true> : k_key_table<false, false>);
         e = cudaSuccess;
-        if (coef_bytes > 48 * 1024) e = allow_dynamic_smem((const void*)kb);
+        e = fit_dynamic_smem((const void*)kb, coef_bytes);
         if (e == cudaSuccess) {
           const int bgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 32);
           kb<<<bgrid, 256, coef_bytes, st>>>(a, t);

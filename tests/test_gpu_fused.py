@@ -240,3 +240,21 @@ def test_bound_is_tight_for_identical_relations(m):
         assert one["limb_bits"] == 0 and one["max_limbs"] >= 4
         assert one["rows"] == want and e["rows"] == want
         s.close()
+
+
+@pytest.mark.parametrize("r,m", [(3, 4096), (6, 4096), (2, 2048), (5, 1024), (7, 4096)])
+def test_small_width_single_launch_smem_edges(r, m):
+    """The single-launch form for widths up to 4096 keeps a set's r sketches of one row in
+    shared memory (r m 4 bytes, at most 96 KB): exactly 48 KB of dynamic shared memory beside
+    the kernel's static reduction array (r = 3, m = 4096), the largest (r = 6), smaller ones,
+    and r = 7 at m = 4096 (112 KB: the general fused path).  Star queries with r - 1 joins,
+    rows equal to the oracle's."""
+    rng = random.Random(17 * r + m)
+    attrs = [r - 1] + [1] * (r - 1)
+    edges = [(0, k, k + 1, 0) for k in range(r - 1)]
+    rels = random_relations(rng, attrs, 3000, 1 << 12)
+    d = 7
+    seed = rng.randrange(1 << 60)
+    e = _estimate(attrs, edges, m, d, seed, rels, "fused")
+    assert e["limb_bits"] == 0 and 1 <= e["max_limbs"] <= 9
+    assert e["rows"] == _oracle_rows(attrs, edges, m, d, seed, rels)
