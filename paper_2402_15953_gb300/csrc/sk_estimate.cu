@@ -1525,66 +1525,86 @@ sk_status fu_prime_pass(sk_set* s, const FuPrime& fp, int64_t M, uint32_t* V, ui
 
 // ---------------------------------------------------------------------------
 // Small widths (m <= 4096, every relation's row in one CTA's shared memory): the whole
-// pairwise fused estimate in three launches and one host synchronisation.  k_fu_small_bound
-// turns the norm partials into each row's bound and the number of primes (as fu_row_bits
-// and fu_setup do on the host), k_fu_small gives CTA (row, prime) the row's r counter vectors
-// mod that prime, transforms them in shared memory, forms sum_nu prod_k C_k(s_k nu) and
-// writes the row's residue; CTAs of primes beyond the count return at once.
+// pairwise fused estimate in one launch and one host synchronisation.  CTA (row, prime)
+// first bounds its row as fu_row_bits does (l1 and l2 norms of the row's r counter vectors,
+// |X_row| <= prod_k ||c_k||_1 with the two largest l1/l2 savings of the pairwise form) and
+// takes the row's own number of primes, the fewest whose product exceeds 8 times the bound
+// (one for a row with an all-zero vector, whose estimate is 0; none when nine do not
+// reach it); a CTA whose prime is beyond that count returns.  The others reduce the
+// vectors mod the prime, transform them in shared memory, form sum_nu prod_k C_k(s_k nu)
+// and write the row's residue.  Every CTA of a row computes the same count (same data,
+// same reduction order).
 // ---------------------------------------------------------------------------
 struct FuSmallArgs {
   const int64_t* const* rel;     // r relation counter blocks [d][m]
   const uint32_t* tw;            // twiddle tables [prime][m] (w^t | w^-t, Montgomery form)
   uint32_t r2[kFuMaxPrimes], r3[kFuMaxPrimes], r4[kFuMaxPrimes], minv[kFuMaxPrimes];
   double log2p[kFuMaxPrimes];
-  int r, d, logm, nch;
+  int r, d, logm;
   unsigned long long negmask;
-  const double* part;            // norm partials [r d][nch][2]
-  int* np;                       // primes used (0: more than kFuMaxPrimes would be needed)
-  uint32_t* res;                 // [d][kFuMaxPrimes]
+  uint32_t* res;                 // [d][kFuMaxPrimes] residues, then [d] prime counts (int)
 };
 
-// One CTA: row bounds (one thread per row, fu_row_bits's arithmetic) and their maximum.
-__global__ void k_fu_small_bound(FuSmallArgs a) {
-  __shared__ double worst;   // largest row bound in bits; rows with a zero relation vector are 0
-  if (threadIdx.x == 0) worst = 0.0;
-  __syncthreads();
-  for (int row = threadIdx.x; row < a.d; row += blockDim.x) {
-    double b = 0.0, best1 = 0.0, best2 = 0.0;
-    bool zero = false;
-    for (int k = 0; k < a.r && !zero; k++) {
-      const int64_t v = (int64_t)k * a.d + row;
+// The number of primes row `row` needs (all threads of the CTA get it; 256 threads).
+__device__ int fu_small_row_primes(const FuSmallArgs& a, int row, double (*wsum)[8], int* s_np) {
+  const int m = 1 << a.logm;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double b = 0.0, best1 = 0.0, best2 = 0.0;   // thread 0's running bound (fu_row_bits)
+  bool zero = false;
+  for (int k = 0; k < a.r; k++) {
+    const int64_t* src = a.rel[k] + (int64_t)row * m;
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      const int64_t c = src[j];
+      const double x = (double)(c < 0 ? 0ull - (uint64_t)c : (uint64_t)c);
+      s1 += x;
+      s2 += x * x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      wsum[0][warp] = s1;
+      wsum[1][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
       double v1 = 0.0, sq = 0.0;
-      for (int c = 0; c < a.nch; c++) {
-        v1 += a.part[2 * (v * a.nch + c)];
-        sq += a.part[2 * (v * a.nch + c) + 1];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        v1 += wsum[0][w];
+        sq += wsum[1][w];
       }
-      const double v2 = sqrt(sq);
       if (v1 <= 0.0) {
         zero = true;
-        break;
-      }
-      b += log2(v1 * (1.0 + 1e-9));
-      const double save = log2(v1 * (1.0 + 1e-9)) - log2(v2 * (1.0 + 1e-9));
-      if (save > best1) {
-        best2 = best1;
-        best1 = save;
-      } else if (save > best2) {
-        best2 = save;
+      } else if (!zero) {
+        const double v2 = sqrt(sq);
+        b += log2(v1 * (1.0 + 1e-9));
+        const double save = log2(v1 * (1.0 + 1e-9)) - log2(v2 * (1.0 + 1e-9));
+        if (save > best1) {
+          best2 = best1;
+          best1 = save;
+        } else if (save > best2) {
+          best2 = save;
+        }
       }
     }
-    if (zero) continue;
-    const double bits = a.r >= 2 ? b - best1 - best2 : b;
-    unsigned long long* w = (unsigned long long*)&worst;   // non-negative doubles order as integers
-    atomicMax(w, (unsigned long long)__double_as_longlong(bits < 0.0 ? 0.0 : bits));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int np = 1;
+    if (!zero) {
+      const double bits = a.r >= 2 ? b - best1 - best2 : b;
+      double cover = 0.0;
+      np = 0;
+      while (np < kFuMaxPrimes && cover < bits + 3.0) cover += a.log2p[np++];
+      if (cover < bits + 3.0) np = 0;
+    }
+    *s_np = np;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double bits = worst;
-    int np = 0;
-    double cover = 0.0;
-    while (np < kFuMaxPrimes && cover < bits + 3.0) cover += a.log2p[np++];
-    *a.np = cover < bits + 3.0 ? 0 : np;
-  }
+  return *s_np;
 }
 
 template <int PI>
@@ -1623,8 +1643,12 @@ __device__ __forceinline__ void fu_small_body(const FuSmallArgs& a, int row, uin
 __global__ void __launch_bounds__(256) k_fu_small(FuSmallArgs a) {
   extern __shared__ __align__(16) unsigned char fs_smem[];
   __shared__ uint32_t red[256];
+  __shared__ double wsum[2][8];
+  __shared__ int s_np;
   const int row = blockIdx.x, pi = blockIdx.y;
-  if (pi >= *a.np) return;   // uniform across the CTA
+  const int np = fu_small_row_primes(a, row, wsum, &s_np);
+  if (pi == 0 && threadIdx.x == 0) ((int*)(a.res + (int64_t)a.d * kFuMaxPrimes))[row] = np;
+  if (pi >= np) return;   // uniform across the CTA
   uint32_t* V = (uint32_t*)fs_smem;
   switch (pi) {
     case 0: fu_small_body<0>(a, row, V, red); break;
@@ -1861,9 +1885,9 @@ sk_status fu_twiddles(sk_set* s, const FuPrime& fp, int64_t M, cudaStream_t st) 
 // The fused estimate for queries whose components all join two attributes and a
 // power-of-two width: one product of spectra per prime.  *done false when it does not
 // apply.
-// The small-width form (see k_fu_small): twiddles for every prime once per set, then norms,
-// bound and per-(row, prime) residues in three launches, one read-back.  *done false when
-// the bound needs more than kFuMaxPrimes primes (the caller then takes the general path).
+// The small-width form (see k_fu_small): twiddles for every prime once per set, then each
+// row's bound and residues in one launch, one read-back.  *done false when a row's bound
+// needs more than kFuMaxPrimes primes (the caller then takes the general path).
 sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long long negmask, cudaStream_t st,
                                       bool* done) {
   *done = false;
@@ -1889,11 +1913,9 @@ sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long
     if (ts != SK_OK) return ts;
     s->fu_np = kFuMaxPrimes;
   }
-  // scratch: norm partials | residues [d][kFuMaxPrimes] | prime count
-  const int nch = fu_l1_chunks((int64_t)r * d, m);
-  const size_t l1_bytes = ((size_t)r * d * nch * 16 + 255) & ~(size_t)255;
-  const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
-  SK_CK(ensure(s->scratch, l1_bytes + res_bytes + 256, st));
+  // scratch: residues [d][kFuMaxPrimes], then each row's prime count
+  const size_t out_words = (size_t)d * kFuMaxPrimes + d;
+  SK_CK(ensure(s->scratch, out_words * 4, st));
   FuSmallArgs a;
   a.rel = s->d_fu_rel;
   a.tw = s->d_fu_tw;
@@ -1910,32 +1932,30 @@ sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long
   a.r = r;
   a.d = d;
   a.logm = logm;
-  a.nch = nch;
   a.negmask = negmask;
-  a.part = (double*)s->scratch.ptr;
-  a.res = (uint32_t*)((char*)s->scratch.ptr + l1_bytes);
-  a.np = (int*)((char*)s->scratch.ptr + l1_bytes + res_bytes);
-  k_fu_norms<<<(unsigned)((int64_t)r * d * nch), 256, 0, st>>>(s->d_fu_rel, d, m, nch, (double*)s->scratch.ptr);
-  k_fu_small_bound<<<1, 256, 0, st>>>(a);
+  a.res = (uint32_t*)s->scratch.ptr;
   const size_t smem = (size_t)r * m * sizeof(uint32_t);
   SK_CK(fit_dynamic_smem((const void*)k_fu_small, smem));
   k_fu_small<<<dim3((unsigned)d, kFuMaxPrimes), 256, smem, st>>>(a);
-  count_launch(3);
+  count_launch();
   SK_CK(cudaGetLastError());
-  std::vector<uint32_t> res((size_t)d * kFuMaxPrimes);
-  int np = 0;
-  SK_CK(cudaMemcpyAsync(res.data(), a.res, res.size() * 4, cudaMemcpyDeviceToHost, st));
-  SK_CK(cudaMemcpyAsync(&np, a.np, sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<uint32_t> res(out_words);
+  SK_CK(cudaMemcpyAsync(res.data(), a.res, out_words * 4, cudaMemcpyDeviceToHost, st));
   SK_CK(cudaStreamSynchronize(st));
-  if (np == 0) return SK_OK;   // beyond nine primes
+  const int* np = (const int*)(res.data() + (size_t)d * kFuMaxPrimes);
+  int npmax = 0;
+  for (int row = 0; row < d; row++) {
+    if (np[row] == 0) return SK_OK;   // a row beyond nine primes: the general path
+    npmax = std::max(npmax, np[row]);
+  }
   I256 rows[SK_MAX_ROWS], sorted[SK_MAX_ROWS];
   for (int row = 0; row < d; row++)
-    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, np, pr, &rows[row])) return SK_ERR_OVERFLOW;
+    if (!fu_crt(res.data() + (size_t)row * kFuMaxPrimes, np[row], pr, &rows[row])) return SK_ERR_OVERFLOW;
   std::memcpy(sorted, rows, sizeof(I256) * d);
   std::sort(sorted, sorted + d, [](const I256& x, const I256& y) { return i256_lt(x, y); });
   fill_estimate(out, rows, sorted, d);
   out->max_residual = 0.0;
-  out->max_limbs = np;   // CRT primes
+  out->max_limbs = npmax;   // CRT primes of the widest row
   out->limb_bits = 0;
   out->corr_steps = s->corr_steps;
   out->retries = 0;

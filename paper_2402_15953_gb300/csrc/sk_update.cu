@@ -871,6 +871,15 @@ int sm_count() {
 
 }  // namespace
 
+// CTAs for the shared-memory sub-sketch kernels: 16 tuples per thread (4096 per CTA of 256),
+// or for small batches up to one CTA per SM with at least max(256, m) tuples each, so that a
+// CTA's flush of its m-counter rows stays below its own counter updates and a batch of a few
+// thousand tuples does not run on a handful of SMs.
+int64_t smem_grid_want(int64_t n, int64_t m, int sms) {
+  const int64_t per = std::max<int64_t>(256, std::min<int64_t>(m, 4096));
+  return std::max<int64_t>((n + 4095) / 4096, std::min<int64_t>(sms, (n + per - 1) / per));
+}
+
 sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols, int64_t col_stride,
                         const int64_t* weights, const int64_t* domain, cudaStream_t st) {
   const RelPlan& rp = s->rel[relation];
@@ -923,10 +932,11 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
                 s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16;
     const int part_fmt = s->d <= 9 ? (part_record_bytes() == 32 ? 0 : 2) : 1;
     // Automatic choice: the tables replace per-tuple hashing by gathers, which pays when
-    // the domains are small against the batch and the counter updates hit L2 (for a sketch
+    // the domains are small against a batch of at least 2^16 tuples (below that the table's
+    // launch and allocation cost more than the hashing) and the counter updates hit L2 (for a sketch
     // much larger than L2 the update is bound by its atomics either way and the gathers
     // only add traffic: 27.7 vs 24.7 ms for 8 x 1e7 rows into 128 MB sketches).
-    const bool worth = ktm == 1 || (total * 4 <= n * (int64_t)rp.a &&
+    const bool worth = ktm == 1 || (n >= ((int64_t)1 << 16) && total * 4 <= n * (int64_t)rp.a &&
                                     (size_t)s->d * (size_t)s->m * sizeof(int64_t) <= ((size_t)32 << 20));
     void* staging = nullptr;
     if (fits && worth && total > 0 && part) {
@@ -966,7 +976,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
         } else if (e == cudaSuccess) {
           if (use_smem) {
             const int per_sm = sub_bytes <= 48 * 1024 ? 4 : (sub_bytes <= 100 * 1024 ? 2 : 1);
-            const int64_t want = (n + 256 * 16 - 1) / (256 * 16);
+            const int64_t want = smem_grid_want(n, s->m, sms);
             const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)sms * per_sm);
             const int64_t tpc = (n + (int64_t)grid * 256 - 1) / ((int64_t)grid * 256) * 256;
             a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(tpc, 1);
@@ -1013,7 +1023,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
   if (use_smem) {
     const size_t smem = coef_bytes + sub_bytes;
     const int per_sm = smem <= 48 * 1024 ? 4 : (smem <= 100 * 1024 ? 2 : 1);
-    int64_t want = (n + 256 * 16 - 1) / (256 * 16);
+    int64_t want = smem_grid_want(n, s->m, sms);
     int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)sms * per_sm);
     const int64_t tpc = (n + (int64_t)grid * 256 - 1) / ((int64_t)grid * 256) * 256;
     a.smem_wmax = (int64_t)0x7fffffff / std::max<int64_t>(tpc, 1);

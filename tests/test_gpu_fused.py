@@ -258,3 +258,25 @@ def test_small_width_single_launch_smem_edges(r, m):
     e = _estimate(attrs, edges, m, d, seed, rels, "fused")
     assert e["limb_bits"] == 0 and 1 <= e["max_limbs"] <= 9
     assert e["rows"] == _oracle_rows(attrs, edges, m, d, seed, rels)
+
+
+def test_small_width_rows_take_their_own_prime_counts():
+    """The single-launch form bounds each row by itself: at m = 2, relation 1 holds two keys
+    of weight +2^50 and -2^50, so in rows where they share a bin with the same sign its vector
+    is zero (estimate 0, one prime) and elsewhere the row needs several primes.  Every row
+    equals the oracle's, over seeds that produce both kinds of rows."""
+    zero_rows = wide_rows = 0
+    for seed in (11, 12, 13, 14):
+        rng = random.Random(seed)
+        x, z = 5, 9
+        r1 = (np.array([[x, z]], dtype=np.int64), np.array([1 << 50, -(1 << 50)], dtype=np.int64))
+        keys = [x] + [rng.randrange(40) for _ in range(199)]
+        r2 = (np.array([keys], dtype=np.int64),
+              np.array([rng.choice([-1, 1]) * rng.randrange(1, 1 << 40) for _ in keys], dtype=np.int64))
+        rels = [r1, r2]
+        e = _estimate([1, 1], [(0, 0, 1, 0)], 2, 9, seed, rels, "fused")
+        assert e["limb_bits"] == 0
+        assert e["rows"] == _oracle_rows([1, 1], [(0, 0, 1, 0)], 2, 9, seed, rels), seed
+        zero_rows += sum(1 for v in e["rows"] if v == 0)
+        wide_rows += sum(1 for v in e["rows"] if abs(v) > (1 << 62))
+    assert zero_rows > 0 and wide_rows > 0
