@@ -52,6 +52,10 @@ def parse_args():
                     help="star: the headline step; batched: 256 relations, persistent plan vs per-relation "
                          "launches; serving: request loop latency")
     ap.add_argument("--requests", type=int, default=4000)
+    ap.add_argument("--serving-rates", default="0.1,0.3,0.5,0.7,0.9",
+                    help="serving: offered arrival rates as fractions of the saturated request rate")
+    ap.add_argument("--sweep-requests", type=int, default=10_000,
+                    help="serving: requests per offered-rate point")
     ap.add_argument("--no-domains", action="store_true",
                     help="do not declare the key domains (every tuple is hashed; no key tables)")
     ap.add_argument("--estimate-priority", default="normal", choices=["high", "normal"],
@@ -736,8 +740,8 @@ def run_serving(args, world, rank):
     """64 live sets (chains of 2-6 relations, m = 2^14..2^18, d = 9); update batches of
     log-uniform 1e3..1e6 tuples (Zipf 1.1 keys over 1e6, 5% of rows deleted) and estimate
     requests, 10:1, Poisson arrivals; HBM budget 32 GB.  First every request is submitted
-    at once (saturated throughput), then arrivals at 50% and 90% of that rate; latency =
-    arrival to result on the host.  Parity: every estimate of the saturated run equals the
+    at once (saturated throughput), then arrivals at 10, 30, 50, 70 and 90% of that rate, 1e4
+    requests per point; latency = arrival to result on the host.  Parity: every estimate of the saturated run equals the
     same request run one by one, and the oracle's for two sets."""
     import numpy as np
     import torch
@@ -898,8 +902,11 @@ def run_serving(args, world, rank):
     cap = capacity(trace)
     seq, seq_rows = sequential(trace)
     points = {"saturated": sat, "server_capacity": cap, "sequential_one_by_one": seq}
-    for frac in (0.5, 0.9):
-        points[f"rate_{int(frac * 100)}pct"], _ = run(trace, frac * sat["requests_per_s"])
+    sweep = make_trace(args.sweep_requests, 3)
+    for frac in [float(x) for x in args.serving_rates.split(",") if x]:
+        pt, _ = run(sweep, frac * sat["requests_per_s"])
+        pt["offered_requests_per_s"] = frac * sat["requests_per_s"]
+        points[f"rate_{int(round(frac * 100))}pct"] = pt
     clocks = clk.stop()
     mixed_equal = set(sat_rows) == set(seq_rows) and all(sat_rows[j] == seq_rows[j] for j in seq_rows)
     oracle_ok, checked = oracle_check(trace, seq_rows)
