@@ -327,6 +327,7 @@ __host__ __device__ __forceinline__ uint64_t gl_pow(uint64_t b, uint64_t e) {
 struct CplxOps {
   using T = double2;
   static constexpr bool kExact = false;   // rounding: twiddles always come from the table
+  static constexpr bool kReg = false;     // transforms through smem_dif_il
   static __device__ __forceinline__ T mul(T a, T b) { return cmul(a, b); }
   static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
   static __device__ __forceinline__ T sub(T a, T b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -345,6 +346,7 @@ struct CplxOps {
 struct GlOps {
   using T = uint64_t;
   static constexpr bool kExact = true;
+  static constexpr bool kReg = false;   // transforms through smem_dif_il
   static __device__ __forceinline__ T mul(T a, T b) { return gl_mul(a, b); }
   static __device__ __forceinline__ T add(T a, T b) { return gl_add(a, b); }
   static __device__ __forceinline__ T sub(T a, T b) { return gl_sub(a, b); }
@@ -497,10 +499,127 @@ __device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register transforms (exact arithmetics only, lengths L = 2^8..2^10).  A length-L DFT in
+// natural order is taken as A x B (L = A B): with x_i at i = B a + b and X_k at k = c + A e,
+//   X[c + A e] = sum_b w_B^(b e) (w_L^(b c) sum_a x[B a + b] w_A^(a c)),
+// so step 1 gives each thread one b: the A-point DFT over a of its stride-B elements, held in
+// registers, times w_L^(b c), written back to the same positions B c + b; step 2 gives each
+// thread one c: the B-point DFT over b of the contiguous block B c .. B c + B - 1, written
+// to the positions c + A e.  Every twiddle is a power of w_L, read from an L-entry table in
+// shared memory (the same entry across the threads of one vector: broadcast reads).
+// ---------------------------------------------------------------------------
+template <int LOG>
+__host__ __device__ constexpr int bitrev_const(int k) {
+  int r = 0;
+  for (int i = 0; i < LOG; i++) r |= ((k >> i) & 1) << (LOG - 1 - i);
+  return r;
+}
+
+// 2^LOG-point DFT of x (natural order in and out); wt[j] = w_N^j for j < N / 2.  Radix-2
+// decimation in frequency (stage s pairs j and j + N / 2^(s+1) with the twiddle
+// w_N^(j 2^s)), then the bit reversal as a renaming of registers.
+template <class Ops, int LOG>
+__device__ __forceinline__ void reg_dft(typename Ops::T (&x)[1 << LOG], const typename Ops::T (&wt)[(1 << LOG) / 2]) {
+  using T = typename Ops::T;
+  constexpr int N = 1 << LOG;
+#pragma unroll
+  for (int st = 0; st < LOG; st++) {
+    const int h = N >> (st + 1);
+#pragma unroll
+    for (int blk = 0; blk < N; blk += 2 * h) {
+#pragma unroll
+      for (int j = 0; j < h; j++) {
+        const T u = x[blk + j], v = x[blk + j + h];
+        x[blk + j] = Ops::add(u, v);
+        const T dl = Ops::sub(u, v);
+        x[blk + j + h] = j == 0 ? dl : Ops::mul(dl, wt[j << st]);
+      }
+    }
+  }
+  T y[N];
+#pragma unroll
+  for (int k = 0; k < N; k++) y[k] = x[bitrev_const<LOG>(k)];
+#pragma unroll
+  for (int k = 0; k < N; k++) x[k] = y[k];
+}
+
+// In-place natural-order DFTs of `cnt` (a power of two) vectors of length L = 2^(LA + LB),
+// element i of vector v at s[i S + v]; stw[e] = w_L^e for e < L.  Needs cnt 2^max(LA, LB)
+// <= blockDim.x (one A- or B-point DFT per thread and step).  Ends with a barrier.
+template <class Ops, int LA, int LB>
+__device__ void smem_ntt_2lvl(typename Ops::T* s, int cnt, int S, const typename Ops::T* stw) {
+  using T = typename Ops::T;
+  constexpr int A = 1 << LA, B = 1 << LB;
+  const int lc = __ffs(cnt) - 1;
+  const int t = threadIdx.x;
+  {
+    T w[A / 2];
+#pragma unroll
+    for (int j = 0; j < A / 2; j++) w[j] = stw[B * j];   // w_A^j
+    if (t < cnt * B) {
+      const int v = t & (cnt - 1), b = t >> lc;
+      T x[A];
+#pragma unroll
+      for (int a = 0; a < A; a++) x[a] = s[(B * a + b) * S + v];
+      reg_dft<Ops, LA>(x, w);
+#pragma unroll
+      for (int c = 1; c < A; c++) x[c] = Ops::mul(x[c], stw[b * c]);
+#pragma unroll
+      for (int c = 0; c < A; c++) s[(B * c + b) * S + v] = x[c];
+    }
+  }
+  __syncthreads();
+  {
+    T w[B / 2];
+#pragma unroll
+    for (int j = 0; j < B / 2; j++) w[j] = stw[A * j];   // w_B^j
+    const bool act = t < cnt * A;
+    const int v = t & (cnt - 1), c = t >> lc;
+    T x[B];
+    if (act) {
+#pragma unroll
+      for (int b = 0; b < B; b++) x[b] = s[(B * c + b) * S + v];
+    }
+    __syncthreads();   // every block read before any position c + A e is written
+    if (act) {
+      reg_dft<Ops, LB>(x, w);
+#pragma unroll
+      for (int e = 0; e < B; e++) s[(c + A * e) * S + v] = x[e];
+    }
+  }
+  __syncthreads();
+}
+
+// The register transform for length 2^logL when this arithmetic has one (kReg) and the tile
+// of cnt vectors fits it; fills stw (L entries) from the length-N half table first.  false:
+// nothing done (the caller takes smem_dif_il, bit-reversed output).
+template <class Ops>
+__device__ bool smem_ntt_reg(typename Ops::T* s, int cnt, int S, int logL, const typename Ops::T* __restrict__ tw,
+                             int64_t twstride, int64_t N, bool inv, typename Ops::T* stw) {
+  if constexpr (Ops::kReg) {
+    if (logL < 8 || logL > 10 || (cnt << (logL - logL / 2)) > (int)blockDim.x) return false;
+    const int L = 1 << logL;
+    for (int e = threadIdx.x; e < L; e += blockDim.x) stw[e] = twid<Ops>(tw, ((int64_t)e * twstride) & (N - 1), N >> 1, inv);
+    __syncthreads();
+    if (logL == 8) smem_ntt_2lvl<Ops, 4, 4>(s, cnt, S, stw);
+    else if (logL == 9) smem_ntt_2lvl<Ops, 4, 5>(s, cnt, S, stw);
+    else smem_ntt_2lvl<Ops, 5, 5>(s, cnt, S, stw);
+    return true;
+  } else {
+    return false;
+  }
+}
+
+// loads each thread of the four-step passes keeps in flight while filling its tile (16
+// measured no faster than 8 for 32-bit residues)
+template <class T>
+constexpr int kLoadBatchOf = 8;
+
 // four-step, pass 1: length-R transforms down the columns of the R x C view
 // (element n1 * C + n2), then the twiddle w_N^(n2 k1); in place.  Tile: cb columns.
 template <class Ops>
-__global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC, int cb,
+__global__ void __launch_bounds__(512, 2) k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC, int cb,
                           const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
   using T = typename Ops::T;
   extern __shared__ __align__(16) unsigned char xf_smem[];
@@ -513,12 +632,26 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
   const int64_t vec = blockIdx.x >> (logC - lcb);
   const int c0 = (blockIdx.x & (blocks_per_vec - 1)) * cb;
   T* v = buf + vec * N;
-  for (int idx = threadIdx.x; idx < R * cb; idx += blockDim.x) {
-    const int c = idx & (cb - 1), n1 = idx >> lcb;
-    sm[n1 * S + c] = v[(int64_t)n1 * C + c0 + c];
+  // the tile: kLoadBatch loads per thread in flight before their shared-memory stores
+  constexpr int kLoadBatch = kLoadBatchOf<T>;
+  for (int i0 = threadIdx.x; i0 < R * cb; i0 += kLoadBatch * blockDim.x) {
+    T tmp[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; u++) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < R * cb) tmp[u] = v[(int64_t)(idx >> lcb) * C + c0 + (idx & (cb - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; u++) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < R * cb) sm[(idx >> lcb) * S + (idx & (cb - 1))] = tmp[u];
+    }
   }
   __syncthreads();
-  smem_dif_il<Ops>(sm, cb, S, logR, tw, C, inv, r4);
+  // natural-order register transform where it applies (its twiddle table after the tile),
+  // else the radix-2 one with bit-reversed output
+  const bool nat = smem_ntt_reg<Ops>(sm, cb, S, logR, tw, C, N, inv, sm + (int64_t)R * S);
+  if (!nat) smem_dif_il<Ops>(sm, cb, S, logR, tw, C, inv, r4);
   const int64_t half = N >> 1;
   if (Ops::kExact && (blockDim.x & (cb - 1)) == 0) {
     // each thread keeps one column n2 and walks rows k1 = k1_0 + j kstep: the twiddle
@@ -529,7 +662,7 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
     T w = twid<Ops>(tw, (n2 * (threadIdx.x >> lcb)) & (N - 1), half, inv);
     const T ws = twid<Ops>(tw, (n2 * kstep) & (N - 1), half, inv);
     for (int k1 = threadIdx.x >> lcb; k1 < R; k1 += kstep) {
-      v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
+      v[(int64_t)k1 * C + n2] = Ops::mul(sm[(nat ? k1 : bitrev(k1, logR)) * S + c], w);
       w = Ops::mul(w, ws);
     }
   } else {
@@ -537,7 +670,7 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
       const int c = idx & (cb - 1), k1 = idx >> lcb;
       const int64_t n2 = c0 + c;
       const T w = twid<Ops>(tw, (n2 * k1) & (N - 1), half, inv);
-      v[(int64_t)k1 * C + n2] = Ops::mul(sm[bitrev(k1, logR) * S + c], w);
+      v[(int64_t)k1 * C + n2] = Ops::mul(sm[(nat ? k1 : bitrev(k1, logR)) * S + c], w);
     }
   }
 }
@@ -545,7 +678,7 @@ __global__ void k_xf_cols(typename Ops::T* __restrict__ buf, int logR, int logC,
 // four-step, pass 2: length-C transforms along the rows k1, written to the
 // natural-order output X[k1 + R k2]; out of place.  Tile: rb rows.
 template <class Ops>
-__global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::T* __restrict__ out, int logR,
+__global__ void __launch_bounds__(512, 2) k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::T* __restrict__ out, int logR,
                           int logC, int rb, const typename Ops::T* __restrict__ tw, bool inv, typename Ops::T r4) {
   using T = typename Ops::T;
   extern __shared__ __align__(16) unsigned char xf_smem[];
@@ -559,15 +692,26 @@ __global__ void k_xf_rows(const typename Ops::T* __restrict__ in, typename Ops::
   const int r0 = (blockIdx.x & (blocks_per_vec - 1)) * rb;
   const T* vi = in + vec * N;
   T* vo = out + vec * N;
-  for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
-    const int rr = idx >> logC, n2 = idx & (C - 1);
-    sm[n2 * S + rr] = vi[(int64_t)(r0 + rr) * C + n2];
+  constexpr int kLoadBatch = kLoadBatchOf<T>;
+  for (int i0 = threadIdx.x; i0 < C * rb; i0 += kLoadBatch * blockDim.x) {
+    T tmp[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; u++) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < C * rb) tmp[u] = vi[(int64_t)(r0 + (idx >> logC)) * C + (idx & (C - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; u++) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < C * rb) sm[(idx & (C - 1)) * S + (idx >> logC)] = tmp[u];
+    }
   }
   __syncthreads();
-  smem_dif_il<Ops>(sm, rb, S, logC, tw, R, inv, r4);
+  const bool nat = smem_ntt_reg<Ops>(sm, rb, S, logC, tw, R, N, inv, sm + (int64_t)C * S);
+  if (!nat) smem_dif_il<Ops>(sm, rb, S, logC, tw, R, inv, r4);
   for (int idx = threadIdx.x; idx < C * rb; idx += blockDim.x) {
     const int rr = idx & (rb - 1), k2 = idx >> lrb;
-    vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[bitrev(k2, logC) * S + rr];
+    vo[(int64_t)(r0 + rr) + (int64_t)R * k2] = sm[(nat ? k2 : bitrev(k2, logC)) * S + rr];
   }
 }
 
@@ -1078,7 +1222,20 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
   while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
   if ((cb & (cb - 1)) || (rb & (rb - 1))) return SK_ERR_INVALID_ARG;   // the kernels index by shifts
-  const size_t smc = (size_t)(cb + 1) * R * esz, smr = (size_t)(rb + 1) * C * esz;   // padded tiles
+  // the register transform (exact arithmetics, lengths 2^8..2^10) takes one A- or B-point DFT
+  // per thread: at most 512 >> max(log A, log B) vectors per tile; plus its twiddle table
+  size_t smc_tw = 0, smr_tw = 0;
+  if (Ops::kReg) {
+    if (logR >= 8 && logR <= 10) {
+      cb = std::min(cb, 512 >> (logR - logR / 2));
+      smc_tw = (size_t)R * esz;
+    }
+    if (logC >= 8 && logC <= 10) {
+      rb = std::min(rb, 512 >> (logC - logC / 2));
+      smr_tw = (size_t)C * esz;
+    }
+  }
+  const size_t smc = (size_t)(cb + 1) * R * esz + smc_tw, smr = (size_t)(rb + 1) * C * esz + smr_tw;   // padded tiles
   SK_CK(allow_dynamic_smem((const void*)k_xf_cols<Ops>));
   SK_CK(allow_dynamic_smem((const void*)k_xf_rows<Ops>));
   k_xf_cols<Ops><<<(unsigned)(batch * (C / cb)), 512, smc, st>>>(src, logR, logC, cb, tw, inv, r4);
@@ -1293,6 +1450,7 @@ template <int PI>
 struct MontOps {
   using T = uint32_t;
   static constexpr bool kExact = true;
+  static constexpr bool kReg = true;    // lengths 2^8..2^10 through smem_ntt_2lvl
   static __device__ __forceinline__ T mul(T a, T b) { return mont32(a, b, c_fu_p[PI], c_fu_pinv[PI]); }
   static __device__ __forceinline__ T add(T a, T b) {
     const uint32_t p = c_fu_p[PI], s = a + b;
@@ -1335,10 +1493,20 @@ __global__ void __launch_bounds__(256) k_fu_norms(const int64_t* const* base, in
   const int64_t j0 = ch * len, j1 = j0 + len < m ? j0 + len : m;
   const int64_t* c = base[v / per] + (v % per) * m;
   double s1 = 0.0, s2 = 0.0;
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    const double x = (double)__ldg(c + j);
-    s1 += fabs(x);
-    s2 += x * x;
+  constexpr int U = 8;   // loads in flight per thread
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += U * (int64_t)blockDim.x) {
+    int64_t x[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t jj = j + u * (int64_t)blockDim.x;
+      x[u] = jj < j1 ? __ldg(c + jj) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const double v = (double)x[u];
+      s1 += fabs(v);
+      s2 += v * v;
+    }
   }
   red1[threadIdx.x] = s1;
   red2[threadIdx.x] = s2;
@@ -1421,13 +1589,22 @@ __global__ void k_fu_load(const int64_t* const* rel, int r, int d, int64_t m, ui
   const int k = blockIdx.y;            // relation: its d x m counters are contiguous
   const int64_t* src = rel[k];
   out += (int64_t)k * dm;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < dm; g += step) {
-    const int64_t c = src[g];
-    const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
-    uint32_t h = (uint32_t)(mag >> 32);
-    if (h >= p) h -= p;
-    const uint32_t v = O::add(O::mul(h, r3), O::mul((uint32_t)mag, r2));
-    out[g] = c < 0 ? O::neg(v) : v;
+  constexpr int U = 4;   // loads in flight per thread
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < dm; g0 += U * step) {
+    int64_t cv[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) cv[u] = g0 + u * step < dm ? src[g0 + u * step] : 0;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t g = g0 + u * step;
+      if (g >= dm) break;
+      const int64_t c = cv[u];
+      const uint64_t mag = c < 0 ? 0ull - (uint64_t)c : (uint64_t)c;
+      uint32_t h = (uint32_t)(mag >> 32);
+      if (h >= p) h -= p;
+      const uint32_t v = O::add(O::mul(h, r3), O::mul((uint32_t)mag, r2));
+      out[g] = c < 0 ? O::neg(v) : v;
+    }
   }
 }
 
@@ -1440,10 +1617,18 @@ __global__ void __launch_bounds__(256) k_fu_reduce(const uint32_t* W, int r, int
   const int row = blockIdx.x / nchunk, c = blockIdx.x % nchunk;
   const int64_t clen = M / nchunk;
   uint32_t s = 0;
+  constexpr int KR = 8;   // factors loaded before their products
   for (int64_t nu = (int64_t)c * clen + threadIdx.x; nu < (int64_t)(c + 1) * clen; nu += blockDim.x) {
     const int64_t neg_nu = (M - nu) & (M - 1);
-    uint32_t prod = W[(int64_t)row * M + ((negmask & 1ull) ? neg_nu : nu)];
-    for (int k = 1; k < r; k++)
+    uint32_t f[KR];
+#pragma unroll
+    for (int k = 0; k < KR; k++)
+      if (k < r) f[k] = W[((int64_t)k * d + row) * M + (((negmask >> k) & 1ull) ? neg_nu : nu)];
+    uint32_t prod = f[0];
+#pragma unroll
+    for (int k = 1; k < KR; k++)
+      if (k < r) prod = O::mul(prod, f[k]);
+    for (int k = KR; k < r; k++)
       prod = O::mul(prod, W[((int64_t)k * d + row) * M + (((negmask >> k) & 1ull) ? neg_nu : nu)]);
     s = O::add(s, prod);
   }
@@ -1819,7 +2004,7 @@ sk_status fu_setup(sk_set* s, int64_t M, bool pairwise, cudaStream_t st, FuSetup
   }
   // scratch: norm partials [r][d][l1ch][2] doubles | residues [d][9] | partials [d][nchunk]
   int nchunk = 1;
-  while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)d * nchunk * 2 <= 1024) nchunk *= 2;
+  while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)d * nchunk * 2 <= 4096) nchunk *= 2;
   const int l1ch = fu_l1_chunks((int64_t)r * d, m);
   const size_t l1_bytes = ((size_t)r * d * l1ch * 16 + 255) & ~(size_t)255;
   const size_t res_bytes = ((size_t)d * kFuMaxPrimes * 4 + 255) & ~(size_t)255;
@@ -2484,10 +2669,18 @@ __global__ void __launch_bounds__(256) k_fu_reduce_many(const uint32_t* W, const
   const int c = blockIdx.x % nchunk;
   const int64_t clen = M / nchunk;
   uint32_t s = 0;
+  constexpr int KR = 8;   // factors loaded before their products
   for (int64_t nu = (int64_t)c * clen + threadIdx.x; nu < (int64_t)(c + 1) * clen; nu += blockDim.x) {
     const int64_t neg_nu = (M - nu) & (M - 1);
-    uint32_t prod = W[(f.base + f.row) * M + ((f.negmask & 1ull) ? neg_nu : nu)];
-    for (int k = 1; k < f.r; k++)
+    uint32_t fk[KR];
+#pragma unroll
+    for (int k = 0; k < KR; k++)
+      if (k < f.r) fk[k] = W[(f.base + (int64_t)k * f.d + f.row) * M + (((f.negmask >> k) & 1ull) ? neg_nu : nu)];
+    uint32_t prod = fk[0];
+#pragma unroll
+    for (int k = 1; k < KR; k++)
+      if (k < f.r) prod = O::mul(prod, fk[k]);
+    for (int k = KR; k < f.r; k++)
       prod = O::mul(prod, W[(f.base + (int64_t)k * f.d + f.row) * M + (((f.negmask >> k) & 1ull) ? neg_nu : nu)]);
     s = O::add(s, prod);
   }
