@@ -1488,6 +1488,12 @@ __global__ void k_fu_twiddle(uint32_t* tw, uint32_t* itw, int64_t n, uint32_t w,
 // host adds a vector's partials in order (double; the bounds carry a safety margin).
 __global__ void __launch_bounds__(256) k_fu_norms(const int64_t* const* base, int per, int64_t m, int nch,
                                                   double* part) {
+  // Each thread sums 8 loaded values at a time in FP32, as |c| 2^-32 and (|c| 2^-32)^2 (the
+  // scaling keeps the square of 2^63 inside the float range), and adds each 8-term sum into
+  // double accumulators: GB300's FP64 rate would bound a loop of double operations per
+  // element.  A term is within 2^-22 of its value and an 8-term float sum within 7 2^-24
+  // more, so the partials are within a relative 2^-19 of the exact sums (the double
+  // additions add nothing comparable), inside the 2^-10 margin fu_row_bits applies.
   __shared__ double red1[256], red2[256];
   const int64_t v = blockIdx.x / nch, ch = blockIdx.x % nch, len = (m + nch - 1) / nch;
   const int64_t j0 = ch * len, j1 = j0 + len < m ? j0 + len : m;
@@ -1501,12 +1507,17 @@ __global__ void __launch_bounds__(256) k_fu_norms(const int64_t* const* base, in
       const int64_t jj = j + u * (int64_t)blockDim.x;
       x[u] = jj < j1 ? __ldg(c + jj) : 0;
     }
+    float f1 = 0.0f, f2 = 0.0f;
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const double v = (double)x[u];
-      s1 += fabs(v);
-      s2 += v * v;
+      const uint64_t mag = x[u] < 0 ? 0ull - (uint64_t)x[u] : (uint64_t)x[u];
+      // |c| 2^-32 = hi + lo 2^-32
+      const float a = fmaf((float)(uint32_t)mag, 2.3283064365386963e-10f, (float)(uint32_t)(mag >> 32));
+      f1 += a;
+      f2 = fmaf(a, a, f2);
     }
+    s1 += (double)f1;
+    s2 += (double)f2;
   }
   red1[threadIdx.x] = s1;
   red2[threadIdx.x] = s2;
@@ -1519,8 +1530,8 @@ __global__ void __launch_bounds__(256) k_fu_norms(const int64_t* const* base, in
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    part[2 * (int64_t)blockIdx.x] = red1[0];
-    part[2 * (int64_t)blockIdx.x + 1] = red2[0];
+    part[2 * (int64_t)blockIdx.x] = red1[0] * 4294967296.0;                 // sum |c|
+    part[2 * (int64_t)blockIdx.x + 1] = red2[0] * 18446744073709551616.0;   // sum c^2
   }
 }
 
@@ -1564,11 +1575,14 @@ sk_status fu_norms(const int64_t* const* base, int per, int64_t nvec, int64_t m,
 // margin of 1e-9 for the rounding of the double sums.
 double fu_row_bits(const double* l1, const double* l2, int r, int64_t stride, bool pairwise) {
   double b = 0.0, best1 = 0.0, best2 = 0.0;
+  // the norms come from k_fu_norms's FP32 partial sums: within a relative 2^-19 of the exact
+  // ones, so scaling l1 up by 2^-10 keeps b an upper bound; l2 scaled up only lowers the savings
+  constexpr double kUp = 1.0 + 1.0 / 1024.0;
   for (int k = 0; k < r; k++) {
     const double v1 = l1[k * stride], v2 = l2[k * stride];
     if (v1 <= 0.0) return -1.0;
-    b += std::log2(v1 * (1.0 + 1e-9));
-    const double save = std::log2(v1 * (1.0 + 1e-9)) - std::log2(v2 * (1.0 + 1e-9));
+    b += std::log2(v1 * kUp);
+    const double save = std::log2(v1) - std::log2(v2 * kUp);
     if (save > best1) {
       best2 = best1;
       best1 = save;
