@@ -500,7 +500,7 @@ __device__ void smem_dif_il(typename Ops::T* s, int cnt, int S, int logL, const 
 }
 
 // ---------------------------------------------------------------------------
-// Register transforms (exact arithmetics only, lengths L = 2^8..2^10).  A length-L DFT in
+// Register transforms (exact arithmetics only, lengths L = 2^6..2^10).  A length-L DFT in
 // natural order is taken as A x B (L = A B): with x_i at i = B a + b and X_k at k = c + A e,
 //   X[c + A e] = sum_b w_B^(b e) (w_L^(b c) sum_a x[B a + b] w_A^(a c)),
 // so step 1 gives each thread one b: the A-point DFT over a of its stride-B elements, held in
@@ -598,13 +598,17 @@ template <class Ops>
 __device__ bool smem_ntt_reg(typename Ops::T* s, int cnt, int S, int logL, const typename Ops::T* __restrict__ tw,
                              int64_t twstride, int64_t N, bool inv, typename Ops::T* stw) {
   if constexpr (Ops::kReg) {
-    if (logL < 8 || logL > 10 || (cnt << (logL - logL / 2)) > (int)blockDim.x) return false;
+    if (logL < 6 || logL > 10 || (cnt << (logL - logL / 2)) > (int)blockDim.x) return false;
     const int L = 1 << logL;
     for (int e = threadIdx.x; e < L; e += blockDim.x) stw[e] = twid<Ops>(tw, ((int64_t)e * twstride) & (N - 1), N >> 1, inv);
     __syncthreads();
-    if (logL == 8) smem_ntt_2lvl<Ops, 4, 4>(s, cnt, S, stw);
-    else if (logL == 9) smem_ntt_2lvl<Ops, 4, 5>(s, cnt, S, stw);
-    else smem_ntt_2lvl<Ops, 5, 5>(s, cnt, S, stw);
+    switch (logL) {
+      case 6: smem_ntt_2lvl<Ops, 3, 3>(s, cnt, S, stw); break;
+      case 7: smem_ntt_2lvl<Ops, 3, 4>(s, cnt, S, stw); break;
+      case 8: smem_ntt_2lvl<Ops, 4, 4>(s, cnt, S, stw); break;
+      case 9: smem_ntt_2lvl<Ops, 4, 5>(s, cnt, S, stw); break;
+      default: smem_ntt_2lvl<Ops, 5, 5>(s, cnt, S, stw); break;
+    }
     return true;
   } else {
     return false;
@@ -1222,15 +1226,15 @@ sk_status xform(typename Ops::T* src, typename Ops::T* dst, int64_t batch, int64
   while (cb > 4 && batch * (C / cb) < want) cb >>= 1;
   while (rb > 1 && batch * (R / rb) < want) rb >>= 1;
   if ((cb & (cb - 1)) || (rb & (rb - 1))) return SK_ERR_INVALID_ARG;   // the kernels index by shifts
-  // the register transform (exact arithmetics, lengths 2^8..2^10) takes one A- or B-point DFT
+  // the register transform (exact arithmetics, lengths 2^6..2^10) takes one A- or B-point DFT
   // per thread: at most 512 >> max(log A, log B) vectors per tile; plus its twiddle table
   size_t smc_tw = 0, smr_tw = 0;
   if (Ops::kReg) {
-    if (logR >= 8 && logR <= 10) {
+    if (logR >= 6 && logR <= 10) {
       cb = std::min(cb, 512 >> (logR - logR / 2));
       smc_tw = (size_t)R * esz;
     }
-    if (logC >= 8 && logC <= 10) {
+    if (logC >= 6 && logC <= 10) {
       rb = std::min(rb, 512 >> (logC - logC / 2));
       smr_tw = (size_t)C * esz;
     }
@@ -1450,7 +1454,7 @@ template <int PI>
 struct MontOps {
   using T = uint32_t;
   static constexpr bool kExact = true;
-  static constexpr bool kReg = true;    // lengths 2^8..2^10 through smem_ntt_2lvl
+  static constexpr bool kReg = true;    // lengths 2^6..2^10 through smem_ntt_2lvl
   static __device__ __forceinline__ T mul(T a, T b) { return mont32(a, b, c_fu_p[PI], c_fu_pinv[PI]); }
   static __device__ __forceinline__ T add(T a, T b) {
     const uint32_t p = c_fu_p[PI], s = a + b;
