@@ -1169,6 +1169,27 @@ double twiddle_error(int64_t M, const double2* d_tw, cudaStream_t st) {
 // ever used by earlier work of this estimate on the same stream (sk_estimate_join
 // synchronises its stream before returning), so freeing and reallocating in stream
 // order needs no device-wide synchronisation.
+// (Re)allocates a per-set table on the stream (stream-ordered: no device-wide
+// synchronisation, which cudaFree would impose on every other stream, e.g. a server's update
+// streams, the first time a set is estimated at a width).
+cudaError_t table_alloc(void** p, size_t bytes, cudaStream_t st) {
+  if (*p) {
+    cudaError_t e = cudaFreeAsync(*p, st);
+    if (e != cudaSuccess) return e;
+    *p = nullptr;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
+
+// The device copy of the set's relation counter pointers (stream-ordered, once per set).
+cudaError_t fu_rel_table(sk_set* s, cudaStream_t st) {
+  if (s->d_fu_rel) return cudaSuccess;
+  cudaError_t e = cudaMallocAsync((void**)&s->d_fu_rel, sizeof(int64_t*) * s->r, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * s->r, cudaMemcpyHostToDevice, st);
+  return e;
+}
+
 cudaError_t ensure(Scratch& s, size_t bytes, cudaStream_t st) {
   if (s.bytes >= bytes) return cudaSuccess;
   if (s.ptr) {
@@ -1285,9 +1306,7 @@ sk_status corr_ntt(sk_set* s, const I256* a, const I256* x, I256* z, int* zbits,
   const int d = s->d;
   const int logM = ilog2(M);
   if (s->gl_m != M) {
-    if (s->d_gl_tw) cudaFree(s->d_gl_tw);
-    s->d_gl_tw = nullptr;
-    SK_CK(cudaMalloc(&s->d_gl_tw, (size_t)M * sizeof(uint64_t)));   // [w^t | w^-t], t < M/2
+    SK_CK(table_alloc((void**)&s->d_gl_tw, (size_t)M * sizeof(uint64_t), st));   // [w^t | w^-t], t < M/2
     const uint64_t w = gl_pow(7, (kGL - 1) / (uint64_t)M);          // 7 generates GF(q)*
     if (M >= 2 && gl_pow(w, (uint64_t)M / 2) != kGL - 1) return SK_ERR_INEXACT;   // not a primitive root
     const uint64_t winv = gl_pow(w, kGL - 2);
@@ -2016,10 +2035,7 @@ sk_status fu_setup(sk_set* s, int64_t M, bool pairwise, cudaStream_t st, FuSetup
   const int64_t m = s->m;
   const int r = s->r, d = s->d;
   const std::vector<FuPrime>& pr = fu_primes();
-  if (!s->d_fu_rel) {
-    SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
-    SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
-  }
+  SK_CK(fu_rel_table(s, st));
   // scratch: norm partials [r][d][l1ch][2] doubles | residues [d][9] | partials [d][nchunk]
   int nchunk = 1;
   while ((int64_t)nchunk * 2 * 256 <= M && (int64_t)d * nchunk * 2 <= 4096) nchunk *= 2;
@@ -2042,10 +2058,8 @@ sk_status fu_setup(sk_set* s, int64_t M, bool pairwise, cudaStream_t st, FuSetup
   while (np < kFuMaxPrimes && cover < bits + 3.0) cover += pr[np++].log2p;
   f->np = cover < bits + 3.0 ? 0 : np;
   if (f->np && (s->fu_m != M || !s->d_fu_tw)) {
-    if (s->d_fu_tw) cudaFree(s->d_fu_tw);
-    s->d_fu_tw = nullptr;
     s->fu_np = 0;
-    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * M * sizeof(uint32_t)));
+    SK_CK(table_alloc((void**)&s->d_fu_tw, (size_t)kFuMaxPrimes * M * sizeof(uint32_t), st));
     s->fu_m = M;
   }
   return SK_OK;
@@ -2097,15 +2111,10 @@ sk_status run_estimate_pairwise_small(sk_set* s, sk_estimate* out, unsigned long
   const int64_t m = s->m;
   const int r = s->r, d = s->d;
   const std::vector<FuPrime>& pr = fu_primes();
-  if (!s->d_fu_rel) {
-    SK_CK(cudaMalloc(&s->d_fu_rel, sizeof(int64_t*) * r));
-    SK_CK(cudaMemcpy(s->d_fu_rel, s->rel_ctr.data(), sizeof(int64_t*) * r, cudaMemcpyHostToDevice));
-  }
+  SK_CK(fu_rel_table(s, st));
   if (s->fu_m != m || !s->d_fu_tw) {
-    if (s->d_fu_tw) cudaFree(s->d_fu_tw);
-    s->d_fu_tw = nullptr;
     s->fu_np = 0;
-    SK_CK(cudaMalloc(&s->d_fu_tw, (size_t)kFuMaxPrimes * m * sizeof(uint32_t)));
+    SK_CK(table_alloc((void**)&s->d_fu_tw, (size_t)kFuMaxPrimes * m * sizeof(uint32_t), st));
     s->fu_m = m;
   }
   if (s->fu_np < kFuMaxPrimes) {
@@ -2449,9 +2458,7 @@ sk_status run_estimate(sk_set* s, sk_estimate* out, cudaStream_t st) {
   const size_t small_bytes = 2 * SK_MAX_ROWS * sizeof(I256) + 256 + cert_words * 8 + 3 * 1024 * 8 + 64;
   SK_CK(ensure(s->scratch, small_off + small_bytes, st));
   if (s->twiddle_m != M) {
-    if (s->d_twiddle) cudaFree(s->d_twiddle);
-    s->d_twiddle = nullptr;
-    SK_CK(cudaMalloc(&s->d_twiddle, (size_t)(M / 2) * sizeof(double2)));
+    SK_CK(table_alloc((void**)&s->d_twiddle, (size_t)(M / 2) * sizeof(double2), st));
     s->twiddle_m = M;
     k_twiddle<<<grid_for(M / 2), 256, 0, st>>>((double2*)s->d_twiddle, M);
     count_launch();
