@@ -2766,7 +2766,7 @@ sk_status fu_group(sk_set** sets, const std::vector<int>& idx, int64_t M, sk_est
                b_l1 = al((size_t)nvec * l1ch * 16), b_res = al((size_t)nout * kFuMaxPrimes * 4), b_part = al((size_t)nout * nchunk * 4),
                b_tw = al((size_t)M * 4), b_v = al((size_t)nvec * M * 4);
   char* blk = nullptr;
-  SK_CK(cudaMallocAsync((void**)&blk, b_rows + b_outs + b_l1 + b_res + b_part + b_tw + 2 * b_v, st));
+  SK_CK(pool_malloc_async((void**)&blk, b_rows + b_outs + b_l1 + b_res + b_part + b_tw + 2 * b_v, st));
   const int64_t** d_rows = (const int64_t**)blk;
   FuOut* d_outs = (FuOut*)(blk + b_rows);
   double* d_l1 = (double*)(blk + b_rows + b_outs);

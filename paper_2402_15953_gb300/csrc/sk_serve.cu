@@ -150,7 +150,9 @@ sk_status launch_batch(sk_server* sv, SvBatch* b) {
   size_t total = head;
   for (SvRequest* q : b->reqs) total += align256(q->bytes);
   char* buf = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&buf, total, sv->copy_stream);
+  // from the library's pool, which keeps its memory mapped between batches (the device's
+  // default pool would return it at every synchronisation and map it again for the next)
+  cudaError_t e = sk::pool_malloc_async((void**)&buf, total, sv->copy_stream);
   if (e != cudaSuccess) return set_status_from_cuda(e);
   std::vector<sk_update_item> items;
   std::vector<std::pair<SvRequest*, std::pair<int64_t*, int64_t*>>> direct;   // own calls
