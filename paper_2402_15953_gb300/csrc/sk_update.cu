@@ -110,17 +110,19 @@ __global__ void __launch_bounds__(256, (A > 0 && V8 && NARROW && POW2) ? 5 : 1) 
 // phases over windows of the batch.  Each row's bins are split into S = m / 2^L parts of
 // 2^L bins, L = min(log2 m, 15), so S is 1 or 2.
 //   1. k_tab_items: per tuple the key-table gathers and each row's bin sum and sign product
-//      (Eqs. 2-3), written tile by tile (32 consecutive tuples, one warp).  Per tile and row:
-//      32 16-bit items, the tuples of part 0 first and then those of part 1 (each item the
-//      bin's offset within its part in bits 0..14 and the sign in bit 15), and one 16-bit
-//      word with the two parts' counts; the tile's rows form one contiguous block.  A tuple
-//      with a key outside its declared domain is left out (and reported, as in every other
-//      path).  Stores carry an L2 evict-first hint, so the items do not push the key tables'
-//      records out of L2.
+//      (Eqs. 2-3).  Each warp of this persistent kernel owns one region of C item slots per
+//      row (C = 32 x its tile count) and appends its tiles' items there: the part-0 items
+//      from the region's start upward, the part-1 items from its end downward (each item the
+//      bin's offset within its part in bits 0..14 and the sign in bit 15).  At the end the warp
+//      writes each row's part-0 count and its count of valid tuples.  A tuple with a key
+//      outside its declared domain is left out (and reported, as in every other path).
+//      Stores carry an L2 evict-first hint, so the items do not push the key tables' records
+//      out of L2.
 //   2. k_part_accum: a CTA owns part h of one row as 2^L int32 counters in shared memory
-//      (at most 128 KB); over a range of tiles each warp takes one tile row per step, lane k
-//      holding slot k, adds the signs of part h's items with shared-memory atomics, and the
-//      CTA finally adds each counter into the int64 sketch with one 64-bit reduction.
+//      (at most 128 KB) over the regions of a range of phase-1 warps; its warps take pieces of
+//      those regions, each lane 8 items (one 16-byte load) at a time, and add the signs with
+//      shared-memory atomics, reading only part h's items; the CTA finally adds each counter
+//      into the int64 sketch with one 64-bit reduction.
 // Every counter receives the same sum as in k_update_tab (integer addition in any order);
 // a CTA's int32 counter holds at most its range's tuple count in magnitude, kept below 2^31.
 //
@@ -130,12 +132,16 @@ __global__ void __launch_bounds__(256, (A > 0 && V8 && NARROW && POW2) ? 5 : 1) 
 // bin sum (below A 2^16 < 2^20: no carry between lanes).  For 10 <= d <= 14 the narrow
 // 16-bit records of k_key_table are used (row pairs summed as described at k_tab_items).
 // ---------------------------------------------------------------------------
+constexpr int kPartMaxCtasPerSm = 8;   // phase-1 CTAs of 256 threads per SM, at most
+
 struct PartArgs {
-  uint16_t* items;               // tile t, row j: [(t d + j) 32 + slot]
-  uint16_t* cnts;                // tile t, row j: [t d + j] = count of part 0 | count of part 1 << 8
+  uint16_t* items;               // phase-1 warp w, row j: region items + (w d + j) C
+  uint32_t* cnts;                // phase-1 warp w: [16 w + j] part-0 items of row j, [16 w + 15] valid tuples
   const int64_t* col[5];         // column u of the window's first tuple
   int64_t W;                     // window capacity, a multiple of 256
   int64_t cnt;                   // tuples in the window, <= W
+  int64_t C;                     // item slots per (warp, row) region: 32 x tiles per warp
+  int nwarps;                    // warps of the phase-1 grid
   int logL;                      // part width 2^L
 };
 
@@ -250,9 +256,10 @@ __device__ __forceinline__ void ld_record24(const uint64_t* tbl, uint64_t k, uin
 // Persistent: each thread walks the window with the grid's stride, loading the keys of its
 // next tuple before it gathers the records of the current one, so the key stream's latency
 // overlaps the gathers.  Lanes of a warp take consecutive tuples (one tile) and iterate
-// together (the ballots need the whole warp).
+// together (the ballots need the whole warp).  Four CTAs per SM (64 registers): with the
+// running counts five (48 registers) spilled and took the star's F update from 3.10 to 3.84 ms.
 template <int A, int FMT>
-__global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
+__global__ void __launch_bounds__(256, 4) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   const int64_t gend = (q.cnt + 31) & ~(int64_t)31;
   const uint32_t mask = (uint32_t)p.m - 1u;
@@ -263,6 +270,10 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
   const uint64_t pol = policy_evict_first();
   const uint4* tbl = (const uint4*)t.tbl;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t rb = (uint32_t)(g >> 5) * (uint32_t)d;     // this warp's row-0 region index
+  const uint32_t C = (uint32_t)q.C;
+  // counts so far: lane j < d holds row j's part-0 items, lane 15 the valid tuples
+  uint32_t cw = 0;
   // keys of the thread's next tuple, checked against their domains as they arrive: the
   // in-domain keys (< 2^31) as 32-bit values, bit u of okm set when key u is in its domain
   uint32_t kx[A], okm = 0;
@@ -276,9 +287,9 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
   for (; g < gend; g += step) {
     const bool in = g < q.cnt;
     const bool ok = in && okm == (1u << A) - 1u;
-    uint64_t kg[A];   // global record indices
+    uint32_t kg[A];   // global record indices (the host keeps this path's tables below 2^32 records)
 #pragma unroll
-    for (int u = 0; u < A; u++) kg[u] = (uint64_t)t.base[u] + kx[u];
+    for (int u = 0; u < A; u++) kg[u] = (uint32_t)t.base[u] + kx[u];
     if (in && !ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);   // left out of the tile below
     const int64_t gn = g + step;
     okm = 0;
@@ -291,19 +302,23 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
     }
     const uint32_t vb = __ballot_sync(0xffffffffu, ok);
     const uint32_t nv = __popc(vb), rv = __popc(vb & lt);   // valid tuples in the tile / before this lane
-    uint16_t* ip = q.items + ((g >> 5) * d << 5);   // this tile's row 0
-    uint16_t* cp = q.cnts + (g >> 5) * d;
-    // one row: compact the tile's valid tuples by part (part 0 first); with r1 the part-1
-    // tuples before this lane, a part-1 tuple goes to c0 + r1 and a part-0 one to rv - r1.
-    // Lane j keeps row j's count word; the tile's d count words go out in one store below.
-    uint32_t cword = 0;
+    const uint32_t nval = __shfl_sync(0xffffffffu, cw, 15);  // valid tuples before the tile
+    uint32_t add = nv;   // this tile's part-0 items of row `lane` (lane < d), its valid tuples (lane 15)
+    // one row: with r1 the part-1 tuples before this lane, a part-0 tuple goes to slot
+    // (part-0 items so far) + rv - r1 and a part-1 one to C - 1 - (part-1 items so far) - r1
     auto put = [&](int j, uint32_t bin, uint32_t neg) {
       const bool hi = (bin >> q.logL) != 0;
       const uint32_t hb = __ballot_sync(0xffffffffu, ok && hi);
-      const uint32_t n1 = __popc(hb), c0 = nv - n1, r1 = __popc(hb & lt);
-      const uint32_t pos = hi ? c0 + r1 : rv - r1;
-      if (ok) st_u16_hint(ip + 32 * j + pos, (uint16_t)((bin & low) | (neg << 15)), pol);
-      if (lane == (unsigned)j) cword = c0 | (n1 << 8);
+      const uint32_t n1 = __popc(hb), r1 = __popc(hb & lt);
+      const uint32_t c0 = __shfl_sync(0xffffffffu, cw, j);
+      const uint32_t pos = hi ? C - 1u - (nval - c0) - r1 : c0 + rv - r1;
+      // slot (rb + j) C + pos, formed here rather than kept as d row pointers across the
+      // loop (registers)
+      uint64_t slot;
+      asm volatile("{\n\t.reg .u32 r;\n\tadd.u32 r, %1, %2;\n\tmad.wide.u32 %0, r, %3, %4;\n\t}"
+                   : "=l"(slot) : "r"(rb), "r"((uint32_t)j), "r"(C), "l"((uint64_t)pos));
+      if (ok) st_u16_hint(q.items + slot, (uint16_t)((bin & low) | (neg << 15)), pol);
+      if (lane == (unsigned)j) add = nv - n1;
     };
     uint32_t sg = 0;
     if (FMT == 0) {
@@ -312,7 +327,7 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
 #pragma unroll
         for (int u = 0; u < A; u++) {
           uint32_t w[8];
-          ld_record32(tbl + kg[u] * 2, w);
+          ld_record32(tbl + (uint64_t)kg[u] * 2, w);
           acc0 += ((uint64_t)w[1] << 32) | w[0];
           acc1 += ((uint64_t)w[3] << 32) | w[2];
           acc2 += ((uint64_t)w[5] << 32) | w[4];
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
 #pragma unroll
         for (int u = 0; u < A; u++) {
           uint32_t w[8];
-          ld_record32(tbl + kg[u] * 2, w);
+          ld_record32(tbl + (uint64_t)kg[u] * 2, w);
           sg ^= w[7];
 #pragma unroll
           for (int j = 0; j < 7; j++) {
@@ -368,8 +383,11 @@ __global__ void __launch_bounds__(256, FMT == 1 ? 4 : 5) k_tab_items(UpdArgs p, 
         put(j, sum & mask, (sg >> j) & 1u);
       }
     }
-    if (lane < (unsigned)d) st_u16_hint(cp + lane, (uint16_t)cword, pol);
+    cw += add;   // after the rows: their shuffles all read the counts before the tile
   }
+  // the warp's counts: lane j < d row j's part-0 items, lane 15 the valid tuples
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (lane < (unsigned)d || lane == 15u) q.cnts[wg * 16 + lane] = cw;
 }
 
 // shared counter at saddr += v when x < n (unsigned): one compare, one predicated reduction
@@ -378,13 +396,12 @@ __device__ __forceinline__ void red_shared_if_lt(uint32_t saddr, int v, uint32_t
                ::"r"(saddr), "r"(v), "r"(x), "r"(n) : "memory");
 }
 
-// blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row`, tile range c of nrange
-// (ranges of seg tuples, a multiple of 256, taken with stride nrange * seg).  A thread takes
-// 8 slots of one tile row (one 16-byte load and the tile row's count word) per unit; with
-// 1024 threads, unit u + 1024 is 256 tiles further at the same slot offset, so the thread's
-// pointers advance by a constant stride.  Two units per iteration, loads first.
+// blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row` over the regions of the
+// phase-1 warps [c R, min(c R + R, nwarps)), each region's part-h chunks (8 items, one 16-byte
+// load) split into 2^logP pieces.  Warp k of the CTA takes pieces k, k + 32, ...; lane l of a
+// warp takes the piece's chunks l, l + 32, ..., two per iteration, loads first.
 __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long long* ctr, int64_t m, int d,
-                                                     int logL, int64_t seg, int nrange) {
+                                                     int logL, int R, int logP) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* cnt = (int*)smem_raw;
   const int S = (int)(m >> logL);
@@ -396,15 +413,13 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
   for (int k = threadIdx.x; k < L; k += blockDim.x) cnt[k] = 0;
   __syncthreads();
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(cnt);
-  const uint32_t off = (threadIdx.x & 3u) << 3;        // this thread's slots of a tile row: [off, off + 8)
-  const int64_t tstep = blockDim.x >> 2;                 // tiles between a thread's consecutive units
-  const int64_t istride = tstep * ((int64_t)d << 5);     // the same in items
-  const int64_t cstride = tstep * d;                     // and in count words
-  // slots [off, off + 8) of one tile row: add the signs of part h's items
-  auto unit = [&](uint4 v, uint32_t cw) {
-    const uint32_t lo = h ? (cw & 0xffu) : 0u;
-    const uint32_t n = h ? (cw >> 8) : (cw & 0xffu);
-    const uint32_t b = off - lo;                         // slot off + k is in part h when b + k < n
+  const uint32_t lane = threadIdx.x & 31u;
+  const int w0 = c * R;
+  const int w1 = min(w0 + R, q.nwarps);
+  const int npc = (w1 - w0) << logP;
+  const uint32_t C = (uint32_t)q.C;
+  // slots b .. b + 7 counted from the part's first item: add the signs of those below n
+  auto unit = [&](uint4 v, uint32_t b, uint32_t n) {
     const uint32_t e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -414,19 +429,23 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
       red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k, n);
     }
   };
-  for (int64_t a = (int64_t)c * seg; a < q.cnt; a += (int64_t)nrange * seg) {
-    const int64_t te = (a + seg < q.cnt ? a + seg : q.cnt) + 31 >> 5;   // tiles [a / 32, te)
-    int64_t t = (a >> 5) + (threadIdx.x >> 2);
-    const uint16_t* ip = q.items + (t * d + row) * 32 + off;
-    const uint16_t* cp = q.cnts + t * d + row;
-    for (; t + tstep < te; t += 2 * tstep, ip += 2 * istride, cp += 2 * cstride) {
-      const uint4 v1 = *(const uint4*)ip;
-      const uint4 v2 = *(const uint4*)(ip + istride);
-      const uint32_t c1 = __ldg(cp), c2 = __ldg(cp + cstride);
-      unit(v1, c1);
-      unit(v2, c2);
+  for (int pc = (int)(threadIdx.x >> 5); pc < npc; pc += (int)(blockDim.x >> 5)) {
+    const int w = w0 + (pc >> logP);
+    const uint32_t piece = (uint32_t)pc & ((1u << logP) - 1u);
+    const uint32_t n0 = q.cnts[(int64_t)w * 16 + row], nv = q.cnts[(int64_t)w * 16 + 15];
+    const uint32_t n = h ? nv - n0 : n0;         // part h's items in this region
+    const uint32_t lo = h ? C - n : 0u;          // and the first of them
+    const uint32_t kb = lo >> 3, nk = ((lo + n + 7) >> 3) - kb;
+    const uint32_t ke = kb + (uint32_t)(((uint64_t)nk * (piece + 1)) >> logP);
+    uint32_t k = kb + (uint32_t)(((uint64_t)nk * piece) >> logP) + lane;
+    const uint16_t* rg = q.items + ((int64_t)w * d + row) * q.C;
+    for (; k + 32 < ke; k += 64) {
+      const uint4 v1 = *(const uint4*)(rg + 8 * k);
+      const uint4 v2 = *(const uint4*)(rg + 8 * (k + 32));
+      unit(v1, 8 * k - lo, n);
+      unit(v2, 8 * (k + 32) - lo, n);
     }
-    if (t < te) unit(*(const uint4*)ip, __ldg(cp));
+    if (k < ke) unit(*(const uint4*)(rg + 8 * k), 8 * k - lo, n);
   }
   __syncthreads();
   unsigned long long* out = ctr + (int64_t)row * m + ((int64_t)h << logL);
@@ -436,30 +455,39 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
   }
 }
 
-// Persistent grid: as many CTAs as fit on the GPU (at most one tuple per thread).
+// CTAs of k_tab_items<A, FMT> per SM (no shared memory: the whole unified array is left to
+// L1, which caches the hot records).
 template <int A, int FMT>
-cudaError_t launch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int sms, cudaStream_t st) {
+cudaError_t tab_items_per_sm(int* per_sm) {
   auto kern = k_tab_items<A, FMT>;
-  // no shared memory: leave the whole unified array to L1, which caches the hot records
   cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  int per_sm = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
-  if (e != cudaSuccess) return e;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((q.cnt + 255) / 256, (int64_t)sms * std::max(1, per_sm)));
-  kern<<<grid, 256, 0, st>>>(a, t, q);
-  count_launch();
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, 256, 0);
+  *per_sm = std::max(1, std::min(*per_sm, kPartMaxCtasPerSm));
+  return e;
 }
 
 template <int FMT>
-cudaError_t dispatch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int sms, cudaStream_t st) {
-  switch (a.a) {
-    case 1: return launch_tab_items<1, FMT>(a, t, q, sms, st);
-    case 2: return launch_tab_items<2, FMT>(a, t, q, sms, st);
-    case 3: return launch_tab_items<3, FMT>(a, t, q, sms, st);
-    case 4: return launch_tab_items<4, FMT>(a, t, q, sms, st);
-    default: return launch_tab_items<5, FMT>(a, t, q, sms, st);
+cudaError_t tab_items_occupancy(int A, int* per_sm) {
+  switch (A) {
+    case 1: return tab_items_per_sm<1, FMT>(per_sm);
+    case 2: return tab_items_per_sm<2, FMT>(per_sm);
+    case 3: return tab_items_per_sm<3, FMT>(per_sm);
+    case 4: return tab_items_per_sm<4, FMT>(per_sm);
+    default: return tab_items_per_sm<5, FMT>(per_sm);
   }
+}
+
+template <int FMT>
+cudaError_t dispatch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArgs& q, int grid, cudaStream_t st) {
+  switch (a.a) {
+    case 1: k_tab_items<1, FMT><<<grid, 256, 0, st>>>(a, t, q); break;
+    case 2: k_tab_items<2, FMT><<<grid, 256, 0, st>>>(a, t, q); break;
+    case 3: k_tab_items<3, FMT><<<grid, 256, 0, st>>>(a, t, q); break;
+    case 4: k_tab_items<4, FMT><<<grid, 256, 0, st>>>(a, t, q); break;
+    default: k_tab_items<5, FMT><<<grid, 256, 0, st>>>(a, t, q); break;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 // SK_PART_UPDATE=0 keeps the single-phase k_update_tab for batches the partitioned update
@@ -483,17 +511,30 @@ int64_t part_window(int64_t n) {
   return std::min<int64_t>((n + 255) / 256 * 256, (cap + 255) / 256 * 256);
 }
 
-size_t part_staging_bytes(int d, int64_t W) {
-  return (size_t)d * W * sizeof(uint16_t) + (size_t)d * (W / 32) * sizeof(uint16_t);
+// Regions of a window of W tuples: the phase-1 grid has at most sms x kPartMaxCtasPerSm CTAs
+// of 256 threads, so its warps' regions hold at most W + that many threads' tiles per row.
+size_t part_items_bytes(int d, int64_t W, int sms) {
+  const int64_t threads = (int64_t)sms * kPartMaxCtasPerSm * 256;
+  return ((size_t)d * (size_t)(W + threads) * sizeof(uint16_t) + 255) & ~(size_t)255;
+}
+
+size_t part_staging_bytes(int d, int64_t W, int sms) {
+  return part_items_bytes(d, W, sms) + (size_t)sms * kPartMaxCtasPerSm * 8 * 16 * sizeof(uint32_t);
 }
 
 // Both phases over every window of the batch; staging (part_staging_bytes) is caller-owned.
 cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* staging, int sms, cudaStream_t st) {
   const int64_t n = a.n;
+  int tab_per_sm = 1;
+  cudaError_t e = fmt == 0   ? tab_items_occupancy<0>(a.a, &tab_per_sm)
+                  : fmt == 2 ? tab_items_occupancy<2>(a.a, &tab_per_sm)
+                             : tab_items_occupancy<1>(a.a, &tab_per_sm);
+  if (e != cudaSuccess) return e;
+  const int64_t full_grid = (int64_t)sms * tab_per_sm;
   const int64_t W = part_window(n);
   PartArgs q;
   q.items = (uint16_t*)staging;
-  q.cnts = (uint16_t*)((char*)staging + (size_t)a.d * W * sizeof(uint16_t));
+  q.cnts = (uint32_t*)((char*)staging + part_items_bytes(a.d, W, sms));
   q.W = W;
   int logm = 0;
   while (((int64_t)1 << logm) < (int64_t)a.m) logm++;
@@ -501,7 +542,7 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
   q.logL = logL;
   const int S = (int)(a.m >> logL);
   const size_t smem = (size_t)4 << logL;
-  cudaError_t e = allow_dynamic_smem((const void*)k_part_accum);
+  e = allow_dynamic_smem((const void*)k_part_accum);
   int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part_accum, 1024, smem);
   const int64_t slots = (int64_t)sms * std::max(1, per_sm);
@@ -509,19 +550,32 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
   for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
     q.cnt = std::min(W, n - i0);
     for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
-    e = fmt == 0   ? dispatch_tab_items<0>(a, t, q, sms, st)
-        : fmt == 2 ? dispatch_tab_items<2>(a, t, q, sms, st)
-                   : dispatch_tab_items<1>(a, t, q, sms, st);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((q.cnt + 255) / 256, full_grid));
+    const int64_t gend = (q.cnt + 31) / 32 * 32;
+    q.C = 32 * ((gend + (int64_t)grid * 256 - 1) / ((int64_t)grid * 256));
+    q.nwarps = grid * 8;
+    e = fmt == 0   ? dispatch_tab_items<0>(a, t, q, grid, st)
+        : fmt == 2 ? dispatch_tab_items<2>(a, t, q, grid, st)
+                   : dispatch_tab_items<1>(a, t, q, grid, st);
     if (e != cudaSuccess) break;
-    // ranges per (row, part): the grid a whole number of waves when that takes 2..64 waves
+    // ranges of phase-1 warps per (row, part): the grid a whole number of waves when that
+    // takes 2..64 waves; pieces per region so that a CTA's 32 warps get equal shares
     int64_t nr = 0;
     for (int64_t k = 2; k <= 64 && !nr; k++)
       if ((k * slots) % units == 0) nr = k * slots / units;
     if (!nr) nr = (4 * slots + units - 1) / units;
-    nr = std::max<int64_t>(1, std::min<int64_t>(nr, (q.cnt + 255) / 256));
-    const int64_t seg = ((q.cnt + nr - 1) / nr + 255) / 256 * 256;
-    nr = (q.cnt + seg - 1) / seg;
-    k_part_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, logL, seg, (int)nr);
+    nr = std::max<int64_t>(1, std::min<int64_t>(nr, q.nwarps));
+    const int R = (int)((q.nwarps + nr - 1) / nr);
+    nr = (q.nwarps + R - 1) / R;
+    int logP = 3;
+    for (int lp = 0; lp < 3; lp++) {
+      const int64_t pcs = (int64_t)R << lp;
+      if ((pcs + 31) / 32 * 32 * 100 <= pcs * 105) {
+        logP = lp;
+        break;
+      }
+    }
+    k_part_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, logL, R, logP);
     count_launch();
     e = cudaGetLastError();
   }
@@ -926,10 +980,11 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
     t.rvec = key_record_vectors(s->d, t.narrow);
     // The two-phase partitioned update (unit weights, power-of-two 1024 <= m <= 2^16, d <= 14,
     // at most 5 attributes, sketch too large for one CTA's shared memory, at least 16 tuples
-    // per counter of a row) takes 24-byte records for d <= 9 (the 32-byte 20-bit lane ones
-    // with SK_PART_RECORD=32) and the narrow 32-byte format otherwise.
+    // per counter of a row, fewer than 2^32 table records) takes 24-byte records for d <= 9
+    // (the 32-byte 20-bit lane ones with SK_PART_RECORD=32) and the narrow 32-byte format
+    // otherwise.
     bool part = part_update_mode() != 0 && pow2 && weights == nullptr && rp.a <= 5 && !use_smem && s->m >= 1024 &&
-                s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16;
+                s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16 && total < ((int64_t)1 << 32);
     const int part_fmt = s->d <= 9 ? (part_record_bytes() == 32 ? 0 : 2) : 1;
     // Automatic choice: the tables replace per-tuple hashing by gathers, which pays when
     // the domains are small against a batch of at least 2^16 tuples (below that the table's
@@ -940,7 +995,7 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
                                     (size_t)s->d * (size_t)s->m * sizeof(int64_t) <= ((size_t)32 << 20));
     void* staging = nullptr;
     if (fits && worth && total > 0 && part) {
-      e = pool_malloc_async(&staging, part_staging_bytes(s->d, part_window(n)), st);
+      e = pool_malloc_async(&staging, part_staging_bytes(s->d, part_window(n), sms), st);
       if (e != cudaSuccess) {
         cudaGetLastError();   // no room for the planes: single-phase update
         staging = nullptr;

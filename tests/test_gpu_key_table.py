@@ -210,11 +210,13 @@ def test_partitioned_update_edges(monkeypatch):
     """The two-phase update at its edges: one row (d = 1) at m = 2^16; a window whose every
     tuple has a key outside its domain (all reported and skipped: the tiles hold no items);
     window lengths that leave a ragged last tile (not a multiple of 32 or of 8); one part per
-    row (m = 4096, d = 13: the smallest sketch that does not fit one CTA's shared memory)."""
+    row (m = 4096, d = 13: the smallest sketch that does not fit one CTA's shared memory);
+    every tuple with the same keys, so that each row's items all fall in one part and every
+    warp's region of that row fills from one end to the other."""
     monkeypatch.setenv("SK_KEY_TABLE", "1")
     rng = np.random.default_rng(77)
     cases = [(2, 1, 1 << 16, (1 << 20) + 3, 0, False), (3, 9, 1 << 16, (1 << 20) + 37, 262_144 + 256, True),
-             (1, 13, 4096, 65_536 + 13, 0, False)]
+             (1, 13, 4096, 65_536 + 13, 0, False), (4, 9, 1 << 16, (1 << 20) + 29, 0, "same")]
     for a, d, m, n, window, bad_window in cases:
         if window:
             monkeypatch.setenv("SK_PART_WINDOW", str(window))
@@ -222,7 +224,9 @@ def test_partitioned_update_edges(monkeypatch):
             monkeypatch.delenv("SK_PART_WINDOW", raising=False)
         doms = [int(x) for x in rng.integers(500, 50_000, size=a)]
         cols = np.stack([synth.zipf_keys(n, 1.2, doms[u], 900 + u).numpy() for u in range(a)])
-        if bad_window:   # every tuple of the second window out of domain
+        if bad_window == "same":   # one key per attribute for every tuple
+            cols[:, :] = cols[:, :1]
+        elif bad_window:   # every tuple of the second window out of domain
             cols[0, window:2 * window] = doms[0] + 5
         attrs, edges = _star(a)
         L0 = pkg.sk_launch_count()
