@@ -155,10 +155,6 @@ __device__ __forceinline__ void st_u16_hint(uint16_t* ptr, uint16_t v, uint64_t 
   asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(pol) : "memory");
 }
 
-__device__ __forceinline__ void st_u32_hint(uint32_t* ptr, uint32_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
-}
-
 __device__ __forceinline__ int64_t ld_key_policy(const int64_t* ptr, uint64_t pol) {
   int64_t v;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
@@ -490,12 +486,14 @@ cudaError_t dispatch_tab_items(const UpdArgs& a, const TabArgs& t, const PartArg
   return cudaGetLastError();
 }
 
-// SK_PART_UPDATE=0 keeps the single-phase k_update_tab for batches the partitioned update
-// could take; SK_PART_WINDOW caps the tuples per window (default and largest: 2^30, which
-// keeps every shared-memory counter of k_part_accum below 2^31 in magnitude).
+// SK_PART_UPDATE=0 keeps the single-phase k_update_tab (and the per-tuple update) for batches
+// the partitioned updates could take; =2 gives the wide partitioned update every batch whose
+// width, rows, arity and weights it accepts, whatever the sketch's size and the batch length.
+// SK_PART_WINDOW caps the tuples per window (default and largest: 2^30, which keeps every
+// shared-memory counter of k_part_accum below 2^31 in magnitude; 2^24 for the wide update).
 int part_update_mode() {
   const char* v = std::getenv("SK_PART_UPDATE");
-  return (v && v[0] == '0') ? 0 : 1;
+  return (v && v[0] == '0') ? 0 : ((v && v[0] == '2') ? 2 : 1);
 }
 
 // SK_PART_RECORD=32 takes the 32-byte 20-bit lane records instead of the 24-byte ones for d <= 9.
@@ -577,6 +575,347 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
     }
     k_part_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, logL, R, logP);
     count_launch();
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Partitioned update for wide sketches (unit weights, power-of-two 2^17 <= m <= 2^24, d <= 16,
+// at most 5 attributes, declared domains: the chain of eight relations at m = 2^20).  A d x m
+// int64 sketch of 128 MB does not stay in L2, and one 64-bit reduction per (tuple, row) then
+// waits on DRAM.  Each row's bins are split into S = m / 2^15 parts of 2^15 bins (the int32
+// counters of one part fill 128 KB of one SM's shared memory); the items of a window are
+// sorted by part in four steps:
+//   1. k_wide_items: one CTA per chunk of kWideChunk tuples gathers the A key-table records
+//      (wide format: one 32-bit word per row, bin in bits 0..30, sign in bit 31) of each tuple,
+//      writes row j's item (bin mod m | sign << 31; 0x7fffffff for a tuple left out for a key
+//      outside its domain) to plane[j][i] and counts each row's items per part in shared
+//      memory; the counts go to H[(j S + b) nchunk + c];
+//   2. an exclusive scan of H in place (k_scan_*): H[(j S + b) nchunk + c] becomes the first
+//      position of chunk c's part-b items of row j in the sorted item array, whose row-major,
+//      part-major order the flat scan gives;
+//   3. k_wide_scatter: per (chunk, row) the chunk's items ranked within their parts in shared
+//      memory (16-bit: offset within the part | sign << 15) and written out part by part,
+//      each part's run contiguous;
+//   4. k_wide_accum: a CTA owns part b of row j as 2^15 int32 counters over a range of that
+//      part's items, adds with shared-memory atomics and adds each counter into the int64
+//      sketch with one 64-bit reduction.
+// Every counter receives the same integer sum as with one reduction per (tuple, row).
+// ---------------------------------------------------------------------------
+constexpr int kWideChunk = 2048;   // tuples per phase-1 CTA (256 threads x 8)
+constexpr int kWideMaxRows = 16;
+constexpr int kWideMaxParts = 512;  // m <= 2^24
+
+struct WideArgs {
+  uint32_t* plane;     // [d][W] 32-bit items of the window
+  uint16_t* sorted;    // [d W + 8] 16-bit items, row-major then part-major
+  uint32_t* H;         // [d][S][nchunk] per-chunk part counts
+  uint32_t* OFF;       // [d][S][nchunk] their exclusive scan: first position in `sorted`
+  uint32_t* bsum;      // scan block sums
+  int64_t W;           // window capacity
+  int64_t cnt;         // tuples in the window
+  const int64_t* col[5];
+  int nchunk;
+  int S;
+};
+
+template <int A>
+__global__ void __launch_bounds__(256) k_wide_items(UpdArgs p, TabArgs t, WideArgs q) {
+  __shared__ uint32_t hist[kWideMaxRows * kWideMaxParts];
+  const int d = p.d, S = q.S;
+  for (int k = threadIdx.x; k < d * S; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  const uint32_t mask = (uint32_t)p.m - 1u;
+  const int rv = (d + 3) >> 2;   // 16-byte vectors per record
+  const int64_t c0 = (int64_t)blockIdx.x * kWideChunk;
+  for (int k = 0; k < kWideChunk / 256; k++) {
+    const int64_t i = c0 + k * 256 + threadIdx.x;
+    if (i >= q.cnt) break;
+    bool ok = true;
+    const uint4* rec[A];
+#pragma unroll
+    for (int u = 0; u < A; u++) {
+      const int64_t key = ld_key_stream(q.col[u] + i);
+      const bool kin = (uint64_t)key < (uint64_t)p.dom[u];
+      ok = ok && kin;
+      rec[u] = (const uint4*)t.tbl + ((uint64_t)t.base[u] + (kin ? (uint64_t)key : 0ull)) * (uint64_t)t.rvec;
+    }
+    if (!ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
+    for (int v = 0; v < rv; v++) {
+      uint32_t acc[4] = {0, 0, 0, 0}, sg[4] = {0, 0, 0, 0};
+      if (ok) {
+        uint4 w[A];
+#pragma unroll
+        for (int u = 0; u < A; u++) w[u] = __ldg(rec[u] + v);
+#pragma unroll
+        for (int u = 0; u < A; u++) {
+          const uint32_t e[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            acc[h] += e[h] & 0x7fffffffu;
+            sg[h] ^= e[h] >> 31;
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 4; h++) {
+        const int j = 4 * v + h;
+        if (j >= d) break;
+        const uint32_t bin = acc[h] & mask;
+        q.plane[(int64_t)j * q.W + i] = ok ? (bin | (sg[h] << 31)) : 0x7fffffffu;
+        if (ok) atomicAdd(&hist[j * S + (int)(bin >> 15)], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < d * S; k += blockDim.x) q.H[(int64_t)k * q.nchunk + blockIdx.x] = hist[k];
+}
+
+// Exclusive scan of n uint32: k_scan_blocks scans blocks of 4096 of `in` (4 per thread) into
+// `out` and leaves each block's total in bsum; k_scan_sums scans bsum (one CTA); k_scan_add
+// adds the scanned totals to `out`.
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31u) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < (blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= (unsigned)o) s += y;
+    }
+    s_warp[lane] = s;   // inclusive warp totals
+  }
+  __syncthreads();
+  const uint32_t before = wid ? s_warp[wid - 1] : 0u;
+  *total = s_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* bsum) {
+  __shared__ uint32_t s_warp[32];
+  const int64_t base = (int64_t)blockIdx.x * 4096 + (int64_t)threadIdx.x * 4;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    v[k] = base + k < n ? in[base + k] : 0u;
+    sum += v[k];
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan_1024(sum, s_warp, &total);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* bsum, int nb) {
+  __shared__ uint32_t s_warp[32];
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    const int i = b0 + (int)threadIdx.x;
+    const uint32_t v = i < nb ? bsum[i] : 0u;
+    uint32_t total;
+    const uint32_t x = block_excl_scan_1024(v, s_warp, &total);
+    if (i < nb) bsum[i] = carry + x;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(uint32_t* a, int64_t n, const uint32_t* bsum) {
+  const int64_t base = (int64_t)blockIdx.x * 4096;
+  const uint32_t off = bsum[blockIdx.x];
+  for (int k = threadIdx.x; k < 4096; k += blockDim.x)
+    if (base + k < n) a[base + k] += off;
+}
+
+// blockIdx.x = chunk c, blockIdx.y = row j.  Chunk c's items of row j ranked within their
+// parts (a shared-memory counter per part), staged in part order, then written part by part.
+__global__ void __launch_bounds__(256) k_wide_scatter(WideArgs q, int64_t m) {
+  __shared__ uint32_t lstart[kWideMaxParts], rank[kWideMaxParts], gpos[kWideMaxParts];
+  __shared__ uint16_t s_item[kWideChunk], s_part[kWideChunk];
+  __shared__ uint32_t s_warp[32];
+  const int c = blockIdx.x, j = blockIdx.y, S = q.S;
+  // this chunk's part counts (S <= 512: two per thread), their exclusive scan
+  uint32_t n2[2] = {0u, 0u};
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int b = 2 * (int)threadIdx.x + h;
+    if (b < S) {
+      const int64_t k = ((int64_t)j * S + b) * q.nchunk + c;
+      n2[h] = q.H[k];
+      gpos[b] = q.OFF[k];
+    }
+  }
+  uint32_t total;
+  const uint32_t ex = block_excl_scan_1024(n2[0] + n2[1], s_warp, &total);
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int b = 2 * (int)threadIdx.x + h;
+    if (b < S) {
+      lstart[b] = ex + (h ? n2[0] : 0u);
+      rank[b] = 0u;
+    }
+  }
+  __syncthreads();
+  const int64_t i0 = (int64_t)c * kWideChunk;
+  const uint32_t low = (1u << 15) - 1u;
+  for (int k = threadIdx.x; k < kWideChunk; k += blockDim.x) {
+    const int64_t i = i0 + k;
+    if (i >= q.cnt) break;
+    const uint32_t it = q.plane[(int64_t)j * q.W + i];
+    const uint32_t bin = it & 0x7fffffffu;
+    if (bin < (uint32_t)m) {
+      const uint32_t b = bin >> 15;
+      const uint32_t lp = lstart[b] + atomicAdd(&rank[b], 1u);
+      s_item[lp] = (uint16_t)((bin & low) | ((it >> 31) << 15));
+      s_part[lp] = (uint16_t)b;
+    }
+  }
+  __syncthreads();
+  for (uint32_t lp = threadIdx.x; lp < total; lp += blockDim.x) {
+    const uint32_t b = s_part[lp];
+    q.sorted[gpos[b] + (lp - lstart[b])] = s_item[lp];
+  }
+}
+
+// blockIdx.x = b + S (j + d r): part b of row j over range r of nr of that part's items
+// (contiguous in `sorted`: [OFF of (j, b, chunk 0), OFF of (j, b + 1, chunk 0)), the last
+// part's end being the total).  Lanes take consecutive 8-item chunks, two per iteration.
+__global__ void __launch_bounds__(1024) k_wide_accum(WideArgs q, unsigned long long* ctr, int64_t m, int d, int nr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* cnt = (int*)smem_raw;
+  const int S = q.S;
+  const int b = (int)(blockIdx.x % (unsigned)S);
+  const int rest = (int)(blockIdx.x / (unsigned)S);
+  const int j = rest % d;
+  const int r = rest / d;
+  constexpr int L = 1 << 15;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  const int64_t kp = ((int64_t)j * S + b) * q.nchunk;
+  const int64_t last = (int64_t)d * S * q.nchunk - 1;
+  const uint32_t P0 = q.OFF[kp];
+  const uint32_t P1 = (j * S + b + 1 < d * S) ? q.OFF[kp + q.nchunk] : q.OFF[last] + q.H[last];
+  const uint32_t lo = P0 + (uint32_t)(((uint64_t)(P1 - P0) * r) / nr);
+  const uint32_t hi = P0 + (uint32_t)(((uint64_t)(P1 - P0) * (r + 1)) / nr);
+  const uint32_t n = hi - lo;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(cnt);
+  auto unit = [&](uint4 v, uint32_t bo) {   // slots bo .. bo + 7 counted from lo: add those below n
+    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
+      int neg;   // 0 or -1 from the item's sign bit
+      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
+      red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, bo + (uint32_t)k, n);
+    }
+  };
+  const uint32_t ke = (hi + 7) >> 3;
+  uint32_t k = (lo >> 3) + threadIdx.x;
+  for (; k + blockDim.x < ke; k += 2 * blockDim.x) {
+    const uint4 v1 = *(const uint4*)(q.sorted + 8 * (size_t)k);
+    const uint4 v2 = *(const uint4*)(q.sorted + 8 * (size_t)(k + blockDim.x));
+    unit(v1, 8 * k - lo);
+    unit(v2, 8 * (k + blockDim.x) - lo);
+  }
+  if (k < ke) unit(*(const uint4*)(q.sorted + 8 * (size_t)k), 8 * k - lo);
+  __syncthreads();
+  unsigned long long* out = ctr + (int64_t)j * m + ((int64_t)b << 15);
+  for (int x = threadIdx.x; x < L; x += blockDim.x) {
+    const int v = cnt[x];
+    if (v != 0) red_add_global(out + x, (unsigned long long)(int64_t)v);
+  }
+}
+
+// Window capacity of the wide partitioned update: positions in `sorted` stay below 2^28.
+int64_t wide_window(int64_t n) {
+  const char* v = std::getenv("SK_PART_WINDOW");
+  const long long x = v ? std::atoll(v) : 0;
+  const int64_t cap = (x > 0 && x < (1ll << 24)) ? (int64_t)x : ((int64_t)1 << 24);
+  return std::min<int64_t>((n + 255) / 256 * 256, (cap + 255) / 256 * 256);
+}
+
+struct WideLayout {
+  size_t plane, sorted, H, OFF, bsum, total;
+};
+
+WideLayout wide_layout(int d, int64_t m, int64_t W) {
+  const int S = (int)(m >> 15);
+  const int64_t nchunk = (W + kWideChunk - 1) / kWideChunk;
+  const int64_t N = (int64_t)d * S * nchunk;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  WideLayout L;
+  L.plane = 0;
+  L.sorted = L.plane + al((size_t)d * W * sizeof(uint32_t));
+  L.H = L.sorted + al(((size_t)d * W + 8) * sizeof(uint16_t));
+  L.OFF = L.H + al((size_t)N * sizeof(uint32_t));
+  L.bsum = L.OFF + al((size_t)N * sizeof(uint32_t));
+  L.total = L.bsum + al((size_t)((N + 4095) / 4096) * sizeof(uint32_t));
+  return L;
+}
+
+template <int A>
+void launch_wide_items(const UpdArgs& a, const TabArgs& t, const WideArgs& q, cudaStream_t st) {
+  k_wide_items<A><<<q.nchunk, 256, 0, st>>>(a, t, q);
+}
+
+// All four steps over every window of the batch; staging (wide_layout(...).total bytes for
+// the window wide_window(n)) is caller-owned.
+cudaError_t run_wide_partitioned(const UpdArgs& a, const TabArgs& t, void* staging, int sms, cudaStream_t st) {
+  const int64_t n = a.n;
+  const int64_t W = wide_window(n);
+  const WideLayout Ly = wide_layout(a.d, (int64_t)a.m, W);
+  char* base = (char*)staging;
+  WideArgs q;
+  q.plane = (uint32_t*)(base + Ly.plane);
+  q.sorted = (uint16_t*)(base + Ly.sorted);
+  q.H = (uint32_t*)(base + Ly.H);
+  q.OFF = (uint32_t*)(base + Ly.OFF);
+  q.bsum = (uint32_t*)(base + Ly.bsum);
+  q.W = W;
+  q.S = (int)(a.m >> 15);
+  const size_t smem = (size_t)4 << 15;
+  cudaError_t e = allow_dynamic_smem((const void*)k_wide_accum);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wide_accum, 1024, smem);
+  const int64_t slots = (int64_t)sms * std::max(1, per_sm);
+  const int64_t units = (int64_t)q.S * a.d;
+  for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
+    q.cnt = std::min(W, n - i0);
+    for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
+    q.nchunk = (int)((q.cnt + kWideChunk - 1) / kWideChunk);
+    switch (a.a) {
+      case 1: launch_wide_items<1>(a, t, q, st); break;
+      case 2: launch_wide_items<2>(a, t, q, st); break;
+      case 3: launch_wide_items<3>(a, t, q, st); break;
+      case 4: launch_wide_items<4>(a, t, q, st); break;
+      default: launch_wide_items<5>(a, t, q, st); break;
+    }
+    const int64_t N = units * q.nchunk;
+    const int nb = (int)((N + 4095) / 4096);
+    k_scan_blocks<<<nb, 1024, 0, st>>>(q.H, q.OFF, N, q.bsum);
+    k_scan_sums<<<1, 1024, 0, st>>>(q.bsum, nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(q.OFF, N, q.bsum);
+    k_wide_scatter<<<dim3((unsigned)q.nchunk, (unsigned)a.d), 256, 0, st>>>(q, (int64_t)a.m);
+    // ranges per (row, part): the grid a whole number of waves when that takes 1..16 waves
+    int64_t nr = 0;
+    for (int64_t k = 1; k <= 16 && !nr; k++)
+      if ((k * slots) % units == 0) nr = k * slots / units;
+    if (!nr) nr = std::max<int64_t>(1, (2 * slots + units - 1) / units);
+    k_wide_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, (int)nr);
+    count_launch(6);
     e = cudaGetLastError();
   }
   return e;
@@ -986,13 +1325,22 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
     bool part = part_update_mode() != 0 && pow2 && weights == nullptr && rp.a <= 5 && !use_smem && s->m >= 1024 &&
                 s->m <= 65536 && s->d <= 14 && n >= (int64_t)s->m * 16 && total < ((int64_t)1 << 32);
     const int part_fmt = s->d <= 9 ? (part_record_bytes() == 32 ? 0 : 2) : 1;
+    // The wide partitioned update (unit weights, power-of-two 2^17 <= m <= 2^24, d <= 16, at most
+    // 5 attributes, at least m tuples, a sketch larger than 32 MiB, whose counter updates would
+    // leave L2) takes the wide records (one 32-bit word per row).
+    const size_t sketch_bytes = (size_t)s->d * (size_t)s->m * sizeof(int64_t);
+    const int pum = part_update_mode();
+    bool wide = pum != 0 && pow2 && weights == nullptr && rp.a <= 5 && s->m >= ((int64_t)1 << 17) &&
+                s->m <= ((int64_t)1 << 24) && s->d <= kWideMaxRows && total < ((int64_t)1 << 32) &&
+                (pum == 2 || (n >= (int64_t)s->m && sketch_bytes > ((size_t)32 << 20)));
     // Automatic choice: the tables replace per-tuple hashing by gathers, which pays when
     // the domains are small against a batch of at least 2^16 tuples (below that the table's
     // launch and allocation cost more than the hashing) and the counter updates hit L2 (for a sketch
     // much larger than L2 the update is bound by its atomics either way and the gathers
-    // only add traffic: 27.7 vs 24.7 ms for 8 x 1e7 rows into 128 MB sketches).
+    // only add traffic: 27.7 vs 24.7 ms for 8 x 1e7 rows into 128 MB sketches), unless the
+    // wide partitioned update takes the batch: it replaces those atomics.
     const bool worth = ktm == 1 || (n >= ((int64_t)1 << 16) && total * 4 <= n * (int64_t)rp.a &&
-                                    (size_t)s->d * (size_t)s->m * sizeof(int64_t) <= ((size_t)32 << 20));
+                                    (sketch_bytes <= ((size_t)32 << 20) || wide));
     void* staging = nullptr;
     if (fits && worth && total > 0 && part) {
       e = pool_malloc_async(&staging, part_staging_bytes(s->d, part_window(n), sms), st);
@@ -1001,6 +1349,15 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
         staging = nullptr;
         part = false;
       }
+    } else if (fits && worth && total > 0 && wide) {
+      e = pool_malloc_async(&staging, wide_layout(s->d, s->m, wide_window(n)).total, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();   // no room for the planes: per-tuple update
+        staging = nullptr;
+        wide = false;
+      }
+    } else {
+      wide = false;
     }
     if (part) t.rvec = 2;
     const size_t bytes = (size_t)total * (part && part_fmt == 2 ? 24 : (size_t)t.rvec * 16);
@@ -1028,6 +1385,8 @@ sk_status launch_update(sk_set* s, int relation, int64_t n, const int64_t* cols,
         }
         if (e == cudaSuccess && part) {
           e = run_partitioned(a, t, part_fmt, staging, sms, st);
+        } else if (e == cudaSuccess && wide) {
+          e = run_wide_partitioned(a, t, staging, sms, st);
         } else if (e == cudaSuccess) {
           if (use_smem) {
             const int per_sm = sub_bytes <= 48 * 1024 ? 4 : (sub_bytes <= 100 * 1024 ? 2 : 1);

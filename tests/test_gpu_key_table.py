@@ -266,3 +266,53 @@ def test_partitioned_update_heavy_bins(m, d, monkeypatch):
     ref = O.sketch_relation(q, co, 0, cols, None, m, threads=16)
     assert np.abs(ref).max() > 1_000_000
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("a,d,m,n,window,force,same", [
+    (2, 16, 1 << 20, 1_200_007, 0, False, False),      # the chain's inner relations: 2 attributes, d = 16
+    (1, 9, 1 << 19, 600_001, 0, False, False),
+    (2, 16, 1 << 20, 1_100_000, 300_000, False, False),  # several windows, ragged last one
+    (3, 5, 1 << 17, 300_007, 0, True, False),
+    (5, 13, 1 << 18, 200_003, 65_536, True, False),
+    (1, 1, 1 << 24, 100_001, 0, True, False),          # 512 parts per row
+    (2, 16, 1 << 20, 1_048_583, 0, False, True),       # every tuple the same keys: one part per row
+    (4, 10, 1 << 21, 50_000, 0, True, False),          # d not a multiple of the record vector
+])
+def test_wide_partitioned_update_bit_exact(a, d, m, n, window, force, same, monkeypatch):
+    """Unit-weight batches with declared domains into sketches wider than 2^16 bins (the
+    chain of eight relations at m = 2^20, d = 16) take the wide partitioned update: items
+    with per-chunk part counts, a scan, a scatter by part of 2^15 bins, shared-memory
+    accumulation per (row, part).  By default only for sketches larger than 32 MiB with at
+    least m tuples; SK_PART_UPDATE=2 forces it for the smaller cases.  Keys at the table's
+    first and last records and outside the domain (skipped and reported); one window or
+    several; all tuples alike (every row's items in one part).  The launch count shows which
+    path ran: the table build plus six launches per window."""
+    monkeypatch.setenv("SK_KEY_TABLE", "1")
+    if force:
+        monkeypatch.setenv("SK_PART_UPDATE", "2")
+    else:
+        monkeypatch.delenv("SK_PART_UPDATE", raising=False)
+    if window:
+        monkeypatch.setenv("SK_PART_WINDOW", str(window))
+    else:
+        monkeypatch.delenv("SK_PART_WINDOW", raising=False)
+    rng = np.random.default_rng(a * 131 + d + m % 977)
+    doms = [int(x) for x in rng.integers(1000, 300_000, size=a)]
+    cols = np.stack([synth.zipf_keys(n, 1.2, doms[u], 500 + u).numpy() for u in range(a)])
+    if same:
+        cols[:, :] = cols[:, :1]
+    else:
+        cols[0, :5] = [0, doms[0] - 1, -1, doms[0], 3]
+        cols[a - 1, n - 3:] = [doms[a - 1], 0, doms[a - 1] - 1]
+    attrs, edges = _star(a)
+    L0 = pkg.sk_launch_count()
+    got = _run(attrs, edges, m, d, 777 + a, cols, None, doms)
+    launches = pkg.sk_launch_count() - L0
+    per = window if window else n
+    per = (per + 255) // 256 * 256
+    assert launches == 1 + 6 * ((n + per - 1) // per), launches
+    keep = np.all((cols >= 0) & (cols < np.array(doms)[:, None]), axis=0)
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(777 + a, d, q.n_comp, len(q.edges))
+    ref = O.sketch_relation(q, co, 0, cols[:, keep], None, m, threads=16)
+    assert np.array_equal(got, ref)
