@@ -592,13 +592,14 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
 //      writes row j's item (bin mod m | sign << 31; 0x7fffffff for a tuple left out for a key
 //      outside its domain) to plane[j][i] and counts each row's items per part in shared
 //      memory; the counts go to H[(j S + b) nchunk + c];
-//   2. an exclusive scan of H in place (k_scan_*): H[(j S + b) nchunk + c] becomes the first
+//   2. an exclusive scan of H (k_scan_*) into OFF: OFF[(j S + b) nchunk + c] is the first
 //      position of chunk c's part-b items of row j in the sorted item array, whose row-major,
 //      part-major order the flat scan gives;
 //   3. k_wide_scatter: per (chunk, row) the chunk's items ranked within their parts in shared
 //      memory (16-bit: offset within the part | sign << 15) and written out part by part,
 //      each part's run contiguous;
-//   4. k_wide_accum: a CTA owns part b of row j as 2^15 int32 counters over a range of that
+//   4. k_wide_plan lists the phase-2 CTAs (heavy parts split over several), and in
+//      k_wide_accum a CTA owns part b of row j as 2^15 int32 counters over a range of that
 //      part's items, adds with shared-memory atomics and adds each counter into the int64
 //      sketch with one 64-bit reduction.
 // Every counter receives the same integer sum as with one reduction per (tuple, row).
@@ -613,6 +614,8 @@ struct WideArgs {
   uint32_t* H;         // [d][S][nchunk] per-chunk part counts
   uint32_t* OFF;       // [d][S][nchunk] their exclusive scan: first position in `sorted`
   uint32_t* bsum;      // scan block sums
+  uint4* plan;         // phase-2 work: per CTA (row j * S + part b, first item, end, heavy); plan_n[0] CTAs
+  uint32_t* plan_n;
   int64_t W;           // window capacity
   int64_t cnt;         // tuples in the window
   const int64_t* col[5];
@@ -620,51 +623,65 @@ struct WideArgs {
   int S;
 };
 
+// Per tuple the A records' vectors are all loaded before any is summed (up to 4 x A vectors
+// in flight; A <= 2, the chain's relations), and the next tuple's keys are loaded before this
+// tuple's records.
 template <int A>
 __global__ void __launch_bounds__(256) k_wide_items(UpdArgs p, TabArgs t, WideArgs q) {
   __shared__ uint32_t hist[kWideMaxRows * kWideMaxParts];
+  constexpr int VH = A <= 2 ? 4 : 1;   // vectors loaded together per record
   const int d = p.d, S = q.S;
   for (int k = threadIdx.x; k < d * S; k += blockDim.x) hist[k] = 0;
   __syncthreads();
   const uint32_t mask = (uint32_t)p.m - 1u;
   const int rv = (d + 3) >> 2;   // 16-byte vectors per record
   const int64_t c0 = (int64_t)blockIdx.x * kWideChunk;
-  for (int k = 0; k < kWideChunk / 256; k++) {
-    const int64_t i = c0 + k * 256 + threadIdx.x;
-    if (i >= q.cnt) break;
+  const int64_t cend = c0 + kWideChunk < q.cnt ? c0 + kWideChunk : q.cnt;
+  int64_t i = c0 + threadIdx.x;
+  int64_t key[A];
+#pragma unroll
+  for (int u = 0; u < A; u++) key[u] = i < cend ? ld_key_stream(q.col[u] + i) : 0;
+  for (; i < cend; i += 256) {
     bool ok = true;
     const uint4* rec[A];
 #pragma unroll
     for (int u = 0; u < A; u++) {
-      const int64_t key = ld_key_stream(q.col[u] + i);
-      const bool kin = (uint64_t)key < (uint64_t)p.dom[u];
+      const bool kin = (uint64_t)key[u] < (uint64_t)p.dom[u];
       ok = ok && kin;
-      rec[u] = (const uint4*)t.tbl + ((uint64_t)t.base[u] + (kin ? (uint64_t)key : 0ull)) * (uint64_t)t.rvec;
+      rec[u] = (const uint4*)t.tbl + ((uint64_t)t.base[u] + (kin ? (uint64_t)key[u] : 0ull)) * (uint64_t)t.rvec;
     }
-    if (!ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
-    for (int v = 0; v < rv; v++) {
-      uint32_t acc[4] = {0, 0, 0, 0}, sg[4] = {0, 0, 0, 0};
-      if (ok) {
-        uint4 w[A];
+    const int64_t inext = i + 256;
 #pragma unroll
-        for (int u = 0; u < A; u++) w[u] = __ldg(rec[u] + v);
+    for (int u = 0; u < A; u++) key[u] = inext < cend ? ld_key_stream(q.col[u] + inext) : 0;
+    if (!ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
+    for (int v0 = 0; v0 < rv; v0 += VH) {
+      uint4 w[VH][A];
+#pragma unroll
+      for (int vh = 0; vh < VH; vh++)
+#pragma unroll
+        for (int u = 0; u < A; u++)
+          w[vh][u] = (ok && v0 + vh < rv) ? __ldg(rec[u] + v0 + vh) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int vh = 0; vh < VH; vh++) {
+        uint32_t acc[4] = {0, 0, 0, 0}, sg[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int u = 0; u < A; u++) {
-          const uint32_t e[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+          const uint32_t e[4] = {w[vh][u].x, w[vh][u].y, w[vh][u].z, w[vh][u].w};
 #pragma unroll
           for (int h = 0; h < 4; h++) {
             acc[h] += e[h] & 0x7fffffffu;
             sg[h] ^= e[h] >> 31;
           }
         }
-      }
 #pragma unroll
-      for (int h = 0; h < 4; h++) {
-        const int j = 4 * v + h;
-        if (j >= d) break;
-        const uint32_t bin = acc[h] & mask;
-        q.plane[(int64_t)j * q.W + i] = ok ? (bin | (sg[h] << 31)) : 0x7fffffffu;
-        if (ok) atomicAdd(&hist[j * S + (int)(bin >> 15)], 1u);
+        for (int h = 0; h < 4; h++) {
+          const int j = 4 * (v0 + vh) + h;
+          if (j < d) {
+            const uint32_t bin = acc[h] & mask;
+            q.plane[(int64_t)j * q.W + i] = ok ? (bin | (sg[h] << 31)) : 0x7fffffffu;
+            if (ok) atomicAdd(&hist[j * S + (int)(bin >> 15)], 1u);
+          }
+        }
       }
     }
   }
@@ -744,7 +761,7 @@ __global__ void __launch_bounds__(1024) k_scan_add(uint32_t* a, int64_t n, const
 // parts (a shared-memory counter per part), staged in part order, then written part by part.
 __global__ void __launch_bounds__(256) k_wide_scatter(WideArgs q, int64_t m) {
   __shared__ uint32_t lstart[kWideMaxParts], rank[kWideMaxParts], gpos[kWideMaxParts];
-  __shared__ uint16_t s_item[kWideChunk], s_part[kWideChunk];
+  __shared__ uint32_t s_pk[kWideChunk];   // item | part << 16
   __shared__ uint32_t s_warp[32];
   const int c = blockIdx.x, j = blockIdx.y, S = q.S;
   // this chunk's part counts (S <= 512: two per thread), their exclusive scan
@@ -779,37 +796,62 @@ __global__ void __launch_bounds__(256) k_wide_scatter(WideArgs q, int64_t m) {
     if (bin < (uint32_t)m) {
       const uint32_t b = bin >> 15;
       const uint32_t lp = lstart[b] + atomicAdd(&rank[b], 1u);
-      s_item[lp] = (uint16_t)((bin & low) | ((it >> 31) << 15));
-      s_part[lp] = (uint16_t)b;
+      s_pk[lp] = (bin & low) | ((it >> 31) << 15) | (b << 16);
     }
   }
   __syncthreads();
   for (uint32_t lp = threadIdx.x; lp < total; lp += blockDim.x) {
-    const uint32_t b = s_part[lp];
-    q.sorted[gpos[b] + (lp - lstart[b])] = s_item[lp];
+    const uint32_t pk = s_pk[lp], b = pk >> 16;
+    q.sorted[gpos[b] + (lp - lstart[b])] = (uint16_t)pk;
   }
 }
 
-// blockIdx.x = b + S (j + d r): part b of row j over range r of nr of that part's items
-// (contiguous in `sorted`: [OFF of (j, b, chunk 0), OFF of (j, b + 1, chunk 0)), the last
-// part's end being the total).  Lanes take consecutive 8-item chunks, two per iteration.
-__global__ void __launch_bounds__(1024) k_wide_accum(WideArgs q, unsigned long long* ctr, int64_t m, int d, int nr) {
+// Phase-2 work list: part b of row j gets ceil(items / B) CTAs over equal ranges of its items
+// (B = twice the mean part's items, at least 2^16), so a part that a heavy bin makes large is
+// spread over several SMs; a CTA of such a part is marked heavy.  One CTA of 1024 threads:
+// entries e = j S + b, scanned in rounds of 1024.
+__global__ void __launch_bounds__(1024) k_wide_plan(WideArgs q, int d, uint32_t B, uint32_t maxc) {
+  __shared__ uint32_t s_warp[32];
+  const int64_t ne = (int64_t)d * q.S;
+  const int64_t last = ne * q.nchunk - 1;
+  uint32_t carry = 0;
+  for (int64_t e0 = 0; e0 < ne; e0 += 1024) {
+    const int64_t e = e0 + threadIdx.x;
+    uint32_t P0 = 0, P1 = 0, k = 0;
+    if (e < ne) {
+      P0 = q.OFF[e * q.nchunk];
+      P1 = e + 1 < ne ? q.OFF[(e + 1) * q.nchunk] : q.OFF[last] + q.H[last];
+      k = (P1 - P0 + B - 1) / B;
+    }
+    uint32_t total;
+    const uint32_t first = carry + block_excl_scan_1024(k, s_warp, &total);
+    for (uint32_t r = 0; r < k; r++) {
+      if (first + r >= maxc) break;
+      const uint32_t lo = P0 + (uint32_t)(((uint64_t)(P1 - P0) * r) / k);
+      const uint32_t hi = P0 + (uint32_t)(((uint64_t)(P1 - P0) * (r + 1)) / k);
+      q.plan[first + r] = make_uint4((uint32_t)e, lo, hi, k > 1 ? 1u : 0u);
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) q.plan_n[0] = carry < maxc ? carry : maxc;
+}
+
+// One CTA per work-list entry (CTAs past the list's length return at once): part b of row j as
+// 2^15 int32 counters over its items [lo, hi) of `sorted`.  Lanes take consecutive 8-item
+// chunks, two per iteration.  In a heavy CTA each lane first merges runs of equal items among
+// its 8 (a heavy bin's items make most of such a part) and adds each run with one atomic.
+__global__ void __launch_bounds__(1024) k_wide_accum(WideArgs q, unsigned long long* ctr, int64_t m) {
+  if (blockIdx.x >= q.plan_n[0]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* cnt = (int*)smem_raw;
+  const uint4 wk = q.plan[blockIdx.x];
   const int S = q.S;
-  const int b = (int)(blockIdx.x % (unsigned)S);
-  const int rest = (int)(blockIdx.x / (unsigned)S);
-  const int j = rest % d;
-  const int r = rest / d;
+  const int j = (int)(wk.x / (uint32_t)S), b = (int)(wk.x % (uint32_t)S);
+  const uint32_t lo = wk.y, hi = wk.z;
+  const bool heavy = wk.w != 0;
   constexpr int L = 1 << 15;
   for (int k = threadIdx.x; k < L; k += blockDim.x) cnt[k] = 0;
   __syncthreads();
-  const int64_t kp = ((int64_t)j * S + b) * q.nchunk;
-  const int64_t last = (int64_t)d * S * q.nchunk - 1;
-  const uint32_t P0 = q.OFF[kp];
-  const uint32_t P1 = (j * S + b + 1 < d * S) ? q.OFF[kp + q.nchunk] : q.OFF[last] + q.H[last];
-  const uint32_t lo = P0 + (uint32_t)(((uint64_t)(P1 - P0) * r) / nr);
-  const uint32_t hi = P0 + (uint32_t)(((uint64_t)(P1 - P0) * (r + 1)) / nr);
   const uint32_t n = hi - lo;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(cnt);
   auto unit = [&](uint4 v, uint32_t bo) {   // slots bo .. bo + 7 counted from lo: add those below n
@@ -822,15 +864,38 @@ __global__ void __launch_bounds__(1024) k_wide_accum(WideArgs q, unsigned long l
       red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, bo + (uint32_t)k, n);
     }
   };
+  auto unit_merge = [&](uint4 v, uint32_t bo) {
+    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+    uint32_t prev = 0xffffffffu;   // no item has bits 16..31 set
+    int run = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t it = (e[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+      const bool valid = bo + (uint32_t)k < n;
+      const int sv = (it >> 15) ? -1 : 1;
+      if (valid && it == prev) {
+        run += sv;
+      } else if (valid) {
+        if (run != 0) atomicAdd(cnt + (prev & 0x7fffu), run);
+        prev = it;
+        run = sv;
+      }
+    }
+    if (run != 0) atomicAdd(cnt + (prev & 0x7fffu), run);
+  };
   const uint32_t ke = (hi + 7) >> 3;
   uint32_t k = (lo >> 3) + threadIdx.x;
-  for (; k + blockDim.x < ke; k += 2 * blockDim.x) {
-    const uint4 v1 = *(const uint4*)(q.sorted + 8 * (size_t)k);
-    const uint4 v2 = *(const uint4*)(q.sorted + 8 * (size_t)(k + blockDim.x));
-    unit(v1, 8 * k - lo);
-    unit(v2, 8 * (k + blockDim.x) - lo);
+  if (heavy) {
+    for (; k < ke; k += blockDim.x) unit_merge(*(const uint4*)(q.sorted + 8 * (size_t)k), 8 * k - lo);
+  } else {
+    for (; k + blockDim.x < ke; k += 2 * blockDim.x) {
+      const uint4 v1 = *(const uint4*)(q.sorted + 8 * (size_t)k);
+      const uint4 v2 = *(const uint4*)(q.sorted + 8 * (size_t)(k + blockDim.x));
+      unit(v1, 8 * k - lo);
+      unit(v2, 8 * (k + blockDim.x) - lo);
+    }
+    if (k < ke) unit(*(const uint4*)(q.sorted + 8 * (size_t)k), 8 * k - lo);
   }
-  if (k < ke) unit(*(const uint4*)(q.sorted + 8 * (size_t)k), 8 * k - lo);
   __syncthreads();
   unsigned long long* out = ctr + (int64_t)j * m + ((int64_t)b << 15);
   for (int x = threadIdx.x; x < L; x += blockDim.x) {
@@ -848,7 +913,8 @@ int64_t wide_window(int64_t n) {
 }
 
 struct WideLayout {
-  size_t plane, sorted, H, OFF, bsum, total;
+  size_t plane, sorted, H, OFF, bsum, plan, plan_n, total;
+  uint32_t maxc;   // phase-2 work-list capacity
 };
 
 WideLayout wide_layout(int d, int64_t m, int64_t W) {
@@ -862,7 +928,11 @@ WideLayout wide_layout(int d, int64_t m, int64_t W) {
   L.H = L.sorted + al(((size_t)d * W + 8) * sizeof(uint16_t));
   L.OFF = L.H + al((size_t)N * sizeof(uint32_t));
   L.bsum = L.OFF + al((size_t)N * sizeof(uint32_t));
-  L.total = L.bsum + al((size_t)((N + 4095) / 4096) * sizeof(uint32_t));
+  L.plan = L.bsum + al((size_t)((N + 4095) / 4096) * sizeof(uint32_t));
+  // at most one CTA per (row, part) plus one per 2^16 items
+  L.maxc = (uint32_t)((int64_t)d * S + ((int64_t)d * W >> 16) + 1);
+  L.plan_n = L.plan + al((size_t)L.maxc * sizeof(uint4));
+  L.total = L.plan_n + 256;
   return L;
 }
 
@@ -884,14 +954,14 @@ cudaError_t run_wide_partitioned(const UpdArgs& a, const TabArgs& t, void* stagi
   q.H = (uint32_t*)(base + Ly.H);
   q.OFF = (uint32_t*)(base + Ly.OFF);
   q.bsum = (uint32_t*)(base + Ly.bsum);
+  q.plan = (uint4*)(base + Ly.plan);
+  q.plan_n = (uint32_t*)(base + Ly.plan_n);
   q.W = W;
   q.S = (int)(a.m >> 15);
   const size_t smem = (size_t)4 << 15;
   cudaError_t e = allow_dynamic_smem((const void*)k_wide_accum);
-  int per_sm = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wide_accum, 1024, smem);
-  const int64_t slots = (int64_t)sms * std::max(1, per_sm);
   const int64_t units = (int64_t)q.S * a.d;
+  (void)sms;
   for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
     q.cnt = std::min(W, n - i0);
     for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
@@ -909,13 +979,12 @@ cudaError_t run_wide_partitioned(const UpdArgs& a, const TabArgs& t, void* stagi
     k_scan_sums<<<1, 1024, 0, st>>>(q.bsum, nb);
     k_scan_add<<<nb, 1024, 0, st>>>(q.OFF, N, q.bsum);
     k_wide_scatter<<<dim3((unsigned)q.nchunk, (unsigned)a.d), 256, 0, st>>>(q, (int64_t)a.m);
-    // ranges per (row, part): the grid a whole number of waves when that takes 1..16 waves
-    int64_t nr = 0;
-    for (int64_t k = 1; k <= 16 && !nr; k++)
-      if ((k * slots) % units == 0) nr = k * slots / units;
-    if (!nr) nr = std::max<int64_t>(1, (2 * slots + units - 1) / units);
-    k_wide_accum<<<(unsigned)(units * nr), 1024, smem, st>>>(q, a.ctr, (int64_t)a.m, a.d, (int)nr);
-    count_launch(6);
+    // phase-2 work: B = twice the mean part's items (at least 2^16) per CTA
+    const uint32_t B = (uint32_t)std::max<int64_t>((int64_t)1 << 16, 2 * (q.cnt * a.d) / std::max<int64_t>(1, units));
+    const uint32_t maxc = (uint32_t)std::min<int64_t>((int64_t)Ly.maxc, units + ((int64_t)a.d * q.cnt) / B + 1);
+    k_wide_plan<<<1, 1024, 0, st>>>(q, a.d, B, maxc);
+    k_wide_accum<<<maxc, 1024, smem, st>>>(q, a.ctr, (int64_t)a.m);
+    count_launch(7);
     e = cudaGetLastError();
   }
   return e;

@@ -286,7 +286,7 @@ def test_wide_partitioned_update_bit_exact(a, d, m, n, window, force, same, monk
     least m tuples; SK_PART_UPDATE=2 forces it for the smaller cases.  Keys at the table's
     first and last records and outside the domain (skipped and reported); one window or
     several; all tuples alike (every row's items in one part).  The launch count shows which
-    path ran: the table build plus six launches per window."""
+    path ran: the table build plus seven launches per window."""
     monkeypatch.setenv("SK_KEY_TABLE", "1")
     if force:
         monkeypatch.setenv("SK_PART_UPDATE", "2")
@@ -310,7 +310,7 @@ def test_wide_partitioned_update_bit_exact(a, d, m, n, window, force, same, monk
     launches = pkg.sk_launch_count() - L0
     per = window if window else n
     per = (per + 255) // 256 * 256
-    assert launches == 1 + 6 * ((n + per - 1) // per), launches
+    assert launches == 1 + 7 * ((n + per - 1) // per), launches
     keep = np.all((cols >= 0) & (cols < np.array(doms)[:, None]), axis=0)
     q = O.canonical_query(attrs, edges)
     co = O.draw_coefficients(777 + a, d, q.n_comp, len(q.edges))
