@@ -1133,11 +1133,12 @@ def run_subqueries(args, world, rank):
 
     fam = pkg.SketchFamily(wl.num_join_attrs, wl.edges, subs, wl.m, wl.d, wl.hash_seed)
     fam.set_estimator(args.estimator)
+    doms = declared_domains(args, wl)
 
     def fam_step():
         fam.reset()
         for kk, rel in enumerate(wl.relations):
-            fam.update(kk, rel.cols)
+            fam.update(kk, rel.cols, domain=doms[kk])
         return fam.estimate()
 
     # one SketchSet per sub-query, over the columns that sub-query joins
@@ -1147,16 +1148,17 @@ def run_subqueries(args, world, rank):
         attrs = [len(sub)] + [1] * len(sub)
         edges = [(0, t, 1 + t, 0) for t in range(len(sub))]
         fcols = wl.relations[0].cols[sub].contiguous() if len(sub) < k else wl.relations[0].cols
+        fdom = None if doms[0] is None else [doms[0][j] for j in sub]
         naive.append((pkg.SketchSet(attrs, edges, wl.m, wl.d, wl.hash_seed),
-                      [fcols] + [wl.relations[dd].cols for dd in dims]))
+                      [fcols] + [wl.relations[dd].cols for dd in dims], [fdom] + [doms[dd] for dd in dims]))
         naive[-1][0].set_estimator(args.estimator)
 
     def naive_step():
         outs = []
-        for sset, cols in naive:
+        for sset, cols, cdoms in naive:
             sset.reset()
             for kk, c in enumerate(cols):
-                sset.update(kk, c)
+                sset.update(kk, c, domain=cdoms[kk])
             outs.append(sset.estimate())
         return outs
 
@@ -1183,7 +1185,7 @@ def run_subqueries(args, world, rank):
     for _ in range(reps):
         fam.reset()
         for kk, rel in enumerate(wl.relations):
-            fam.update(kk, rel.cols)
+            fam.update(kk, rel.cols, domain=doms[kk])
     e1.record(stream)
     torch.cuda.synchronize()
     fam_upd_ms = e0.elapsed_time(e1) / reps
@@ -1210,15 +1212,16 @@ def run_subqueries(args, world, rank):
             "estimator": args.estimator,
             "config": {"workload": f"star F(K1..K{k}) {n_fact:.0e} rows Zipf 1.1 over [0,1e6), D_i {n_dim:.0e} "
                                    f"uniform; m=65536, d=9; all {len(subs)} connected sub-queries",
-                       "tuples_per_step": total},
+                       "tuples_per_step": total,
+                       "key_domains": "undeclared" if args.no_domains else "declared [0, 1e6) per column"},
             "family": {"ms_per_step": fam_ms, "update_ms": fam_upd_ms, "estimate_ms": fam_ms - fam_upd_ms,
                        "views": info["views"], "counter_bytes": info["counter_bytes"],
                        "gpu_launches_per_step": launches},
-            "one_set_per_subquery": {"ms_per_step": naive_ms, "relation_sketches": sum(len(c) for _, c in naive)},
+            "one_set_per_subquery": {"ms_per_step": naive_ms, "relation_sketches": sum(len(c) for _, c, _ in naive)},
             "speedup": naive_ms / fam_ms, "clocks": clocks,
             "parity": {"full_query_rows_equal_plain_set": same_full,
                        "subquery_join0_rows_0_1_equal_oracle": oracle_ok, "ok": bool(same_full and oracle_ok)}}
-    for sset, _ in naive:
+    for sset, _, _ in naive:
         sset.close()
     fam.close()
     return line

@@ -535,6 +535,11 @@ sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_row
   const size_t smem = (size_t)fam->d * fr.row_len * sizeof(uint64_t);
   const bool pow2 = (fam->m & (fam->m - 1)) == 0;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (domain_hint && !dev_weights) {
+    bool done = false;
+    const sk_status ps = family_partitioned_update(a, v.nv, v.amask, v.jmask, v.ctr, st, &done);
+    if (done || ps != SK_OK) return ps;
+  }
   cudaError_t e = pow2 ? dispatch_views<true>(a, v, smem, st) : dispatch_views<false>(a, v, smem, st);
   return set_status_from_cuda(e);
 }

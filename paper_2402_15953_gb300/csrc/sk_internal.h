@@ -137,5 +137,13 @@ std::vector<uint64_t> draw_coefficients(uint64_t seed, int d, int row_len);
 sk_status make_estimation_set(const QueryInfo& c, int64_t m, int d, uint64_t seed, std::vector<uint64_t> h_coef,
                               std::vector<int64_t*> rel_ctr, sk_set** out);
 void destroy_set(sk_set* s);
+namespace dev {
+struct UpdArgs;
+}
+// Sub-query family views of one relation through the partitioned update when the batch and
+// the views allow it (sk_update.cu); *done = false when it launched nothing.
+sk_status family_partitioned_update(const dev::UpdArgs& a, int nv, const uint32_t* amask,
+                                    const unsigned long long* jmask, unsigned long long* const* ctr, cudaStream_t st,
+                                    bool* done);
 
 }  // namespace sk

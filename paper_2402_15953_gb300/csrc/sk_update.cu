@@ -143,6 +143,7 @@ struct PartArgs {
   int64_t C;                     // item slots per (warp, row) region: 32 x tiles per warp
   int nwarps;                    // warps of the phase-1 grid
   int logL;                      // part width 2^L
+  const uint32_t* vbits;         // nullptr, or bit (i mod 32) of word i / 32: window tuple i is kept
 };
 
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(256, 4) k_tab_items(UpdArgs p, TabArgs t, Part
   }
   for (; g < gend; g += step) {
     const bool in = g < q.cnt;
-    const bool ok = in && okm == (1u << A) - 1u;
+    const bool ok = in && okm == (1u << A) - 1u && (!q.vbits || ((q.vbits[g >> 5] >> lane) & 1u));
     uint32_t kg[A];   // global record indices (the host keeps this path's tables below 2^32 records)
 #pragma unroll
     for (int u = 0; u < A; u++) kg[u] = (uint32_t)t.base[u] + kx[u];
@@ -521,7 +522,11 @@ size_t part_staging_bytes(int d, int64_t W, int sms) {
 }
 
 // Both phases over every window of the batch; staging (part_staging_bytes) is caller-owned.
-cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* staging, int sms, cudaStream_t st) {
+// colp: the first tuple's key of each of the a.a attributes (nullptr: a.cols + u a.stride).
+// vbits: nullptr, or one bit per batch tuple (bit i mod 32 of word i / 32) that must be set
+// for the tuple to be added.
+cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* staging, int sms, cudaStream_t st,
+                            const int64_t* const* colp = nullptr, const uint32_t* vbits = nullptr) {
   const int64_t n = a.n;
   int tab_per_sm = 1;
   cudaError_t e = fmt == 0   ? tab_items_occupancy<0>(a.a, &tab_per_sm)
@@ -547,7 +552,9 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
   const int64_t units = (int64_t)S * a.d;
   for (int64_t i0 = 0; i0 < n && e == cudaSuccess; i0 += W) {
     q.cnt = std::min(W, n - i0);
-    for (int u = 0; u < 5; u++) q.col[u] = u < a.a ? a.cols + (int64_t)u * a.stride + i0 : nullptr;
+    for (int u = 0; u < 5; u++)
+      q.col[u] = u < a.a ? (colp ? colp[u] : a.cols + (int64_t)u * a.stride) + i0 : nullptr;
+    q.vbits = vbits ? vbits + i0 / 32 : nullptr;   // windows start at multiples of 256
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((q.cnt + 255) / 256, full_grid));
     const int64_t gend = (q.cnt + 31) / 32 * 32;
     q.C = 32 * ((gend + (int64_t)grid * 256 - 1) / ((int64_t)grid * 256));
@@ -1542,6 +1549,115 @@ sk_status launch_merge(int64_t* dst, const int64_t* src, int64_t count, cudaStre
   k_merge<<<grid, 256, 0, st>>>((unsigned long long*)dst, (const unsigned long long*)src, count);
   count_launch();
   return set_status_from_cuda(cudaGetLastError());
+}
+
+// One bit per tuple: all of the relation's keys inside their declared domains (a tuple with a
+// key outside is reported and left out of every view).
+__global__ void __launch_bounds__(256) k_valid_bits(UpdArgs p, uint32_t* bits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = i < p.n;
+  if (ok)
+    for (int u = 0; u < p.a; u++) {
+      const int64_t key = ld_key_stream(p.cols + (int64_t)u * p.stride + i);
+      if ((uint64_t)key >= (uint64_t)p.dom[u]) ok = false;
+    }
+  if (i < p.n && !ok) record(p.status, SK_ERR_KEY_OUT_OF_DOMAIN);
+  const uint32_t b = __ballot_sync(0xffffffffu, ok);
+  if ((threadIdx.x & 31u) == 0 && i < p.n) bits[i >> 5] = b;
+}
+
+// Sub-query family views of one relation through the two-phase partitioned update (see
+// run_partitioned): when every attribute has exactly one sign slot, a view's sign is the
+// product of its attributes' slot-0 signs and its bin the sum of their bins, so one 24-byte
+// key table over the relation's attributes (built once) serves every view, and each view's
+// counters get both phases over the view's attributes (a validity pass over all of the
+// relation's keys first: a tuple is left out of every view when any key is outside its
+// domain, as in the per-tuple view update).  Taken for unit weights with declared
+// domains, power-of-two 1024 <= m <= 2^16, d <= 9, views of at most 5 attributes, at least
+// 16 m tuples and views too large for one CTA's shared memory; *done = false (nothing
+// launched) otherwise, and the caller runs its per-tuple view update.
+sk_status family_partitioned_update(const UpdArgs& a, int nv, const uint32_t* amask, const unsigned long long* jmask,
+                                    unsigned long long* const* ctr, cudaStream_t st, bool* done) {
+  *done = false;
+  const int64_t n = a.n;
+  const bool pow2 = (a.m & (a.m - 1)) == 0;
+  if (part_update_mode() == 0 || key_table_mode() == 0 || !a.has_dom || a.w != nullptr || !pow2 || a.m < 1024 ||
+      a.m > 65536 || a.d > 9 || a.a < 1 || a.a > kMaxAttrs || n < (int64_t)a.m * 16 ||
+      (size_t)a.d * a.m * sizeof(int) <= 200 * 1024 || !all_deg1(a))
+    return SK_OK;
+  TabArgs t;
+  int64_t total = 0;
+  int off = 0;
+  for (int u = 0; u < a.a; u++) {
+    if (a.dom[u] < 1 || a.dom[u] > (1ll << 31)) return SK_OK;
+    t.base[u] = total;
+    t.off[u] = off;
+    total += a.dom[u];
+    off += 2 + 4 * a.deg[u];
+  }
+  t.base[a.a] = total;
+  t.narrow = 1;
+  t.rvec = 2;
+  if (total >= ((int64_t)1 << 32) || (key_table_mode() != 1 && total * 4 > n * (int64_t)a.a)) return SK_OK;
+  for (int v = 0; v < nv; v++) {
+    // slot i is attribute i's only slot: a view's signs are those of its attributes
+    if (__builtin_popcount(amask[v]) > 5 || (unsigned long long)amask[v] != jmask[v]) return SK_OK;
+  }
+  const size_t tbytes = (size_t)total * 24;
+  if (tbytes > key_table_max_bytes()) return SK_OK;
+  const int sms = sm_count();
+  void* tbl = nullptr;
+  void* staging = nullptr;
+  if (pool_malloc_async(&tbl, tbytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return SK_OK;
+  }
+  const size_t sbytes = part_staging_bytes(a.d, part_window(n), sms);
+  const size_t vbytes = (size_t)(n + 31) / 32 * sizeof(uint32_t);
+  if (pool_malloc_async(&staging, sbytes + ((vbytes + 255) & ~(size_t)255), st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(tbl, st);
+    return SK_OK;
+  }
+  *done = true;
+  uint32_t* vbits = (uint32_t*)((char*)staging + sbytes);
+  t.tbl = (uint32_t*)tbl;
+  const size_t coef_bytes = (size_t)a.d * a.row_len * sizeof(uint64_t);
+  cudaError_t e = fit_dynamic_smem((const void*)k_key_table_l24<true>, coef_bytes);
+  if (e == cudaSuccess) {
+    const int bgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 32);
+    k_key_table_l24<true><<<bgrid, 256, coef_bytes, st>>>(a, t);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_valid_bits<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, vbits);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  for (int v = 0; v < nv && e == cudaSuccess; v++) {
+    UpdArgs av = a;
+    TabArgs tv = t;
+    const int64_t* colp[5];
+    int k = 0;
+    for (int u = 0; u < a.a; u++) {
+      if (!((amask[v] >> u) & 1u)) continue;
+      av.dom[k] = a.dom[u];
+      av.deg[k] = a.deg[u];
+      tv.base[k] = t.base[u];
+      colp[k] = a.cols + (int64_t)u * a.stride;
+      k++;
+    }
+    if (k == 0) continue;
+    av.a = k;
+    tv.base[k] = total;
+    av.ctr = ctr[v];
+    e = run_partitioned(av, tv, 2, staging, sms, st, colp, vbits);
+  }
+  cudaError_t ef = cudaFreeAsync(tbl, st);
+  const cudaError_t es = cudaFreeAsync(staging, st);
+  if (ef == cudaSuccess) ef = es;
+  return set_status_from_cuda(e != cudaSuccess ? e : ef);
 }
 
 }  // namespace sk

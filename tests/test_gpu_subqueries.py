@@ -159,3 +159,46 @@ def test_six_attribute_relation_and_view_limit():
     fam = pkg.SketchFamily(attrs, edges, subs[:64], 64, 3, 1)
     assert fam.info()["subqueries"] == 64
     fam.close()
+
+
+@pytest.mark.parametrize("m,n,doms,bad", [(1 << 13, 200_003, [5000, 7000, 30_000, 300], False),
+                                          (1 << 16, 1_048_607, [5000, 70_000, 100_000, 300], True)])
+def test_star_family_partitioned_views(m, n, doms, bad):
+    """A 4-dimension star's family with declared key domains and unit weights: the fact
+    relation's 15 views (one per non-empty subset of its joins; every attribute in one join)
+    go through one key table and the two-phase partitioned update per view (table build,
+    validity pass, two launches per view).  Every sub-query's sketches bit-exact against the oracle (the
+    estimator, unchanged, is checked on these sketches elsewhere); with keys outside their
+    domain, those tuples are skipped and reported."""
+    import itertools
+    import synth
+    k = 4
+    attrs, edges = [k] + [1] * k, [(0, i, 1 + i, 0) for i in range(k)]
+    subs = [list(c) for size in range(1, k + 1) for c in itertools.combinations(range(k), size)]
+    fcols = np.stack([synth.zipf_keys(n, 1.1, doms[u], 60 + u).numpy() for u in range(k)])
+    if bad:
+        fcols[1, 7] = doms[1]
+        fcols[3, n - 1] = -4
+    rng = np.random.default_rng(3)
+    rels = [(fcols, None)] + [(rng.integers(0, doms[u], size=(1, 20_000)).astype(np.int64), None) for u in range(k)]
+    fam = pkg.SketchFamily(attrs, edges, subs, m, 9, 21)
+    fam.set_estimator("fused")
+    L0 = pkg.sk_launch_count()
+    fam.update(0, torch.as_tensor(fcols).cuda(), domain=doms)
+    assert pkg.sk_launch_count() - L0 == 2 + 2 * len(subs)
+    for kk in range(1, k + 1):
+        fam.update(kk, torch.as_tensor(rels[kk][0]).cuda(), domain=[doms[kk - 1]])
+    if bad:
+        with pytest.raises(pkg.SketchError):
+            fam.sync()
+    fam.sync()
+    keep = np.all((fcols >= 0) & (fcols < np.array(doms)[:, None]), axis=0)
+    rels[0] = (fcols[:, keep], None)
+    q = O.canonical_query(attrs, edges)
+    co = O.draw_coefficients(21, 9, q.n_comp, len(q.edges))
+    for i, sub in enumerate(subs):
+        sq = O.subquery(attrs, edges, co, sub)
+        sk = O.sketch_all(sq.query, sq.coeffs, O.subquery_relations(sq, rels), m, threads=16)
+        for ks in range(sq.query.r):
+            assert np.array_equal(fam.sketch(i, ks), sk[ks]), (sub, ks)
+    fam.close()
