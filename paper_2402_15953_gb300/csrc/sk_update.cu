@@ -611,7 +611,7 @@ cudaError_t run_partitioned(const UpdArgs& a, const TabArgs& t, int fmt, void* s
 //      sketch with one 64-bit reduction.
 // Every counter receives the same integer sum as with one reduction per (tuple, row).
 // ---------------------------------------------------------------------------
-constexpr int kWideChunk = 2048;   // tuples per phase-1 CTA (256 threads x 8)
+constexpr int kWideChunk = 4096;   // tuples per phase-1 CTA (256 threads x 16; 2048: chain8 update 9.04 vs 8.72 ms)
 constexpr int kWideMaxRows = 16;
 constexpr int kWideMaxParts = 512;  // m <= 2^24
 
