@@ -254,7 +254,9 @@ __device__ __forceinline__ void ld_record24(const uint64_t* tbl, uint64_t k, uin
 // next tuple before it gathers the records of the current one, so the key stream's latency
 // overlaps the gathers.  Lanes of a warp take consecutive tuples (one tile) and iterate
 // together (the ballots need the whole warp).  Four CTAs per SM (64 registers): with the
-// running counts five (48 registers) spilled and took the star's F update from 3.10 to 3.84 ms.
+// running counts five (48 registers) spilled and took the star's F update from 3.10 to 3.84 ms;
+// six for the instances of one or two attributes (40 registers, no spills) took a sub-query
+// family's update from 8.45 to 9.22 ms.
 template <int A, int FMT>
 __global__ void __launch_bounds__(256, 4) k_tab_items(UpdArgs p, TabArgs t, PartArgs q) {
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
