@@ -395,6 +395,35 @@ __device__ __forceinline__ void red_shared_if_lt(uint32_t saddr, int v, uint32_t
                ::"r"(saddr), "r"(v), "r"(x), "r"(n) : "memory");
 }
 
+__device__ __forceinline__ void red_shared(uint32_t saddr, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+
+// The 8 items of one 16-byte chunk (two per 32-bit word: bin offset in bits 0..14, sign in
+// bit 15) added into the shared counters at sbase; slots b .. b + 7 counted from the run's
+// first item, those at or beyond n skipped.  A chunk wholly inside the run (every chunk but
+// a run's first and last) goes without the per-slot compare.
+__device__ __forceinline__ void add_chunk(uint32_t sbase, uint4 v, uint32_t b, uint32_t n) {
+  const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+  if (n >= 8u && b <= n - 8u) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
+      int neg;   // 0 or -1 from the item's sign bit
+      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
+      red_shared(sbase + ((it & 0x7fffu) << 2), neg | 1);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
+      int neg;
+      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
+      red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k, n);
+    }
+  }
+}
+
 // blockIdx.x = h + S (row + d c), S = m >> logL: part h of row `row` over the regions of the
 // phase-1 warps [c R, min(c R + R, nwarps)), each region's part-h chunks (8 items, one 16-byte
 // load) split into 2^logP pieces.  Warp k of the CTA takes pieces k, k + 32, ...; lane l of a
@@ -418,16 +447,7 @@ __global__ void __launch_bounds__(1024) k_part_accum(PartArgs q, unsigned long l
   const int npc = (w1 - w0) << logP;
   const uint32_t C = (uint32_t)q.C;
   // slots b .. b + 7 counted from the part's first item: add the signs of those below n
-  auto unit = [&](uint4 v, uint32_t b, uint32_t n) {
-    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
-      int neg;   // 0 or -1 from the item's sign bit
-      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
-      red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, b + (uint32_t)k, n);
-    }
-  };
+  auto unit = [&](uint4 v, uint32_t b, uint32_t n) { add_chunk(sbase, v, b, n); };
   for (int pc = (int)(threadIdx.x >> 5); pc < npc; pc += (int)(blockDim.x >> 5)) {
     const int w = w0 + (pc >> logP);
     const uint32_t piece = (uint32_t)pc & ((1u << logP) - 1u);
@@ -863,16 +883,8 @@ __global__ void __launch_bounds__(1024) k_wide_accum(WideArgs q, unsigned long l
   __syncthreads();
   const uint32_t n = hi - lo;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(cnt);
-  auto unit = [&](uint4 v, uint32_t bo) {   // slots bo .. bo + 7 counted from lo: add those below n
-    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const uint32_t it = e[k >> 1] >> (16 * (k & 1));
-      int neg;   // 0 or -1 from the item's sign bit
-      asm("bfe.s32 %0, %1, 15, 1;" : "=r"(neg) : "r"(it));
-      red_shared_if_lt(sbase + ((it & 0x7fffu) << 2), neg | 1, bo + (uint32_t)k, n);
-    }
-  };
+  // slots bo .. bo + 7 counted from lo: add those below n
+  auto unit = [&](uint4 v, uint32_t bo) { add_chunk(sbase, v, bo, n); };
   auto unit_merge = [&](uint4 v, uint32_t bo) {
     const uint32_t e[4] = {v.x, v.y, v.z, v.w};
     uint32_t prev = 0xffffffffu;   // no item has bits 16..31 set
