@@ -418,17 +418,17 @@ def run_ours(args, world, rank, local):
         # adds them into a half-row int32 sketch in shared memory, flushing each counter once
         # (phase 2).
         # HBM roofline: algorithmic bytes = the 40 key bytes per tuple.  traffic = DRAM bytes
-        # of one ncu capture of both phases at 2e7 rows (k_tab_items 1.4752 GB read + 0.4120 GB
+        # of one ncu capture of both phases at 2e7 rows (k_tab_items 1.4755 GB read + 0.4119 GB
         # written, k_part_accum 0.3665 + 0.0002 GB: key stream, record misses and the items'
         # round trip) scaled to this row count, plus the table write (5e6 x 24 B).
-        # L2 roofline beside it: L2 requests per tuple from the same capture (5.72: 5.21 in
-        # phase 1, 0.51 in phase 2; 16.35 with one 64-bit reduction per counter update).
+        # L2 roofline beside it: L2 requests per tuple from the same capture (5.71: 5.21 in
+        # phase 1, 0.50 in phase 2; 16.35 with one 64-bit reduction per counter update).
         # The bound phase 1 meets is the L1 data pipe: 5.97 wavefronts per tuple (one per
         # record gather and lane, plus the key loads and item stores), 82 % of its peak of one
         # wavefront per clock and SM in that capture.
-        traffic = (1.4752 + 0.4120 + 0.3665 + 0.0002) * args.fact_rows / 2e7 + 5 * 1_000_000 * 24 / 1e9
+        traffic = (1.4755 + 0.4119 + 0.3665 + 0.0002) * args.fact_rows / 2e7 + 5 * 1_000_000 * 24 / 1e9
         kernel = "k_key_table_l24 + k_tab_items<5,24B> + k_part_accum (fact table F, two-phase)"
-        l2_req_per_tuple = 5.72
+        l2_req_per_tuple = 5.71
         l2_peak = 188 * 2.016e9
         l2_rate = l2_req_per_tuple * args.fact_rows / fact_s
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -441,7 +441,7 @@ def run_ours(args, world, rank, local):
                                  "per_tuple": l2_req_per_tuple, "kernel": kernel,
                                  "source": "ncu lts__t_requests of k_tab_items + k_part_accum (2e7 rows)"},
                  "roofline_l1_phase1": {"bound": "l1_data_pipe_wavefronts", "per_tuple": 5.97,
-                                        "frac_ncu": 0.821, "kernel": "k_tab_items<5,24B>",
+                                        "frac_ncu": 0.824, "kernel": "k_tab_items<5,24B>",
                                         "source": "ncu l1tex__data_pipe_lsu_wavefronts (2e7 rows)"}}
     else:
         # Per-tuple hashing (no declared domains): integer-ALU roofline, algorithmic work =
