@@ -623,12 +623,15 @@ def run_e2e(args, s, wl, stream, world):
     torch.cuda.synchronize()
     barrier(world)
     steps = max(3, args.steps // 3)
-    t0 = time.perf_counter()
+    # device time with CUDA events: from the step's stream before the first copy is issued to
+    # the same stream after the last estimate (which waited on every copy and update)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for _ in range(steps):
         step()
+    e1.record(stream)
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
-    dt = max_over_ranks(world, dt)
+    dt = max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / steps)
     total = sum(h.shape[1] for h in host)
     d = wl.d
     d2h = 4 * (8 + 3 * d * 32 + 8) + 2 * d * 32 + 4
@@ -982,11 +985,13 @@ def run_e2e_direct(args, s, wl, stream, world):
     torch.cuda.synchronize()
     barrier(world)
     steps = max(3, args.steps // 3)
-    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for _ in range(steps):
         step()
+    e1.record(stream)
     torch.cuda.synchronize()
-    dt = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+    dt = max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / steps)
     total = sum(h.shape[1] for h in host)
     d = wl.d
     d2h = 4 * (256 + (1 + 3 * d) * 8) + 2 * d * 32 + 4
@@ -1032,10 +1037,12 @@ def run_e2e_direct_pipelined(args, wl, world):
     torch.cuda.synchronize()
     barrier(world)
     steps = max(3, args.steps // 3)
-    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(upd)
     outs = run(steps)
+    e1.record(est)
     torch.cuda.synchronize()
-    dt = max_over_ranks(world, (time.perf_counter() - t0) / steps)
+    dt = max_over_ranks(world, e0.elapsed_time(e1) / 1e3 / steps)
     for x in sets:
         x.close()
     total = sum(h.shape[1] for h in host)
