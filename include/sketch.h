@@ -146,15 +146,21 @@ sk_status sk_sketch_create(const sk_query* query, int64_t m, int32_t d, uint64_t
  * n_rows * |Omega|) and the relation's d * m * 8-byte sketch is at most 32 MiB
  * (environment: SK_KEY_TABLE=0 never, =1 whenever the bounds allow).  The table
  * (sum of bounds * 16 or 32 bytes when m <= 2^16 and d <= 14; 24 bytes for the
- * two-phase update below when d <= 9) comes from the device's stream-ordered pool
- * and is released on cuda_stream at the end of the call; if it cannot be
- * allocated the call hashes per tuple.  Unit-weight batches (dev_weights NULL)
- * into a power-of-two 1024 <= m <= 2^16 with d <= 14, at most 5 attributes, at
- * least 16 m rows and a d * m int32 sketch too large for one CTA's shared memory
- * update in two phases through the table: per-tuple bins written as 16-bit items
- * (2 d bytes per row of staging from the same pool), then added per half row in
- * shared memory (SK_PART_UPDATE=0 keeps the one-phase table update).  Results
- * are identical on every path.
+ * two-phase update below when d <= 9; 4 d rounded up to 16 bytes otherwise) comes
+ * from the device's stream-ordered pool and is released on cuda_stream at the end
+ * of the call; if it cannot be allocated the call hashes per tuple.  Unit-weight
+ * batches (dev_weights NULL) into a power-of-two 1024 <= m <= 2^16 with d <= 14, at
+ * most 5 attributes, at least 16 m rows and a d * m int32 sketch too large for one
+ * CTA's shared memory update in two phases through the table: per-tuple bins
+ * written as 16-bit items (2 d bytes per row of staging from the same pool, in
+ * windows of at most 2^30 rows), then added per half row in shared memory.
+ * Unit-weight batches into a power-of-two 2^17 <= m <= 2^24 with d <= 16, at most 5
+ * attributes, at least m rows and a sketch larger than 32 MiB take the table too
+ * (the lookups then replace one L2 reduction per counter update that would miss
+ * L2) and sort each row's bins by part of 2^15 bins before adding them in shared
+ * memory (6 d bytes per row of staging, windows of at most 2^24 rows).
+ * SK_PART_UPDATE=0 keeps the one-phase table update and the per-tuple update for
+ * both.  Results are identical on every path.
  * Asynchronous on cuda_stream; the columns and weights must stay valid until it
  * completes.  n_rows == 0 is a no-op.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
@@ -484,8 +490,16 @@ sk_status sk_family_create(const sk_query* query, int32_t n_sub, const int32_t* 
 /* sk_family_update_batch: Algorithm 2 for a batch of Q's relation `relation`,
  * laid out as for sk_sketch_update_batch (all |Omega(R_k)| columns of Q).  One
  * pass hashes every tuple once per row and adds it to every view of R_k (each
- * view with its own bin sum and sign product).  A relation in no sub-query is a
- * no-op.  Domain violations are recorded and reported by sk_family_sync.
+ * view with its own bin sum and sign product).  When every attribute of R_k has
+ * one sign slot (each in one join of Q), the batch has unit weights and declared
+ * domains, m is a power of two in [1024, 2^16], d <= 9, views have at most 5
+ * attributes and the batch at least 16 m rows, the call instead builds one key
+ * table over R_k's attributes (24 bytes per domain key) and runs the two-phase
+ * update of sk_sketch_update_batch once per view (staging from the same pool;
+ * SK_PART_UPDATE=0 keeps the one-pass update).  A tuple with any key outside its
+ * domain is left out of every view.  A relation in no sub-query is a no-op.
+ * Domain violations are recorded and reported by sk_family_sync.  Results are
+ * identical on both paths.
  * Errors: SK_ERR_INVALID_ARG, SK_ERR_CUDA. */
 sk_status sk_family_update_batch(sk_family* fam, int32_t relation, int64_t n_rows, const int64_t* dev_cols,
                                  int64_t col_stride, const int64_t* dev_weights, const int64_t* domain_hint,
